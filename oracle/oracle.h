@@ -1,0 +1,95 @@
+/*
+ * FP64 CPU oracle for the PnP-ULA Gaussian-deconvolution sampler.
+ *
+ * TEST INFRASTRUCTURE ONLY. This library is the slow, plainly written
+ * reference that the CUDA path is checked against. Only the test suite, the
+ * smoke check and the benchmark's CPU-baseline leg may load it; the product
+ * path never calls it and shares no code with it.
+ *
+ * Every routine follows the paper's definitions directly, with no blocking,
+ * fusion or reordering beyond what the definition states:
+ *   - circular blur H and its adjoint H^T           (Sec. III-A2, Eq. 12 likelihood)
+ *   - multichannel "half-padding" 3x3 convolution    (Sec. II-B, Eqs. 5-6)
+ *   - DnCNN-form denoiser D = Id - G, G = T_K o ... o T_1 (Sec. II-B, Example 1)
+ *   - block-wise denoiser with a halo (Defs. 1-2, Sec. II-B2, receptive-field variant)
+ *   - Philox4x32-10 (Salmon et al., SC'11) + Box-Muller normals
+ *   - one PnP-ULA transition (Eq. 8 / Algorithm 1, x-update), f2 = 0
+ *   - step sizes (Eq. 10 conditions, Sec. III-B Gaussian-noise setting)
+ *   - online (Welford) and two-pass moments (Sec. III-C, footnote on variance)
+ *
+ * Parity pins live in tests/test_oracle_*.py. Status of each function:
+ *   ora_philox4x32_10      pinned (library Philox, statistics)
+ *   ora_normals            pinned (moments, KS, Box-Muller identity)
+ *   ora_blur / ora_blur_adj pinned (DFT convolution theorem, adjoint identity)
+ *   ora_conv_layer         pinned (library conv2d)
+ *   ora_denoise            pinned (layer composition vs library, Id - G form)
+ *   ora_denoise_blockwise  pinned (equals whole image iff halo >= K)
+ *   ora_langevin_step      pinned (closed-form Gaussian recursion and stationary
+ *                          law; projection and linear-prior fixed points)
+ *   ora_run_chain moments  pinned (two-pass vs Welford, stored samples)
+ *   ora_stepsizes          pinned (Eq. 10 inequalities)
+ */
+#ifndef PNP_ORACLE_H
+#define PNP_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* DnCNN-form network: K layers of ks x ks cross-correlations, layer k maps
+ * cin[k] -> cout[k] channels, weights OIHW concatenated over layers, biases
+ * concatenated. ReLU after every layer but the last. */
+typedef struct {
+    int K;
+    const int* cin;
+    const int* cout;
+    int ks;
+    const double* w;
+    const double* b;
+} ora_net;
+
+typedef struct {
+    int ny, nx;              /* image size (one channel)                      */
+    const double* y;         /* observation [ny*nx]                           */
+    const double* h;         /* blur kernel [kh*kw], anchored at (kh/2, kw/2) */
+    int kh, kw;
+    double sigma;            /* noise std: f1(Hx) = ||y - Hx||^2 / (2 sigma^2) */
+    double alpha, eps;       /* prior weight and denoiser noise level         */
+    double lambda;           /* Moreau-Yosida parameter of iota_C; <= 0: term off */
+    double gamma;            /* step size                                     */
+    uint64_t seed;           /* Philox key                                    */
+    const ora_net* net;      /* NULL: no denoiser term                        */
+    int noise;               /* 0: xi := 0 (deterministic recursion)          */
+} ora_problem;
+
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void ora_normals(uint64_t seed, uint32_t t, uint32_t chain, int64_t n, double* xi);
+
+void ora_blur(const double* x, int ny, int nx, const double* h, int kh, int kw, double* out);
+void ora_blur_adj(const double* r, int ny, int nx, const double* h, int kh, int kw, double* out);
+
+void ora_conv_layer(const double* in, int cin, int ny, int nx, const double* w,
+                    const double* b, int cout, int ks, int relu, double* out);
+void ora_denoise(const double* v, int ny, int nx, const ora_net* net, double* out);
+int  ora_denoise_blockwise(const double* v, int ny, int nx, const ora_net* net,
+                           int by, int bx, int halo, double* out);
+
+void ora_stepsizes(double hnorm, double sigma, double alpha, double eps, double lip_eps,
+                   double c, double* lambda, double* gamma);
+
+void ora_langevin_step(const ora_problem* p, const double* x, uint32_t t, uint32_t chain,
+                       double* xnew);
+/* Runs iterations t = t0 .. t0+T-1 from x (updated in place). Samples
+ * x^(t+1) with t+1 > burn_in enter the FP64 Welford moments (mean, m2, *n).
+ * samples (optional) receives every kept sample, [n_kept][ny*nx]. */
+void ora_run_chain(const ora_problem* p, double* x, int t0, int T, int burn_in,
+                   uint32_t chain, double* mean, double* m2, int64_t* n_kept,
+                   double* samples);
+void ora_moments_two_pass(const double* samples, int64_t n, int64_t npix,
+                          double* mean, double* var);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
