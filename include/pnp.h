@@ -1,0 +1,202 @@
+/*
+ * pnp.h -- C ABI of the B300 (sm_103a) PnP-ULA sampler for Gaussian deconvolution.
+ *
+ * The library runs the x-update of the paper's distributed sampler
+ * (Algorithm 1 with f2 = 0, Sec. III-A2 / III-B(i)) on one GPU:
+ *
+ *   x+ = x - gamma H^T (H x - y) / sigma^2 + (alpha gamma / eps^2) (D_eps(x) - x)
+ *          + (gamma / lambda) (proj_[0,1](x) - x) + sqrt(2 gamma) xi          (Eq. 8)
+ *
+ * with H a circular 2-D blur, D_eps a DnCNN-form denoiser (Sec. II-B, Example 1)
+ * evaluated block-wise (Defs. 1-2), xi drawn from a counter-based Philox stream,
+ * and MMSE / pixel-wise variance accumulated online after burn-in (Sec. III-C).
+ *
+ * Conventions for every entry point:
+ *  - Return value is a pnp_status; PNP_OK on success. On failure nothing is
+ *    left half-done on the host side and pnp_last_error() returns a
+ *    thread-local message.
+ *  - "device" pointers are CUDA global-memory pointers on the current device;
+ *    "host" pointers are ordinary CPU memory. The caller owns every buffer it
+ *    passes; objects created by the library own their own device memory and
+ *    free it in the matching destroy call.
+ *  - stream arguments are cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Operator entry points are asynchronous on that stream.
+ *  - Images are row-major FP32 [ny][nx], one channel. Multi-chain and batch
+ *    arrays are [n][ny][nx] with the image index slowest.
+ *  - No callbacks, no exceptions cross the ABI. Calls on one object are not
+ *    thread-safe; different objects may be used from different threads.
+ */
+#ifndef PNP_H
+#define PNP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PNP_OK = 0,
+    PNP_EINVAL = 1,    /* bad argument (sizes, pointers, step sizes, halo < K ...) */
+    PNP_ENOMEM = 2,    /* device allocation failed                                */
+    PNP_EBUSY = 3,     /* admission refused: request can never fit the budget    */
+    PNP_ECUDA = 4,     /* CUDA runtime / driver error (message in pnp_last_error) */
+    PNP_ETIMEOUT = 5,  /* a bounded device-side wait ran out                      */
+    PNP_ESTATE = 6,    /* call not valid in the object's current state           */
+    PNP_ENOTSUP = 7    /* feature not supported on this device                    */
+} pnp_status;
+
+typedef enum {
+    PNP_FP32 = 0,      /* denoiser convolutions in FP32 on CUDA cores                     */
+    PNP_BF16 = 1,      /* BF16 operands, FP32 accumulation, tcgen05 tensor cores          */
+    PNP_FP8 = 2        /* E4M3 operands with per-output-channel scales, FP32 accumulation */
+} pnp_precision;
+
+typedef struct pnp_denoiser pnp_denoiser;
+typedef struct pnp_problem pnp_problem;
+typedef struct pnp_batch pnp_batch;
+typedef struct pnp_server pnp_server;
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* pnp_last_error(void);
+/* Library version string. */
+const char* pnp_version(void);
+
+/* ------------------------------------------------------------------------
+ * Denoiser D_eps = Id - G_eps, G_eps = T_K o ... o T_1,
+ * T_k(v) = ReLU(W_k v + b_k) for k < K, T_K(v) = W_K v + b_K
+ * (Sec. II-B, Eqs. 5-6 and Example 1 "DnCNN").
+ * Layers: 1 -> F, F -> F (K-2 times), F -> 1; 3x3 zero-padded ("half
+ * padding") cross-correlations. weights: host FP32, per layer OIHW
+ * [cout][cin][3][3], concatenated in layer order; biases: host FP32 [cout]
+ * per layer, concatenated. Both are copied. lipschitz_eps is the L_eps bound
+ * of Id - D_eps used for the step sizes (Sec. II-C). Supported: K >= 2,
+ * F in {16, 32, 64} for FP32; F = 64 for BF16/FP8.
+ * ------------------------------------------------------------------------ */
+pnp_status pnp_create_denoiser(int K, int F, const float* weights, const float* biases,
+                               double lipschitz_eps, pnp_denoiser** out);
+void pnp_destroy_denoiser(pnp_denoiser* d);
+
+/* ------------------------------------------------------------------------
+ * Operator entry points (device pointers, asynchronous on `stream`).
+ * ------------------------------------------------------------------------ */
+
+/* r[c] = h (*) x[c] - y for c < nimg: circular convolution with the kh x kw
+ * kernel h (anchored at (kh/2, kw/2)), Gaussian-deconvolution likelihood
+ * residual (Sec. III-A2, Eq. 12). x, r: device [nimg][ny][nx]; y: device
+ * [ny][nx] or NULL (then r = h (*) x); h: device [kh][kw]. kh, kw odd,
+ * <= 31 and <= the image size. */
+pnp_status pnp_blur(const float* x, const float* y, const float* h, int kh, int kw,
+                    int ny, int nx, int nimg, float* r, void* stream);
+
+/* g[c] = scale * H^T r[c]: circular correlation with h (the adjoint of
+ * pnp_blur's operator). Same layout rules as pnp_blur. */
+pnp_status pnp_blur_adjoint(const float* r, const float* h, int kh, int kw, int ny, int nx,
+                            int nimg, float scale, float* g, void* stream);
+
+/* d[c] = D_eps(x[c]) for nimg images [nimg][ny][nx] (device). halo == 0:
+ * layers run over the whole image, each tile reading its neighbours' pixels
+ * directly (exact whole-image result for any block split). halo > 0: the
+ * image is cut into blocks_y x blocks_x blocks (floor rule, Sec. II-B2 Eq. 7),
+ * each block is extended by `halo` pixels, the network runs on every extended
+ * block independently with out-of-image positions held at zero after every
+ * layer, and block interiors are written back (receptive-field variant,
+ * Sec. II-B2); equals the halo == 0 result iff halo >= K.
+ * Scratch: the library allocates and caches device scratch per denoiser
+ * (activations of two layers). */
+pnp_status pnp_denoise(const pnp_denoiser* D, pnp_precision prec, const float* x, int ny,
+                       int nx, int nimg, int blocks_y, int blocks_x, int halo, float* d,
+                       void* stream);
+
+/* One fused PnP-ULA x-update (Eq. 8) for nchain chains sharing y and h:
+ *   g = H^T r / sigma^2 (r = H x - y from pnp_blur, device [nchain][ny][nx]),
+ *   x <- x - gamma g + (alpha gamma/eps^2)(d - x) + (gamma/lambda)(clamp(x,0,1) - x)
+ *        + sqrt(2 gamma) xi,
+ * xi[n] standard normal from Philox4x32-10 with counter (n/4, t, chain, 0) and
+ * key (seed low, seed high), Box-Muller on word pairs. d: device [nchain][ny][nx]
+ * or NULL (no prior term). lambda <= 0 switches the projection term off;
+ * noise = 0 sets xi = 0. If n_kept > 0 the new x enters the FP32 Welford
+ * accumulators (mean, m2; device [nchain][ny][nx]) as sample number n_kept. */
+pnp_status pnp_langevin_update(float* x, const float* r, const float* d, const float* h,
+                               int kh, int kw, int ny, int nx, int nchain, double sigma,
+                               double alpha, double eps, double lambda, double gamma,
+                               uint64_t seed, uint32_t t, int noise, float* mean, float* m2,
+                               int64_t n_kept, void* stream);
+
+/* Final FP64 moments (Sec. III-C footnote): mmse = mean, var = m2 / (n - 1),
+ * out2 = var (want_var != 0) or sqrt(var). mean, m2: device FP32 [n];
+ * mmse, out2: device FP64 [n]. */
+pnp_status pnp_finalize_moments(const float* mean, const float* m2, int64_t npix,
+                                int64_t n_kept, int want_var, double* mmse, double* out2,
+                                void* stream);
+
+/* Step sizes of the Gaussian-noise setting (Eq. 10 with H_2 = 0):
+ * L = hnorm^2/sigma^2, lambda = 0.99 / (4L + 2 alpha L_eps / eps^2),
+ * gamma = c / (3 (L + alpha L_eps / eps^2 + 1/lambda)), 0 < c < 1. */
+pnp_status pnp_stepsizes(double hnorm, double sigma, double alpha, double eps, double lip_eps,
+                         double c, double* lambda, double* gamma);
+
+/* ------------------------------------------------------------------------
+ * Problem: one posterior (Eq. 2 with the Gaussian-deconvolution likelihood)
+ * and its chain state, resident on the device.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int ny, nx;                 /* image size, one channel                                  */
+    const float* y;             /* host [ny*nx]; copied                                     */
+    int kh, kw;                 /* blur size, odd                                           */
+    const float* h;             /* host [kh*kw]; copied; circular boundary                  */
+    double sigma;               /* noise std (> 0)                                          */
+    double alpha, eps;          /* prior weight, denoiser level; eps <= 0 -> eps = sigma,
+                                   alpha < 0 -> 1 (the paper's Gaussian setting)           */
+    double lambda, gamma;       /* <= 0 -> derived by pnp_stepsizes with c = step_c        */
+    double step_c;              /* <= 0 -> 0.99                                             */
+    double hnorm;               /* ||H||_2; <= 0 -> sum |h| (exact for h >= 0)              */
+    int blocks_y, blocks_x;     /* block split (>= 1)                                       */
+    int halo;                   /* 0: direct whole-image layers; > 0: block + halo (>= K)  */
+    int nchain;                 /* chains sharing y, h (>= 1)                               */
+    uint64_t seed;              /* Philox key                                               */
+    int burn_in;                /* samples x^(t) with t > burn_in enter the moments         */
+    pnp_precision precision;    /* denoiser arithmetic                                      */
+    const pnp_denoiser* D;      /* NULL: no prior term                                      */
+    const float* x0;            /* host [nchain][ny*nx] or NULL (zeros)                     */
+    void* stream;               /* stream for all work of this problem (NULL: own stream)  */
+} pnp_problem_desc;
+
+pnp_status pnp_create_problem(const pnp_problem_desc* desc, pnp_problem** out);
+void pnp_destroy_problem(pnp_problem* p);
+/* Derived parameters actually used (host). Any pointer may be NULL. */
+pnp_status pnp_problem_params(const pnp_problem* p, double* lambda, double* gamma,
+                              double* alpha, double* eps);
+/* Enqueue n_iters iterations (asynchronous on the problem's stream). Uses a
+ * captured CUDA graph of one iteration when use_graph != 0. */
+pnp_status pnp_step(pnp_problem* p, int n_iters);
+/* Run T iterations with the given burn-in (resets nothing) and wait. */
+pnp_status pnp_run_chain(pnp_problem* p, int T, int burn_in);
+/* Wait for the problem's stream. */
+pnp_status pnp_sync(pnp_problem* p);
+/* FP64 MMSE and std (want_var = 0) or variance for chain `chain`; host
+ * buffers [ny*nx]; n_kept may be NULL. Synchronous. */
+pnp_status pnp_get_moments(pnp_problem* p, int chain, double* mmse, double* std_or_var,
+                           int64_t* n_kept, int want_var);
+/* Chain state: x host [nchain][ny*nx], t = iterations done. Synchronous. */
+pnp_status pnp_get_state(pnp_problem* p, float* x, int64_t* t);
+pnp_status pnp_set_state(pnp_problem* p, const float* x, int64_t t);
+/* Device pointer of the chain state x [nchain][ny][nx] (valid until destroy). */
+float* pnp_problem_x_device(pnp_problem* p);
+/* Replay one captured CUDA graph per iteration (default on) or launch eagerly. */
+pnp_status pnp_set_graph_mode(int enable);
+
+/* ------------------------------------------------------------------------
+ * Instrumentation: CUDA events around every launch of the hot kernels
+ * ("blur", "update", "conv_fp32", "conv_tc", "conv_edge"). Enabling resets
+ * the counters and forces eager launches (no graph replay). Reading
+ * synchronizes the device and returns the summed device time and launches.
+ * ------------------------------------------------------------------------ */
+pnp_status pnp_kernel_timer(int enable);
+pnp_status pnp_kernel_timer_read(const char* name, double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PNP_H */

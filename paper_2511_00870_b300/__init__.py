@@ -1,0 +1,226 @@
+"""B300 (sm_103a) PnP-ULA sampler for Gaussian deconvolution.
+
+Python binding of the C ABI in ``include/pnp.h``: the functions here only
+marshal arguments (numpy arrays on the host, torch CUDA tensors on the device,
+torch's current stream) into ``libpnp.so``; every step of the sampler runs in
+that library's CUDA kernels. There is no CPU fallback: importing the
+low-level functions loads the library and fails loudly if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from ._lib import (PNP_BF16, PNP_FP8, PNP_FP32, PnpError, ProblemDesc, check, load)  # noqa: F401
+
+__all__ = ["Denoiser", "Problem", "PnpError", "load", "version"]
+
+PRECISIONS = {"fp32": PNP_FP32, "bf16": PNP_BF16, "fp8": PNP_FP8}
+
+
+def _prec(p):
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _ptr(t):
+    if t is None:
+        return C.c_void_p(0)
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _f32p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def version() -> str:
+    return load().pnp_version().decode()
+
+
+# ------------------------------------------------------------------ operators
+
+def pnp_blur(x, y, h, r, stream=None):
+    """r = h (*) x - y (circular); x, r: [n, ny, nx] CUDA float32; y: [ny, nx] or None."""
+    n, ny, nx = x.shape
+    check(load().pnp_blur(_ptr(x), _ptr(y), _ptr(h), h.shape[0], h.shape[1], ny, nx, n, _ptr(r),
+                          _stream(stream)))
+    return r
+
+
+def pnp_blur_adjoint(r, h, g, scale=1.0, stream=None):
+    n, ny, nx = r.shape
+    check(load().pnp_blur_adjoint(_ptr(r), _ptr(h), h.shape[0], h.shape[1], ny, nx, n,
+                                  float(scale), _ptr(g), _stream(stream)))
+    return g
+
+
+def pnp_langevin_update(x, r, d, h, sigma, alpha, eps, lam, gamma, seed, t, noise=True,
+                        mean=None, m2=None, n_kept=0, stream=None):
+    n, ny, nx = x.shape
+    check(load().pnp_langevin_update(_ptr(x), _ptr(r), _ptr(d), _ptr(h), h.shape[0], h.shape[1],
+                                     ny, nx, n, sigma, alpha, eps, lam, gamma, int(seed), int(t),
+                                     int(bool(noise)), _ptr(mean), _ptr(m2), int(n_kept),
+                                     _stream(stream)))
+    return x
+
+
+def pnp_finalize_moments(mean, m2, n_kept, mmse, out2, want_var=False, stream=None):
+    check(load().pnp_finalize_moments(_ptr(mean), _ptr(m2), mean.numel(), int(n_kept),
+                                      int(bool(want_var)), _ptr(mmse), _ptr(out2),
+                                      _stream(stream)))
+    return mmse, out2
+
+
+def pnp_stepsizes(hnorm, sigma, alpha, eps, lip_eps, c=0.99):
+    lam, gam = C.c_double(), C.c_double()
+    check(load().pnp_stepsizes(hnorm, sigma, alpha, eps, lip_eps, c, C.byref(lam), C.byref(gam)))
+    return lam.value, gam.value
+
+
+def pnp_set_graph_mode(enable: bool):
+    check(load().pnp_set_graph_mode(int(bool(enable))))
+
+
+def pnp_kernel_timer(enable: bool):
+    check(load().pnp_kernel_timer(int(bool(enable))))
+
+
+def pnp_kernel_timer_read(name: str):
+    """-> (total device ms, launches) of the named kernel since the timer was enabled."""
+    ms, n = C.c_double(), C.c_int64()
+    check(load().pnp_kernel_timer_read(name.encode(), C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+# ------------------------------------------------------------------ denoiser
+
+class Denoiser:
+    """DnCNN-form denoiser D = Id - G owned by the library (pnp_create_denoiser)."""
+
+    def __init__(self, weights, biases, lipschitz: float):
+        """weights: list of K arrays [cout, cin, 3, 3]; biases: list of K arrays [cout]."""
+        self.K = len(weights)
+        self.F = int(weights[0].shape[0])
+        w = np.ascontiguousarray(np.concatenate([np.asarray(a, np.float32).ravel() for a in weights]))
+        b = np.ascontiguousarray(np.concatenate([np.asarray(a, np.float32).ravel() for a in biases]))
+        h = C.c_void_p()
+        check(load().pnp_create_denoiser(self.K, self.F, _f32p(w), _f32p(b), float(lipschitz),
+                                         C.byref(h)))
+        self.handle = h
+        self.lipschitz = float(lipschitz)
+
+    @classmethod
+    def from_weights(cls, dw):
+        return cls(dw.weights, dw.biases, dw.lipschitz)
+
+    def denoise(self, x, out=None, precision="fp32", blocks=(1, 1), halo=0, stream=None):
+        """pnp_denoise on x [n, ny, nx] (CUDA float32)."""
+        import torch
+        n, ny, nx = x.shape
+        out = torch.empty_like(x) if out is None else out
+        check(load().pnp_denoise(self.handle, _prec(precision), _ptr(x), ny, nx, n, blocks[0],
+                                 blocks[1], halo, _ptr(out), _stream(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pnp_destroy_denoiser(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ problem
+
+class Problem:
+    """One posterior and its chains resident on the GPU (pnp_create_problem)."""
+
+    def __init__(self, y, h, sigma, denoiser: Denoiser | None = None, *, alpha=-1.0, eps=0.0,
+                 lam=0.0, gamma=0.0, step_c=0.0, hnorm=0.0, blocks=(1, 1), halo=0, nchain=1,
+                 seed=0, burn_in=0, precision="fp32", x0=None, stream=None):
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        h = np.ascontiguousarray(h, dtype=np.float32)
+        self.shape = y.shape
+        self.nchain = nchain
+        d = ProblemDesc()
+        d.ny, d.nx = y.shape
+        d.y = _f32p(y)
+        d.kh, d.kw = h.shape
+        d.h = _f32p(h)
+        d.sigma, d.alpha, d.eps = float(sigma), float(alpha), float(eps)
+        d.lam, d.gamma, d.step_c, d.hnorm = float(lam), float(gamma), float(step_c), float(hnorm)
+        d.blocks_y, d.blocks_x = int(blocks[0]), int(blocks[1])
+        d.halo, d.nchain, d.seed, d.burn_in = int(halo), int(nchain), int(seed), int(burn_in)
+        d.precision = _prec(precision)
+        d.D = denoiser.handle if denoiser is not None else None
+        x0a = None
+        if x0 is not None:
+            x0a = np.ascontiguousarray(np.broadcast_to(x0, (nchain,) + y.shape), dtype=np.float32)
+            d.x0 = _f32p(x0a)
+        d.stream = C.c_void_p(int(stream)) if stream is not None else None
+        hdl = C.c_void_p()
+        check(load().pnp_create_problem(C.byref(d), C.byref(hdl)))
+        self.handle = hdl
+        self._denoiser = denoiser   # keep alive
+
+    def params(self):
+        lam, gam, al, ep = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+        check(load().pnp_problem_params(self.handle, C.byref(lam), C.byref(gam), C.byref(al),
+                                        C.byref(ep)))
+        return dict(lam=lam.value, gamma=gam.value, alpha=al.value, eps=ep.value)
+
+    def step(self, n=1):
+        check(load().pnp_step(self.handle, int(n)))
+
+    def sync(self):
+        check(load().pnp_sync(self.handle))
+
+    def run_chain(self, T, burn_in):
+        check(load().pnp_run_chain(self.handle, int(T), int(burn_in)))
+
+    def moments(self, chain=0, want_var=False):
+        ny, nx = self.shape
+        mm = np.empty((ny, nx), np.float64)
+        o2 = np.empty((ny, nx), np.float64)
+        n = C.c_int64()
+        check(load().pnp_get_moments(self.handle, chain, mm.ctypes.data_as(C.POINTER(C.c_double)),
+                                     o2.ctypes.data_as(C.POINTER(C.c_double)), C.byref(n),
+                                     int(bool(want_var))))
+        return mm, o2, n.value
+
+    def state(self):
+        x = np.empty((self.nchain,) + self.shape, np.float32)
+        t = C.c_int64()
+        check(load().pnp_get_state(self.handle, _f32p(x), C.byref(t)))
+        return x, t.value
+
+    def set_state(self, x, t):
+        x = np.ascontiguousarray(np.broadcast_to(x, (self.nchain,) + self.shape), dtype=np.float32)
+        check(load().pnp_set_state(self.handle, _f32p(x), int(t)))
+
+    def x_device_ptr(self):
+        return load().pnp_problem_x_device(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pnp_destroy_problem(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

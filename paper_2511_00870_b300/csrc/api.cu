@@ -1,0 +1,794 @@
+// C ABI of libpnp: argument checking, device buffers, step scheduling and
+// CUDA-graph replay around the kernels of k_stencil.cu, k_conv_simt.cu and
+// k_conv_tc.cu. Every compute step runs on the GPU; the host only validates,
+// allocates, derives the step sizes (Eq. 10) and enqueues work.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pnp_internal.h"
+
+namespace pnp {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+pnp_status fail(pnp_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+pnp_status cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PNP_ENOMEM : PNP_ECUDA;
+}
+
+int num_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = n > 0 ? n : 1;
+    }
+    return cached[dev];
+}
+
+// ------------------------------------------------------------ kernel timer
+struct TimerSlot {
+    std::vector<cudaEvent_t> begin, end;
+    size_t used = 0;
+};
+static TimerSlot g_timers[T_COUNT];
+static bool g_timing = false;
+static const char* g_timer_names[T_COUNT] = {"blur", "update", "conv_fp32", "conv_tc", "conv_edge"};
+
+bool timer_enabled() { return g_timing; }
+void timer_begin(int id, cudaStream_t s) {
+    if (!g_timing) return;
+    TimerSlot& t = g_timers[id];
+    if (t.used == t.begin.size()) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        t.begin.push_back(a);
+        t.end.push_back(b);
+    }
+    cudaEventRecord(t.begin[t.used], s);
+}
+void timer_end(int id, cudaStream_t s) {
+    if (!g_timing) return;
+    TimerSlot& t = g_timers[id];
+    cudaEventRecord(t.end[t.used], s);
+    ++t.used;
+}
+
+cudaError_t conv_tc_layer(const __nv_bfloat16* in, const __nv_bfloat16* wblob, const float* bias,
+                          int ny, int nx, int nimg, const Rect* rects, __nv_bfloat16* out,
+                          int* err, cudaStream_t s);
+
+// Step counter read by the update kernel during graph replay.
+struct StepState {
+    uint32_t t;
+    int32_t burn_in;
+};
+
+__global__ void k_advance(StepState* st) { st->t += 1; }
+
+}  // namespace pnp
+
+using namespace pnp;
+
+struct pnp_problem {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int ny = 0, nx = 0, nchain = 1, kh = 0, kw = 0;
+    int64_t N = 0;
+    float* y = nullptr;
+    float* h = nullptr;
+    float* x = nullptr;
+    float* r = nullptr;
+    float* d = nullptr;
+    float* mean = nullptr;
+    float* m2 = nullptr;
+    double sigma = 0, alpha = 0, eps = 0, lambda = 0, gamma = 0, hnorm = 0;
+    uint64_t seed = 0;
+    int burn_in = 0;
+    pnp_precision prec = PNP_FP32;
+    const pnp_denoiser* D = nullptr;
+    int by = 1, bx = 1, halo = 0;
+    // block + halo mode
+    BlockDesc* blocks = nullptr;
+    int nblocks = 0, ty = 0, tx = 0;
+    float* tiles = nullptr;
+    float* dtiles = nullptr;
+    Rect* rects = nullptr;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    StepState* st = nullptr;
+    int64_t t = 0;
+    cudaGraphExec_t graph = nullptr;
+};
+
+// ------------------------------------------------------------------ helpers
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static pnp_status dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return PNP_OK;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(PNP_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    return PNP_OK;
+}
+
+static void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+static uint16_t f32_to_bf16_rne(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16 | ((u & 0xffff) ? 0x40 : 0));
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    return (uint16_t)(u >> 16);
+}
+
+// ------------------------------------------------------------------ misc API
+
+extern "C" const char* pnp_last_error(void) { return g_err.c_str(); }
+extern "C" const char* pnp_version(void) { return "pnp-b300 0.1 (sm_103a)"; }
+
+extern "C" pnp_status pnp_stepsizes(double hnorm, double sigma, double alpha, double eps,
+                                    double lip_eps, double c, double* lambda, double* gamma) {
+    if (!(hnorm > 0) || !(sigma > 0) || !(eps > 0) || alpha < 0 || lip_eps < 0 || !(c > 0) ||
+        !(c < 1) || !lambda || !gamma)
+        return fail(PNP_EINVAL, "pnp_stepsizes: need hnorm, sigma, eps > 0, alpha, L_eps >= 0, 0 < c < 1");
+    const double L = hnorm * hnorm / (sigma * sigma);
+    const double prior = alpha * lip_eps / (eps * eps);
+    const double lam = 0.99 / (4.0 * L + 2.0 * prior);
+    *lambda = lam;
+    *gamma = c / (3.0 * (L + prior + 1.0 / lam));
+    return PNP_OK;
+}
+
+// ------------------------------------------------------------------ denoiser
+
+extern "C" pnp_status pnp_create_denoiser(int K, int F, const float* weights, const float* biases,
+                                          double lipschitz_eps, pnp_denoiser** out) {
+    if (!out) return fail(PNP_EINVAL, "pnp_create_denoiser: out is NULL");
+    *out = nullptr;
+    if (K < 2 || !(F == 16 || F == 32 || F == 64) || !weights || !biases || !(lipschitz_eps >= 0))
+        return fail(PNP_EINVAL, "pnp_create_denoiser: need K >= 2, F in {16,32,64}, weights, biases");
+    pnp_denoiser* den = new pnp_denoiser();
+    DenoiserDev& D = den->dev;
+    D.K = K;
+    D.F = F;
+    D.lip = lipschitz_eps;
+    cudaGetDevice(&den->device);
+    std::vector<int> cin(K), cout(K);
+    for (int k = 0; k < K; ++k) {
+        cin[k] = k == 0 ? 1 : F;
+        cout[k] = k == K - 1 ? 1 : F;
+    }
+    D.w32_off = new int64_t[K];
+    D.b_off = new int64_t[K];
+    int64_t nw = 0, nb = 0, wsrc = 0;
+    std::vector<int64_t> src_off(K);
+    for (int k = 0; k < K; ++k) {
+        D.w32_off[k] = nw;
+        D.b_off[k] = nb;
+        src_off[k] = wsrc;
+        const int64_t sz = (int64_t)cin[k] * 9 * cout[k];
+        wsrc += sz;
+        nw += (sz + 3) & ~(int64_t)3;
+        nb += (cout[k] + 3) & ~3;
+    }
+    // FP32 [cin][9][cout] per layer
+    std::vector<float> w32(nw, 0.f), b32(nb, 0.f);
+    int64_t bsrc = 0;
+    for (int k = 0; k < K; ++k) {
+        const float* W = weights + src_off[k];
+        for (int co = 0; co < cout[k]; ++co)
+            for (int ci = 0; ci < cin[k]; ++ci)
+                for (int t = 0; t < 9; ++t)
+                    w32[D.w32_off[k] + ((int64_t)ci * 9 + t) * cout[k] + co] =
+                        W[((int64_t)co * cin[k] + ci) * 9 + t];
+        for (int co = 0; co < cout[k]; ++co) b32[D.b_off[k] + co] = biases[bsrc + co];
+        bsrc += cout[k];
+    }
+    pnp_status st = PNP_OK;
+    if ((st = dalloc(&D.w32, nw)) != PNP_OK || (st = dalloc(&D.b32, nb)) != PNP_OK) {
+        pnp_destroy_denoiser(den);
+        return st;
+    }
+    cudaMemcpy(D.w32, w32.data(), nw * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(D.b32, b32.data(), nb * 4, cudaMemcpyHostToDevice);
+    D.hw = new float[wsrc];
+    D.hb = new float[bsrc];
+    memcpy(D.hw, weights, wsrc * 4);
+    memcpy(D.hb, biases, bsrc * 4);
+    if (F == 64) {
+        // tensor-core blobs of the F -> F layers: [tap][cg][co][8 ci] BF16
+        const int nmid = K - 2;
+        std::vector<uint16_t> blob((size_t)std::max(nmid, 1) * 9 * 8 * 64 * 8, 0);
+        for (int m = 0; m < nmid; ++m) {
+            const float* W = weights + src_off[m + 1];
+            for (int t = 0; t < 9; ++t)
+                for (int cg = 0; cg < 8; ++cg)
+                    for (int co = 0; co < 64; ++co)
+                        for (int c8 = 0; c8 < 8; ++c8)
+                            blob[((((size_t)m * 9 + t) * 8 + cg) * 64 + co) * 8 + c8] =
+                                f32_to_bf16_rne(W[((int64_t)co * 64 + cg * 8 + c8) * 9 + t]);
+        }
+        std::vector<float> wf(9 * 64), wl(9 * 64);
+        for (int t = 0; t < 9; ++t)
+            for (int c = 0; c < 64; ++c) {
+                wf[t * 64 + c] = weights[src_off[0] + (int64_t)c * 9 + t];
+                wl[t * 64 + c] = weights[src_off[K - 1] + (int64_t)c * 9 + t];
+            }
+        if ((st = dalloc(&D.wtc, blob.size())) != PNP_OK || (st = dalloc(&D.wfirst, 9 * 64)) != PNP_OK ||
+            (st = dalloc(&D.wlast, 9 * 64)) != PNP_OK) {
+            pnp_destroy_denoiser(den);
+            return st;
+        }
+        cudaMemcpy(D.wtc, blob.data(), blob.size() * 2, cudaMemcpyHostToDevice);
+        cudaMemcpy(D.wfirst, wf.data(), wf.size() * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(D.wlast, wl.data(), wl.size() * 4, cudaMemcpyHostToDevice);
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        pnp_destroy_denoiser(den);
+        return cuda_fail(e, "pnp_create_denoiser");
+    }
+    *out = den;
+    return PNP_OK;
+}
+
+extern "C" void pnp_destroy_denoiser(pnp_denoiser* den) {
+    if (!den) return;
+    DenoiserDev& D = den->dev;
+    dfree(D.w32);
+    dfree(D.b32);
+    dfree(D.wtc);
+    dfree(D.wfirst);
+    dfree(D.wlast);
+    dfree(den->scratch);
+    delete[] D.w32_off;
+    delete[] D.b_off;
+    delete[] D.hw;
+    delete[] D.hb;
+    delete den;
+}
+
+// ------------------------------------------------------------------ operators
+
+static pnp_status check_blur_args(const void* x, const void* h, int kh, int kw, int ny, int nx,
+                                  int nimg, const void* out, const char* who) {
+    if (!x || !h || !out) return fail(PNP_EINVAL, std::string(who) + ": NULL pointer");
+    if (ny < 1 || nx < 1 || nimg < 1) return fail(PNP_EINVAL, std::string(who) + ": empty image");
+    if (kh < 1 || kw < 1 || !(kh & 1) || !(kw & 1) || kh > 31 || kw > 31)
+        return fail(PNP_EINVAL, std::string(who) + ": kernel sizes must be odd and <= 31");
+    if (kh > ny || kw > nx)
+        return fail(PNP_EINVAL, std::string(who) + ": kernel larger than the image");
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_blur(const float* x, const float* y, const float* h, int kh, int kw,
+                               int ny, int nx, int nimg, float* r, void* stream) {
+    PNP_TRY(check_blur_args(x, h, kh, kw, ny, nx, nimg, r, "pnp_blur"));
+    PNP_CUDA_TRY(launch_blur(x, y, h, kh, kw, ny, nx, nimg, r, (cudaStream_t)stream));
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_blur_adjoint(const float* r, const float* h, int kh, int kw, int ny,
+                                       int nx, int nimg, float scale, float* g, void* stream) {
+    PNP_TRY(check_blur_args(r, h, kh, kw, ny, nx, nimg, g, "pnp_blur_adjoint"));
+    PNP_CUDA_TRY(launch_blur_adjoint(r, h, kh, kw, ny, nx, nimg, scale, g, (cudaStream_t)stream));
+    return PNP_OK;
+}
+
+// block table for the block + halo mode (floor rule per axis, Eq. 7)
+static std::vector<BlockDesc> make_blocks(int ny, int nx, int by, int bx, int nimg, int* maxh,
+                                          int* maxw) {
+    std::vector<BlockDesc> v;
+    *maxh = *maxw = 0;
+    for (int img = 0; img < nimg; ++img)
+        for (int i = 0; i < by; ++i)
+            for (int j = 0; j < bx; ++j) {
+                BlockDesc b;
+                b.img = img;
+                b.r0 = (int)((int64_t)i * ny / by);
+                b.r1 = (int)((int64_t)(i + 1) * ny / by);
+                b.c0 = (int)((int64_t)j * nx / bx);
+                b.c1 = (int)((int64_t)(j + 1) * nx / bx);
+                *maxh = std::max(*maxh, b.r1 - b.r0);
+                *maxw = std::max(*maxw, b.c1 - b.c0);
+                v.push_back(b);
+            }
+    return v;
+}
+
+static size_t denoise_scratch_bytes(const DenoiserDev& D, pnp_precision prec, int ny, int nx,
+                                    int nimg) {
+    return prec == PNP_FP32 ? denoise_fp32_scratch(D, ny, nx, nimg)
+                            : denoise_bf16_scratch(D, ny, nx, nimg);
+}
+
+static cudaError_t run_denoise(const DenoiserDev& D, pnp_precision prec, const float* x, int ny,
+                               int nx, int nimg, const Rect* rects, float* d, void* scratch,
+                               cudaStream_t s) {
+    if (prec == PNP_FP32) return denoise_fp32(D, x, ny, nx, nimg, rects, d, (float*)scratch, s);
+    return denoise_bf16(D, x, ny, nx, nimg, rects, d, scratch, s);
+}
+
+static pnp_status check_denoise_args(const pnp_denoiser* den, pnp_precision prec, int ny, int nx,
+                                     int nimg, int by, int bx, int halo) {
+    if (!den) return fail(PNP_EINVAL, "denoiser is NULL");
+    if (ny < 1 || nx < 1 || nimg < 1) return fail(PNP_EINVAL, "empty image");
+    if (prec != PNP_FP32 && prec != PNP_BF16)
+        return fail(PNP_ENOTSUP, "precision not supported by this build");
+    if (prec == PNP_BF16 && den->dev.F != 64) return fail(PNP_EINVAL, "BF16 path needs F = 64");
+    if (halo < 0) return fail(PNP_EINVAL, "halo must be >= 0");
+    if (halo > 0 && (by < 1 || bx < 1 || by > ny || bx > nx))
+        return fail(PNP_EINVAL, "blocks must be >= 1 and <= the image size");
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_denoise(const pnp_denoiser* den, pnp_precision prec, const float* x,
+                                  int ny, int nx, int nimg, int blocks_y, int blocks_x, int halo,
+                                  float* d, void* stream) {
+    PNP_TRY(check_denoise_args(den, prec, ny, nx, nimg, blocks_y, blocks_x, halo));
+    if (!x || !d) return fail(PNP_EINVAL, "pnp_denoise: NULL pointer");
+    pnp_denoiser* dn = const_cast<pnp_denoiser*>(den);
+    const DenoiserDev& D = den->dev;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (halo == 0) {
+        const size_t need = denoise_scratch_bytes(D, prec, ny, nx, nimg);
+        if (dn->scratch_bytes < need) {
+            PNP_CUDA_TRY(cudaStreamSynchronize(s));
+            dfree(dn->scratch);
+            dn->scratch = nullptr;
+            dn->scratch_bytes = 0;
+            PNP_TRY(dalloc((uint8_t**)&dn->scratch, need));
+            PNP_CUDA_TRY(cudaMemset(dn->scratch, 0, need));
+            dn->scratch_bytes = need;
+        }
+        PNP_CUDA_TRY(run_denoise(D, prec, x, ny, nx, nimg, nullptr, d, dn->scratch, s));
+        return PNP_OK;
+    }
+    // block + halo: gather extended blocks, run the network per tile, scatter interiors
+    int mh, mw;
+    std::vector<BlockDesc> bl = make_blocks(ny, nx, blocks_y, blocks_x, nimg, &mh, &mw);
+    const int ty = mh + 2 * halo, tx = mw + 2 * halo, nb = (int)bl.size();
+    const size_t tile_floats = (size_t)nb * ty * tx;
+    const size_t need_net = denoise_scratch_bytes(D, prec, ty, tx, nb);
+    const size_t need = need_net + 2 * tile_floats * 4 + nb * sizeof(Rect) + nb * sizeof(BlockDesc) + 1024;
+    PNP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (dn->scratch_bytes < need) {
+        dfree(dn->scratch);
+        dn->scratch = nullptr;
+        dn->scratch_bytes = 0;
+        PNP_TRY(dalloc((uint8_t**)&dn->scratch, need));
+        PNP_CUDA_TRY(cudaMemset(dn->scratch, 0, need));
+        dn->scratch_bytes = need;
+    }
+    uint8_t* p = (uint8_t*)dn->scratch;
+    void* net_scratch = p;
+    p += (need_net + 255) & ~(size_t)255;
+    float* tiles = (float*)p;
+    p += tile_floats * 4;
+    float* dtiles = (float*)p;
+    p += tile_floats * 4;
+    Rect* rects = (Rect*)p;
+    p += nb * sizeof(Rect);
+    BlockDesc* blocks = (BlockDesc*)p;
+    PNP_CUDA_TRY(cudaMemcpyAsync(blocks, bl.data(), nb * sizeof(BlockDesc), cudaMemcpyHostToDevice, s));
+    PNP_CUDA_TRY(launch_gather_blocks(x, ny, nx, blocks, nb, halo, ty, tx, tiles, rects, s));
+    PNP_CUDA_TRY(run_denoise(D, prec, tiles, ty, tx, nb, rects, dtiles, net_scratch, s));
+    PNP_CUDA_TRY(launch_scatter_blocks(dtiles, ny, nx, blocks, nb, halo, ty, tx, d, s));
+    PNP_CUDA_TRY(cudaStreamSynchronize(s));   // the host block table must outlive the copy
+    return PNP_OK;
+}
+
+static pnp_status fill_update_params(UpdateParams& u, float* x, const float* r, const float* d,
+                                     const float* h, int kh, int kw, int ny, int nx, int nchain,
+                                     double sigma, double alpha, double eps, double lambda,
+                                     double gamma, uint64_t seed, int noise) {
+    if (!(sigma > 0) || !(gamma > 0)) return fail(PNP_EINVAL, "sigma and gamma must be > 0");
+    if (d && !(eps > 0)) return fail(PNP_EINVAL, "eps must be > 0 with a prior term");
+    u.x = x;
+    u.r = r;
+    u.d = d;
+    u.h = h;
+    u.kh = kh;
+    u.kw = kw;
+    u.ny = ny;
+    u.nx = nx;
+    u.nchain = nchain;
+    u.inv_s2 = (float)(1.0 / (sigma * sigma));
+    u.gamma = (float)gamma;
+    u.c_prior = d ? (float)(alpha * gamma / (eps * eps)) : 0.f;
+    u.c_proj = lambda > 0 ? (float)(gamma / lambda) : 0.f;
+    u.c_noise = noise ? (float)std::sqrt(2.0 * gamma) : 0.f;
+    u.key0 = (uint32_t)(seed & 0xffffffffu);
+    u.key1 = (uint32_t)(seed >> 32);
+    u.t = 0;
+    u.t_dev = nullptr;
+    u.mean = nullptr;
+    u.m2 = nullptr;
+    u.inv_n = 0.f;
+    u.burn_dev = nullptr;
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_langevin_update(float* x, const float* r, const float* d, const float* h,
+                                          int kh, int kw, int ny, int nx, int nchain, double sigma,
+                                          double alpha, double eps, double lambda, double gamma,
+                                          uint64_t seed, uint32_t t, int noise, float* mean,
+                                          float* m2, int64_t n_kept, void* stream) {
+    PNP_TRY(check_blur_args(x, h, kh, kw, ny, nx, nchain, r, "pnp_langevin_update"));
+    if (n_kept > 0 && (!mean || !m2)) return fail(PNP_EINVAL, "moments requested without buffers");
+    UpdateParams u;
+    PNP_TRY(fill_update_params(u, x, r, d, h, kh, kw, ny, nx, nchain, sigma, alpha, eps, lambda,
+                               gamma, seed, noise));
+    u.t = t;
+    u.mean = mean;
+    u.m2 = m2;
+    u.inv_n = n_kept > 0 ? (float)(1.0 / (double)n_kept) : 0.f;
+    PNP_CUDA_TRY(launch_langevin_update(u, (cudaStream_t)stream));
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_finalize_moments(const float* mean, const float* m2, int64_t npix,
+                                           int64_t n_kept, int want_var, double* mmse,
+                                           double* out2, void* stream) {
+    if (!mean || !m2 || !mmse || !out2 || npix < 1)
+        return fail(PNP_EINVAL, "pnp_finalize_moments: bad arguments");
+    PNP_CUDA_TRY(launch_finalize_moments(mean, m2, npix, n_kept, want_var, mmse, out2,
+                                         (cudaStream_t)stream));
+    return PNP_OK;
+}
+
+// ------------------------------------------------------------------ problem
+
+extern "C" void pnp_destroy_problem(pnp_problem* p) {
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    for (void* q : {(void*)p->y, (void*)p->h, (void*)p->x, (void*)p->r, (void*)p->d,
+                    (void*)p->mean, (void*)p->m2, (void*)p->blocks, (void*)p->tiles,
+                    (void*)p->dtiles, (void*)p->rects, p->scratch, (void*)p->st})
+        dfree(q);
+    if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+    delete p;
+}
+
+static pnp_status enqueue_iteration(pnp_problem* p) {
+    cudaStream_t s = p->stream;
+    PNP_CUDA_TRY(launch_blur(p->x, p->y, p->h, p->kh, p->kw, p->ny, p->nx, p->nchain, p->r, s));
+    const bool prior = p->D && p->alpha != 0.0;
+    if (prior) {
+        const DenoiserDev& D = p->D->dev;
+        if (p->halo == 0) {
+            PNP_CUDA_TRY(run_denoise(D, p->prec, p->x, p->ny, p->nx, p->nchain, nullptr, p->d,
+                                     p->scratch, s));
+        } else {
+            PNP_CUDA_TRY(launch_gather_blocks(p->x, p->ny, p->nx, p->blocks, p->nblocks, p->halo,
+                                              p->ty, p->tx, p->tiles, p->rects, s));
+            PNP_CUDA_TRY(run_denoise(D, p->prec, p->tiles, p->ty, p->tx, p->nblocks, p->rects,
+                                     p->dtiles, p->scratch, s));
+            PNP_CUDA_TRY(launch_scatter_blocks(p->dtiles, p->ny, p->nx, p->blocks, p->nblocks,
+                                               p->halo, p->ty, p->tx, p->d, s));
+        }
+    }
+    UpdateParams u;
+    PNP_TRY(fill_update_params(u, p->x, p->r, prior ? p->d : nullptr, p->h, p->kh, p->kw, p->ny,
+                               p->nx, p->nchain, p->sigma, p->alpha, p->eps, p->lambda, p->gamma,
+                               p->seed, 1));
+    u.t_dev = &p->st->t;
+    u.burn_dev = &p->st->burn_in;
+    u.mean = p->mean;
+    u.m2 = p->m2;
+    PNP_CUDA_TRY(launch_langevin_update(u, s));
+    k_advance<<<1, 1, 0, s>>>(p->st);
+    PNP_CUDA_TRY(cudaGetLastError());
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_problem** out) {
+    if (!dsc || !out) return fail(PNP_EINVAL, "pnp_create_problem: NULL argument");
+    *out = nullptr;
+    const pnp_problem_desc& q = *dsc;
+    if (q.ny < 1 || q.nx < 1 || !q.y || !q.h) return fail(PNP_EINVAL, "need ny, nx >= 1, y and h");
+    PNP_TRY(check_blur_args(q.y, q.h, q.kh, q.kw, q.ny, q.nx, 1, q.y, "pnp_create_problem"));
+    if (!(q.sigma > 0) || !std::isfinite(q.sigma)) return fail(PNP_EINVAL, "sigma must be > 0");
+    if (q.nchain < 1) return fail(PNP_EINVAL, "nchain must be >= 1");
+    if (q.blocks_y < 1 || q.blocks_x < 1 || q.blocks_y > q.ny || q.blocks_x > q.nx)
+        return fail(PNP_EINVAL, "blocks must be in [1, image size]");
+    if (q.halo < 0) return fail(PNP_EINVAL, "halo must be >= 0");
+    if (q.D && q.halo > 0 && q.halo < q.D->dev.K)
+        return fail(PNP_EINVAL, "halo must cover the receptive field (halo >= K)");
+    if (q.precision != PNP_FP32 && q.precision != PNP_BF16)
+        return fail(PNP_ENOTSUP, "precision not supported by this build");
+    if (q.D && q.precision == PNP_BF16 && q.D->dev.F != 64)
+        return fail(PNP_EINVAL, "BF16 denoiser needs F = 64");
+    const int64_t N = (int64_t)q.ny * q.nx;
+    for (int64_t i = 0; i < N; ++i)
+        if (!std::isfinite(q.y[i])) return fail(PNP_EINVAL, "y contains NaN or Inf");
+    double hsum = 0.0;
+    for (int i = 0; i < q.kh * q.kw; ++i) {
+        if (!std::isfinite(q.h[i])) return fail(PNP_EINVAL, "h contains NaN or Inf");
+        hsum += std::fabs(q.h[i]);
+    }
+    pnp_problem* p = new pnp_problem();
+    cudaGetDevice(&p->device);
+    p->ny = q.ny;
+    p->nx = q.nx;
+    p->N = N;
+    p->nchain = q.nchain;
+    p->kh = q.kh;
+    p->kw = q.kw;
+    p->sigma = q.sigma;
+    p->alpha = q.alpha < 0 ? 1.0 : q.alpha;
+    p->eps = q.eps > 0 ? q.eps : q.sigma;
+    p->hnorm = q.hnorm > 0 ? q.hnorm : hsum;
+    p->seed = q.seed;
+    p->burn_in = q.burn_in;
+    p->prec = q.precision;
+    p->D = q.D;
+    p->by = q.blocks_y;
+    p->bx = q.blocks_x;
+    p->halo = q.halo;
+    const double lip = q.D ? q.D->dev.lip : 0.0;
+    const double alpha_eff = q.D ? p->alpha : 0.0;
+    double lam = q.lambda, gam = q.gamma;
+    if (!(lam > 0) || !(gam > 0)) {
+        double l2, g2;
+        pnp_status st = pnp_stepsizes(p->hnorm, p->sigma, alpha_eff, p->eps, lip,
+                                      q.step_c > 0 ? q.step_c : 0.99, &l2, &g2);
+        if (st != PNP_OK) {
+            delete p;
+            return st;
+        }
+        if (!(lam > 0)) lam = l2;
+        if (!(gam > 0)) gam = g2;
+    }
+    p->lambda = lam;
+    p->gamma = gam;
+    // Eq. 10 (with H_2 = 0) must hold for the parameters actually used
+    {
+        const double L = p->hnorm * p->hnorm / (p->sigma * p->sigma);
+        const double prior = alpha_eff * lip / (p->eps * p->eps);
+        if (!(3.0 * gam * (L + 1.0 / lam + prior) < 1.0) || !(2.0 * L + prior <= 0.5 / lam * (1 + 1e-12))) {
+            delete p;
+            return fail(PNP_EINVAL, "step sizes violate the conditions of Eq. 10");
+        }
+    }
+    pnp_status st = PNP_OK;
+#define ALLOC(ptr, n)                               \
+    if ((st = dalloc(&(ptr), (n))) != PNP_OK) {     \
+        pnp_destroy_problem(p);                     \
+        return st;                                  \
+    }
+    const size_t NC = (size_t)N * q.nchain;
+    ALLOC(p->y, N);
+    ALLOC(p->h, (size_t)q.kh * q.kw);
+    ALLOC(p->x, NC);
+    ALLOC(p->r, NC);
+    ALLOC(p->d, NC);
+    ALLOC(p->mean, NC);
+    ALLOC(p->m2, NC);
+    ALLOC(p->st, 1);
+    if (q.stream) {
+        p->stream = (cudaStream_t)q.stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            pnp_destroy_problem(p);
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        p->own_stream = true;
+    }
+    if (q.D) {
+        const DenoiserDev& D = q.D->dev;
+        if (q.halo == 0) {
+            p->scratch_bytes = denoise_scratch_bytes(D, q.precision, q.ny, q.nx, q.nchain);
+        } else {
+            int mh, mw;
+            std::vector<BlockDesc> bl = make_blocks(q.ny, q.nx, q.blocks_y, q.blocks_x, q.nchain, &mh, &mw);
+            p->nblocks = (int)bl.size();
+            p->ty = mh + 2 * q.halo;
+            p->tx = mw + 2 * q.halo;
+            const size_t tf = (size_t)p->nblocks * p->ty * p->tx;
+            ALLOC(p->blocks, (size_t)p->nblocks);
+            ALLOC(p->tiles, tf);
+            ALLOC(p->dtiles, tf);
+            ALLOC(p->rects, (size_t)p->nblocks);
+            cudaMemcpy(p->blocks, bl.data(), bl.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice);
+            p->scratch_bytes = denoise_scratch_bytes(D, q.precision, p->ty, p->tx, p->nblocks);
+        }
+        uint8_t* sc = nullptr;
+        ALLOC(sc, p->scratch_bytes);
+        p->scratch = sc;
+        cudaMemset(p->scratch, 0, p->scratch_bytes);
+    }
+#undef ALLOC
+    cudaMemcpy(p->y, q.y, N * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(p->h, q.h, (size_t)q.kh * q.kw * 4, cudaMemcpyHostToDevice);
+    if (q.x0) cudaMemcpy(p->x, q.x0, NC * 4, cudaMemcpyHostToDevice);
+    else cudaMemset(p->x, 0, NC * 4);
+    cudaMemset(p->mean, 0, NC * 4);
+    cudaMemset(p->m2, 0, NC * 4);
+    cudaMemset(p->r, 0, NC * 4);
+    cudaMemset(p->d, 0, NC * 4);
+    StepState s0{0u, (int32_t)q.burn_in};
+    cudaMemcpy(p->st, &s0, sizeof(s0), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        pnp_destroy_problem(p);
+        return cuda_fail(e, "pnp_create_problem");
+    }
+    *out = p;
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_problem_params(const pnp_problem* p, double* lambda, double* gamma,
+                                         double* alpha, double* eps) {
+    if (!p) return fail(PNP_EINVAL, "problem is NULL");
+    if (lambda) *lambda = p->lambda;
+    if (gamma) *gamma = p->gamma;
+    if (alpha) *alpha = p->alpha;
+    if (eps) *eps = p->eps;
+    return PNP_OK;
+}
+
+static pnp_status ensure_graph(pnp_problem* p) {
+    if (p->graph) return PNP_OK;
+    // first, make sure every launcher did its one-time setup outside capture
+    cudaGraph_t g = nullptr;
+    PNP_CUDA_TRY(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    pnp_status st = enqueue_iteration(p);
+    cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+    if (st != PNP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&p->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        p->graph = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    return PNP_OK;
+}
+
+static bool g_use_graph = true;
+
+extern "C" pnp_status pnp_kernel_timer(int enable) {
+    PNP_CUDA_TRY(cudaDeviceSynchronize());
+    for (auto& t : g_timers) t.used = 0;
+    g_timing = enable != 0;
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_kernel_timer_read(const char* name, double* total_ms, int64_t* launches) {
+    if (!name || !total_ms || !launches) return fail(PNP_EINVAL, "pnp_kernel_timer_read: NULL");
+    for (int i = 0; i < T_COUNT; ++i) {
+        if (strcmp(name, g_timer_names[i]) != 0) continue;
+        PNP_CUDA_TRY(cudaDeviceSynchronize());
+        double tot = 0.0;
+        for (size_t k = 0; k < g_timers[i].used; ++k) {
+            float ms = 0.f;
+            PNP_CUDA_TRY(cudaEventElapsedTime(&ms, g_timers[i].begin[k], g_timers[i].end[k]));
+            tot += ms;
+        }
+        *total_ms = tot;
+        *launches = (int64_t)g_timers[i].used;
+        return PNP_OK;
+    }
+    return fail(PNP_EINVAL, std::string("unknown kernel timer ") + name);
+}
+
+extern "C" pnp_status pnp_set_graph_mode(int enable) {
+    g_use_graph = enable != 0;
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_step(pnp_problem* p, int n_iters) {
+    if (!p || n_iters < 0) return fail(PNP_EINVAL, "pnp_step: bad arguments");
+    if (n_iters == 0) return PNP_OK;
+    if (g_use_graph && !g_timing) {
+        if (!p->graph) {
+            // one eager iteration first performs the lazy per-kernel setup
+            PNP_TRY(enqueue_iteration(p));
+            p->t += 1;
+            --n_iters;
+            if (n_iters == 0) return PNP_OK;
+            PNP_TRY(ensure_graph(p));
+        }
+        for (int i = 0; i < n_iters; ++i) PNP_CUDA_TRY(cudaGraphLaunch(p->graph, p->stream));
+    } else {
+        for (int i = 0; i < n_iters; ++i) PNP_TRY(enqueue_iteration(p));
+    }
+    p->t += n_iters;
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_sync(pnp_problem* p) {
+    if (!p) return fail(PNP_EINVAL, "problem is NULL");
+    PNP_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_run_chain(pnp_problem* p, int T, int burn_in) {
+    if (!p || T < 0 || burn_in < 0) return fail(PNP_EINVAL, "pnp_run_chain: bad arguments");
+    if (burn_in != p->burn_in) {
+        p->burn_in = burn_in;
+        PNP_CUDA_TRY(cudaMemcpyAsync(&p->st->burn_in, &burn_in, 4, cudaMemcpyHostToDevice, p->stream));
+        PNP_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    }
+    PNP_TRY(pnp_step(p, T));
+    return pnp_sync(p);
+}
+
+extern "C" pnp_status pnp_get_moments(pnp_problem* p, int chain, double* mmse, double* std_or_var,
+                                      int64_t* n_kept, int want_var) {
+    if (!p || !mmse || !std_or_var || chain < 0 || chain >= p->nchain)
+        return fail(PNP_EINVAL, "pnp_get_moments: bad arguments");
+    const int64_t n = std::max<int64_t>(0, p->t - p->burn_in);
+    double* dm = nullptr;
+    PNP_TRY(dalloc(&dm, (size_t)2 * p->N));
+    PNP_CUDA_TRY(launch_finalize_moments(p->mean + chain * p->N, p->m2 + chain * p->N, p->N, n,
+                                         want_var, dm, dm + p->N, p->stream));
+    cudaError_t e = cudaMemcpyAsync(mmse, dm, p->N * 8, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(std_or_var, dm + p->N, p->N * 8, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    cudaFree(dm);
+    if (e != cudaSuccess) return cuda_fail(e, "pnp_get_moments");
+    if (n_kept) *n_kept = n;
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_get_state(pnp_problem* p, float* x, int64_t* t) {
+    if (!p) return fail(PNP_EINVAL, "problem is NULL");
+    if (x) {
+        PNP_CUDA_TRY(cudaMemcpyAsync(x, p->x, (size_t)p->N * p->nchain * 4, cudaMemcpyDeviceToHost, p->stream));
+    }
+    PNP_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    if (t) *t = p->t;
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_set_state(pnp_problem* p, const float* x, int64_t t) {
+    if (!p || t < 0 || t > 0xffffffffLL) return fail(PNP_EINVAL, "pnp_set_state: bad arguments");
+    if (x) {
+        PNP_CUDA_TRY(cudaMemcpyAsync(p->x, x, (size_t)p->N * p->nchain * 4, cudaMemcpyHostToDevice, p->stream));
+    }
+    StepState s0{(uint32_t)t, (int32_t)p->burn_in};
+    PNP_CUDA_TRY(cudaMemcpyAsync(p->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, p->stream));
+    PNP_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    p->t = t;
+    return PNP_OK;
+}
+
+extern "C" float* pnp_problem_x_device(pnp_problem* p) { return p ? p->x : nullptr; }

@@ -1,0 +1,140 @@
+// Internal declarations shared by the CUDA translation units of libpnp.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/pnp.h"
+
+namespace pnp {
+
+// Thread-local error message, set by fail().
+void set_error(const std::string& msg);
+pnp_status fail(pnp_status st, const std::string& msg);
+pnp_status cuda_fail(cudaError_t e, const char* what);
+
+#define PNP_CUDA_TRY(expr)                                         \
+    do {                                                           \
+        cudaError_t _e = (expr);                                   \
+        if (_e != cudaSuccess) return ::pnp::cuda_fail(_e, #expr); \
+    } while (0)
+
+#define PNP_TRY(expr)                           \
+    do {                                        \
+        pnp_status _s = (expr);                 \
+        if (_s != PNP_OK) return _s;            \
+    } while (0)
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Number of SMs of the current device (cached per device).
+int num_sms();
+
+// Optional per-kernel timing with CUDA events (enabled by pnp_kernel_timer;
+// eager launches only). No-ops when disabled.
+bool timer_enabled();
+void timer_begin(int id, cudaStream_t s);
+void timer_end(int id, cudaStream_t s);
+enum TimerId { T_BLUR = 0, T_UPDATE = 1, T_CONV_FP32 = 2, T_CONV_TC = 3, T_CONV_EDGE = 4, T_COUNT = 5 };
+
+// --------------------------------------------------------------------------
+// Valid rectangle of an activation image: positions outside [y0,y1) x [x0,x1)
+// are held at zero after every layer (image border of a block-with-halo tile).
+// --------------------------------------------------------------------------
+struct Rect {
+    int y0, y1, x0, x1;
+};
+
+// --------------------------------------------------------------------------
+// Denoiser parameters on the device.
+// --------------------------------------------------------------------------
+struct DenoiserDev {
+    int K, F;
+    double lip;
+    // FP32 SIMT layouts, per layer: weights [cin][9][cout] (co fastest), bias [cout]
+    float* w32 = nullptr;     // concatenated
+    float* b32 = nullptr;
+    int64_t* w32_off = nullptr;   // host offsets per layer
+    int64_t* b_off = nullptr;
+    // BF16 tensor-core layout of the F->F layers: per layer 9 taps x [8 cg][F co][8 ci]
+    __nv_bfloat16* wtc = nullptr;
+    // FP32 first/last layer weights in tap-major order for the BF16 path
+    float* wfirst = nullptr;  // [9][F]
+    float* wlast = nullptr;   // [9][F]
+    // host copies (FP32, OIHW) for reference / re-packing
+    float* hw = nullptr;
+    float* hb = nullptr;
+};
+
+}  // namespace pnp
+
+struct pnp_denoiser {
+    pnp::DenoiserDev dev;
+    // cached scratch (activation ping-pong), grown on demand
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int device = 0;
+};
+
+namespace pnp {
+
+// ---------------------------------------------------------------- kernels
+cudaError_t launch_blur(const float* x, const float* y, const float* h, int kh, int kw, int ny,
+                        int nx, int nimg, float* r, cudaStream_t s);
+cudaError_t launch_blur_adjoint(const float* r, const float* h, int kh, int kw, int ny, int nx,
+                                int nimg, float scale, float* g, cudaStream_t s);
+
+struct UpdateParams {
+    float* x;
+    const float* r;
+    const float* d;
+    const float* h;
+    int kh, kw, ny, nx, nchain;
+    float inv_s2;       // 1 / sigma^2
+    float gamma;
+    float c_prior;      // alpha gamma / eps^2 (0 if d == NULL)
+    float c_proj;       // gamma / lambda (0 when off)
+    float c_noise;      // sqrt(2 gamma) (0 when noise off)
+    uint32_t key0, key1;
+    uint32_t t;
+    const uint32_t* t_dev;     // if non-null, t is read from device memory (graph replay)
+    float* mean;
+    float* m2;
+    float inv_n;        // 1 / n_kept (0: no accumulation)
+    const int32_t* burn_dev;   // if non-null: sample number n = t + 1 - *burn_dev,
+                               // accumulated when n > 0 (graph replay)
+};
+cudaError_t launch_langevin_update(const UpdateParams& p, cudaStream_t s);
+cudaError_t launch_finalize_moments(const float* mean, const float* m2, int64_t npix,
+                                    int64_t n_kept, int want_var, double* mmse, double* out2,
+                                    cudaStream_t s);
+
+// FP32 SIMT denoiser over a batch of nimg images [nimg][ny][nx]; optional per-image
+// valid rects (device, nimg entries) for block-with-halo tiles. scratch must hold
+// 2 * nimg * F * ny * nx floats. d = x - G(x).
+cudaError_t denoise_fp32(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
+                         const Rect* rects, float* d, float* scratch, cudaStream_t s);
+size_t denoise_fp32_scratch(const DenoiserDev& D, int ny, int nx, int nimg);
+
+// BF16 tcgen05 denoiser (F = 64). scratch must hold denoise_bf16_scratch() bytes.
+cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
+                         const Rect* rects, float* d, void* scratch, cudaStream_t s);
+size_t denoise_bf16_scratch(const DenoiserDev& D, int ny, int nx, int nimg);
+
+// Block-with-halo gather / scatter (Sec. II-B2 receptive-field variant).
+struct BlockDesc {
+    int img;        // source image index
+    int r0, r1;     // interior rows  [r0, r1)
+    int c0, c1;     // interior cols  [c0, c1)
+};
+cudaError_t launch_gather_blocks(const float* x, int ny, int nx, const BlockDesc* blocks,
+                                 int nblocks, int halo, int ty, int tx, float* tiles,
+                                 Rect* rects, cudaStream_t s);
+cudaError_t launch_scatter_blocks(const float* dtiles, int ny, int nx, const BlockDesc* blocks,
+                                  int nblocks, int halo, int ty, int tx, float* d,
+                                  cudaStream_t s);
+
+}  // namespace pnp
