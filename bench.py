@@ -197,7 +197,9 @@ def main():
     den = P.Denoiser.from_weights(dw)
     ny, nx = prob.shape
     npix = ny * nx
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the problems enqueue on it and the events are recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     peaks = load_peaks()
     precs = [p for p in args.precisions.split(",") if p]
     if w["F"] != 64:
