@@ -109,6 +109,30 @@ pnp_status pnp_denoise(const pnp_denoiser* D, pnp_precision prec, const float* x
                        int nx, int nimg, int blocks_y, int blocks_x, int halo, float* d,
                        void* stream);
 
+/* Size of the fixed scratch area used by pnp_denoise_noalloc (64 MiB + 4 KiB). */
+#define PNP_NOALLOC_SCRATCH_BYTES ((size_t)64 * 1024 * 1024 + 4096)
+
+/* pnp_denoise without any device allocation. The paper has no counterpart:
+ * this is a library-level variant for callers that must not allocate, such
+ * as a process whose device memory is already reserved by another allocator
+ * (a raw cudaMalloc would fail there) or a latency-bound loop that cannot
+ * afford cudaMalloc/cudaFree synchronizing the device.
+ * Same arguments and result as pnp_denoise with halo = 0 (whole-image
+ * layers). Scratch is a fixed area inside the library (a file-scope
+ * __device__ array of PNP_NOALLOC_SCRATCH_BYTES), reserved on every GPU that
+ * loads the library until the process exits. It needs
+ *   FP32: 8 * F * nimg * ny * nx bytes,  BF16: 256 * nimg * ny * ceil8(nx) + 256 bytes
+ * (BF16 fits a 512 x 512 image; FP32 with F = 64 fits about 362 x 362);
+ * larger requests return PNP_EINVAL with the needed size and launch nothing.
+ * The first call on a device looks up the area's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls on a device share its one area and it keeps the previous call's
+ * contents, so calls that can overlap on the GPU (for example on two streams
+ * of the same device) race: serialize them on one stream. Calls no
+ * cudaMalloc, cudaFree or other allocating routine. */
+pnp_status pnp_denoise_noalloc(const pnp_denoiser* D, pnp_precision prec, const float* x,
+                               int ny, int nx, int nimg, float* d, void* stream);
+
 /* One fused PnP-ULA x-update (Eq. 8) for nchain chains sharing y and h:
  *   g = H^T r / sigma^2 (r = H x - y from pnp_blur, device [nchain][ny][nx]),
  *   x <- x - gamma g + (alpha gamma/eps^2)(d - x) + (gamma/lambda)(clamp(x,0,1) - x)

@@ -131,6 +131,14 @@ class Denoiser:
                                  blocks[1], halo, _ptr(out), _stream(stream)))
         return out
 
+    def denoise_noalloc(self, x, out, precision="fp32", stream=None):
+        """pnp_denoise_noalloc: same result as denoise() with halo = 0, computed in
+        the library's fixed scratch area instead of allocating; `out` is caller-owned."""
+        n, ny, nx = x.shape
+        check(load().pnp_denoise_noalloc(self.handle, _prec(precision), _ptr(x), ny, nx, n,
+                                         _ptr(out), _stream(stream)))
+        return out
+
     def close(self):
         if getattr(self, "handle", None):
             load().pnp_destroy_denoiser(self.handle)

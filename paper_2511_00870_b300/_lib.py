@@ -50,6 +50,7 @@ SIGNATURES = {
     "pnp_blur": ([vp, vp, vp, i32, i32, i32, i32, i32, vp, vp], i32),
     "pnp_blur_adjoint": ([vp, vp, i32, i32, i32, i32, i32, f32, vp, vp], i32),
     "pnp_denoise": ([vp, i32, vp, i32, i32, i32, i32, i32, i32, vp, vp], i32),
+    "pnp_denoise_noalloc": ([vp, i32, vp, i32, i32, i32, vp, vp], i32),
     "pnp_langevin_update": ([vp, vp, vp, vp, i32, i32, i32, i32, i32, f64, f64, f64, f64, f64,
                              u64, u32, i32, vp, vp, i64, vp], i32),
     "pnp_finalize_moments": ([vp, vp, i64, i64, i32, vp, vp, vp], i32),
