@@ -67,7 +67,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -108,20 +108,25 @@ def dist_setup():
     return ws, rank, local
 
 
-def oracle_baseline(cfg_id, budget_s=20.0):
-    """The FP64 oracle as it stands, on a bounded sample of the workload:
-    whole iterations on a crop of the image (same blur, noise level and
-    network), on this host's cores."""
+def _oracle_setup(cfg_id, crop):
     import oracle
     prob = synth.workload_problem(cfg_id)
     dw = synth.workload_denoiser(cfg_id)
-    ny, nx = prob.shape
-    crop = min(ny, 128 if cfg_id != 1 else ny)
+    crop = min(crop, prob.shape[0], prob.shape[1])
     y = prob.y[:crop, :crop]
     lam, gam = oracle.stepsizes(float(np.abs(prob.h).sum()), prob.sigma, 1.0, prob.sigma,
                                 dw.lipschitz)
     op = oracle.Problem(y, prob.h, prob.sigma, 1.0, prob.sigma, lam, gam, prob.seed,
                         net=oracle.Net.from_weights(dw))
+    return oracle, prob, op, crop
+
+
+def oracle_baseline(cfg_id, budget_s=20.0, crop=128):
+    """The FP64 oracle as it stands, on a bounded sample of the workload:
+    whole iterations on a crop of the image (same blur, noise level and
+    network), on this host's cores."""
+    oracle, prob, op, crop = _oracle_setup(cfg_id, crop)
+    ny, nx = prob.shape
     x = np.zeros((crop, crop))
     t0 = time.perf_counter()
     it = 0
@@ -134,29 +139,37 @@ def oracle_baseline(cfg_id, budget_s=20.0):
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return dict(value=crop * crop * it / dt / 1e6, unit=UNIT, cores=cores, kind="oracle",
                 sample=f"{it} FP64 oracle iterations on a {crop}x{crop} crop of the "
-                       f"{ny}x{nx} workload (same blur, noise, 8-layer net)")
+                       f"{ny}x{nx} workload (same blur, noise, network)")
 
 
 def run_reference(args):
+    """Reference arm: the FP64 oracle; one step = one oracle iteration on a crop
+    of the workload, the crop sized so that the whole run stays within minutes."""
     ws, rank, _ = dist_setup()
     if rank != 0:
         return
     cfg_id = WORKLOADS[args.workload]
     w = synth.WORKLOADS[cfg_id]
-    per = []
     steps = max(1, args.steps)
-    b = None
-    for k in range(args.warmup + steps):
-        b = oracle_baseline(cfg_id, budget_s=max(2.0, 60.0 / (args.warmup + steps)))
-        if k >= args.warmup:
-            per.append(b["value"])
-    val = float(np.mean(per))
+    n = args.warmup + steps
+    crop = 128 if n <= 60 else (64 if n <= 250 else 32)
+    oracle, prob, op, crop = _oracle_setup(cfg_id, crop)
+    x = np.zeros((crop, crop))
+    for it in range(args.warmup):
+        x = oracle.langevin_step(op, x, it)
+    t0 = time.perf_counter()
+    for it in range(args.warmup, n):
+        x = oracle.langevin_step(op, x, it)
+    dt = time.perf_counter() - t0
+    val = crop * crop * steps / dt / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"each step one FP64 oracle iteration on a {crop}x{crop} crop of the "
+              f"{prob.shape[0]}x{prob.shape[1]} workload (same blur, noise, network)")
     line = dict(metric=METRIC, value=val, unit=UNIT, n_gpus=args.gpus, steps=steps,
-                warmup=args.warmup, ms_per_step=None, higher_is_better=True, scaling="weak",
-                vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                warmup=args.warmup, ms_per_step=1e3 * dt / steps, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
                 config=dict(workload=f"{w['name']} (oracle, bounded crop sample)"),
-                cpu_baseline=dict(kind="oracle", cores=b["cores"], sample=b["sample"], value=val,
-                                  unit=UNIT),
+                cpu_baseline=dict(kind="oracle", cores=cores, sample=sample, value=val, unit=UNIT),
                 e2e=dict(value=val, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -164,7 +177,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="deconv1024", choices=sorted(WORKLOADS))
@@ -222,6 +235,7 @@ def main():
         gp = P.Problem(prob.y, prob.h, prob.sigma, den, blocks=w["blocks"], halo=0,
                        seed=prob.seed, burn_in=w["burn_in"], precision=prec,
                        stream=stream.cuda_stream)
+        steps = args.steps if prec == precs[0] else min(args.steps, 200)
         gp.step(args.warmup)
         torch.cuda.synchronize()
         barrier()
@@ -230,14 +244,14 @@ def main():
         sampler.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        gp.step(args.steps)
+        gp.step(steps)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
         ck = sampler.stop()
         ms = e0.elapsed_time(e1)
         ms_max = max_over_ranks(ms)
-        results[prec] = dict(ms=ms_max, value=ws * npix * args.steps / (ms_max * 1e3))
+        results[prec] = dict(ms=ms_max, steps=steps, value=ws * npix * steps / (ms_max * 1e3))
         if prec == precs[0]:
             clocks = ck
         # dominant-kernel timing: same iterations launched eagerly with CUDA events
@@ -335,7 +349,8 @@ def main():
     )
     if "fp32" in results and precs[0] != "fp32":
         line["fp32_plain"] = dict(value=round(results["fp32"]["value"], 3), unit=UNIT,
-                                  ms_per_step=round(results["fp32"]["ms"] / args.steps, 4),
+                                  ms_per_step=round(results["fp32"]["ms"] / results["fp32"]["steps"], 4),
+                                  steps=results["fp32"]["steps"],
                                   speedup_bf16=round(head["value"] / results["fp32"]["value"], 3))
     if quality:
         line["quality"] = quality

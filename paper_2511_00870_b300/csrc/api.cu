@@ -227,18 +227,33 @@ extern "C" pnp_status pnp_create_denoiser(int K, int F, const float* weights, co
     memcpy(D.hw, weights, wsrc * 4);
     memcpy(D.hb, biases, bsrc * 4);
     if (F == 64) {
-        // tensor-core blobs of the F -> F layers: [tap][cg][co][8 ci] BF16
+        // tensor-core blobs of the F -> F layers, BF16 [dx][cg][dy*64 + co][8 ci]:
+        // for a fixed column shift dx the three kernel rows are stacked along N
         const int nmid = K - 2;
         std::vector<uint16_t> blob((size_t)std::max(nmid, 1) * 9 * 8 * 64 * 8, 0);
         for (int m = 0; m < nmid; ++m) {
             const float* W = weights + src_off[m + 1];
-            for (int t = 0; t < 9; ++t)
+            for (int dx = 0; dx < 3; ++dx)
                 for (int cg = 0; cg < 8; ++cg)
-                    for (int co = 0; co < 64; ++co)
-                        for (int c8 = 0; c8 < 8; ++c8)
-                            blob[((((size_t)m * 9 + t) * 8 + cg) * 64 + co) * 8 + c8] =
-                                f32_to_bf16_rne(W[((int64_t)co * 64 + cg * 8 + c8) * 9 + t]);
+                    for (int dy = 0; dy < 3; ++dy)
+                        for (int co = 0; co < 64; ++co)
+                            for (int c8 = 0; c8 < 8; ++c8)
+                                blob[(((((size_t)m * 3 + dx) * 8 + cg) * 192 + dy * 64 + co) * 8) + c8] =
+                                    f32_to_bf16_rne(W[((int64_t)co * 64 + cg * 8 + c8) * 9 + dy * 3 + dx]);
         }
+        D.h_first = new EdgeW();
+        D.h_last = new EdgeW();
+        memset(D.h_first, 0, sizeof(EdgeW));
+        memset(D.h_last, 0, sizeof(EdgeW));
+        int64_t b_last = 0;
+        for (int k = 0; k < K - 1; ++k) b_last += cout[k];
+        for (int t = 0; t < 9; ++t)
+            for (int c = 0; c < 64; ++c) {
+                D.h_first->w[t][c] = weights[src_off[0] + (int64_t)c * 9 + t];
+                D.h_last->w[t][c] = weights[src_off[K - 1] + (int64_t)c * 9 + t];
+            }
+        for (int c = 0; c < 64; ++c) D.h_first->b[c] = biases[c];
+        D.h_last->b[0] = biases[b_last];
         std::vector<float> wf(9 * 64), wl(9 * 64);
         for (int t = 0; t < 9; ++t)
             for (int c = 0; c < 64; ++c) {
@@ -276,6 +291,8 @@ extern "C" void pnp_destroy_denoiser(pnp_denoiser* den) {
     delete[] D.b_off;
     delete[] D.hw;
     delete[] D.hb;
+    delete D.h_first;
+    delete D.h_last;
     delete den;
 }
 

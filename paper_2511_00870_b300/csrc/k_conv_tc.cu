@@ -13,17 +13,27 @@
 // address and a tap shift dy selects another row slot, so each input row is
 // fetched from HBM/L2 once per 128-pixel column strip.
 //
-// GEMM per output row segment: M = 128 pixels, N = 64 output channels,
-// K = 9 taps x 64 input channels, accumulated in TMEM (FP32) as 36 MMAs of
-// 128 x 64 x 16. Warp roles: warp 0 = TMA producer, warp 1 = MMA issuer,
-// warps 2-5 = epilogue (TMEM -> registers, bias, ReLU, zero outside the valid
-// rect, BF16, global store). Input rows circulate through a 6-slot ring;
-// accumulators are double-buffered in TMEM so the epilogue of one row overlaps
-// the MMAs of the next. Every CTA walks a contiguous range of the
-// (image, strip, row) stream, so work is balanced to within one row.
+// The GEMM is organised around input rows: input row i at column shift dx
+// (M = 128 pixels, K = 16 channels per MMA) is multiplied by the stacked
+// weights [W(dy=0,dx); W(dy=1,dx); W(dy=2,dx)] (N = 3 x 64), which adds its
+// contribution to output rows i+1, i and i-1 in one MMA. The output rows'
+// FP32 accumulators sit in adjacent 64-column TMEM slots (slot of output row
+// q = -q mod 8), so per input row 12 MMAs of 128 x 192 x 16 run (split in two
+// where the slot ring wraps) instead of 36 of 128 x 64 x 16, which the tensor
+// core executes at only ~60 % of its rate. Accumulators always accumulate;
+// the epilogue zeroes a slot right after draining it. Warp roles: warp 0 =
+// TMA producer, warp 1 = MMA issuer, warps 2-5 = epilogue (TMEM -> registers,
+// bias, ReLU, zero outside the valid rect, BF16, global store). Input rows
+// circulate through a 6-slot shared-memory ring.
+//
+// One launch covers a table of jobs (images of possibly different sizes,
+// each with its own tensor map): every CTA walks a contiguous range of the
+// concatenated (job, image, strip, row) stream, so the work of all jobs is
+// balanced across the SMs to within one row.
 #include <cuda.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "pnp_internal.h"
 #include "tc_ptx.cuh"
@@ -32,40 +42,93 @@ namespace pnp {
 
 namespace tc {
 constexpr int F = 64;
-constexpr int SEG = 128;                 // output pixels per row segment (UMMA M)
-constexpr int HALO_PX = 8;               // smem row starts 8 px left of the segment
+constexpr int SEG = 128;                    // output pixels per row segment (UMMA M)
+constexpr int HALO_PX = 8;                  // smem row starts 8 px left of the segment
 constexpr int ROW_PX = SEG + 2 * HALO_PX;   // 144
 constexpr int CG_BYTES = ROW_PX * 16;       // 2304: one channel-group plane of a row
 constexpr int ROW_BYTES = 8 * CG_BYTES;     // 18432
 constexpr int NS = 6;                       // input-row ring slots
-constexpr int TAP_W_BYTES = 8 * F * 16;     // 8192: [cg][co][8 ci] of one tap
-constexpr int W_BYTES = 9 * TAP_W_BYTES;    // 73728
+constexpr int NACC = 8;                     // TMEM accumulator slots (64 columns each)
+constexpr int TMEM_COLS = NACC * F;         // 512
+constexpr int NB = 3 * F;                   // stacked rows of one column shift (dy, co)
+constexpr int DX_W_BYTES = 8 * NB * 16;     // 24576: [cg][dy*64+co][8 ci] of one dx
+constexpr int W_BYTES = 3 * DX_W_BYTES;     // 73728
 constexpr int THREADS = 192;
 constexpr int OFF_RING = 0;
 constexpr int OFF_W = OFF_RING + NS * ROW_BYTES;
 constexpr int OFF_BIAS = OFF_W + W_BYTES;
 constexpr int OFF_BAR = OFF_BIAS + F * 4;
-constexpr int NBAR = 2 * NS + 1 + 2 + 2 + 1;   // full, empty, weights, tfull, tempty, drain
+constexpr int NBAR = 2 * NS + 1 + 2 * NACC + 1;   // full, empty, weights, tfull, tempty, drain
 constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
-constexpr int SMEM = OFF_MISC + 16 + 1024;     // + alignment slack
-constexpr uint32_t IDESC = ptx::idesc_bf16_f32(SEG, F);
-constexpr long long BUDGET = 4000000000LL;     // ~2 s of SM clock per wait
+constexpr int SMEM = OFF_MISC + 16 + 1024;        // + alignment slack
+constexpr uint32_t IDESC64 = ptx::idesc_bf16_f32(SEG, 64);
+constexpr uint32_t IDESC128 = ptx::idesc_bf16_f32(SEG, 128);
+constexpr uint32_t IDESC192 = ptx::idesc_bf16_f32(SEG, 192);
+constexpr long long BUDGET = 4000000000LL;        // ~2 s of SM clock per wait
+// descriptor words (no swizzle, K-major): low = start>>4 | (LBO>>4)<<16,
+// high = SBO>>4 | version bit 46
+constexpr uint32_t A_LBO_FIELD = (uint32_t)(CG_BYTES >> 4) << 16;
+constexpr uint32_t B_LBO_FIELD = (uint32_t)((NB * 16) >> 4) << 16;
+constexpr uint32_t DESC_HI = (128u >> 4) | (1u << 14);
 }  // namespace tc
+
+static_assert(sizeof(TcJob) == 256 && alignof(TcJob) == 128, "TcJob layout");
+static_assert(tc::SMEM <= 232448, "shared memory budget");
 
 __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 
-struct TcConvArgs {
-    const __nv_bfloat16* wblob;   // [9 taps][8 cg][64 co][8 ci]
+struct TcCommon {
+    const __nv_bfloat16* wblob;   // [3 dx][8 cg][3 dy x 64 co][8 ci]
     const float* bias;            // [64]
-    __nv_bfloat16* out;
-    const Rect* rects;
     int* err;
-    int ny, nx, nxp, nimg, strips;
+    const TcJob* jobs;            // device table, or nullptr: the single job parameter
+    int njobs;
     int64_t total_rows;
 };
 
+// Position in the concatenated row stream of a launch.
+struct RowPos {
+    const TcJob* J;
+    int img, strip, y, len;
+};
+
+__device__ __forceinline__ const TcJob* job_at(const TcJob& job0, const TcCommon& c, int j) {
+    return c.jobs ? c.jobs + j : &job0;
+}
+
+// Advance job index j to the job holding global row g and decompose g.
+__device__ __forceinline__ RowPos locate(const TcJob& job0, const TcCommon& c, int& j, int64_t g,
+                                         int64_t g_end) {
+    const TcJob* J = job_at(job0, c, j);
+    while (g >= J->row_begin + J->rows && j + 1 < c.njobs) J = job_at(job0, c, ++j);
+    const int64_t local = g - J->row_begin;
+    const int64_t q = local / J->ny;
+    RowPos p;
+    p.J = J;
+    p.y = (int)(local - q * J->ny);
+    p.strip = (int)(q % J->strips);
+    p.img = (int)(q / J->strips);
+    p.len = (int)imin64(imin64(g_end, J->row_begin + J->rows) - g, (int64_t)J->ny - p.y);
+    return p;
+}
+
+// D[tmem] += A * B with both descriptors given by their low words (the high
+// words are the same constant); always accumulates.
+__device__ __forceinline__ void mma_acc(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo,
+                                        uint32_t idesc) {
+    asm volatile(
+        "{\n.reg .b64 da, db;\n"
+        "mov.b64 da, {%1, %2};\n"
+        "mov.b64 db, {%3, %2};\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, 1;\n}\n" ::"r"(d_tmem),
+        "r"(a_lo), "r"(tc::DESC_HI), "r"(b_lo), "r"(idesc)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t slot_of(uint32_t q) { return (tc::NACC - (q % tc::NACC)) % tc::NACC; }
+
 __global__ void __launch_bounds__(tc::THREADS, 1)
-    k_conv_tc(const __grid_constant__ CUtensorMap tin, const TcConvArgs a) {
+    k_conv_tc(const __grid_constant__ TcJob job0, const TcCommon c) {
     using namespace tc;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -77,8 +140,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     uint64_t* empty = bars + NS;
     uint64_t* wbar = bars + 2 * NS;
     uint64_t* tfull = bars + 2 * NS + 1;
-    uint64_t* tempty = bars + 2 * NS + 3;
-    uint64_t* drain = bars + 2 * NS + 5;
+    uint64_t* tempty = tfull + NACC;
+    uint64_t* drain = tempty + NACC;
     uint32_t* tmem_slot = (uint32_t*)(smem + OFF_MISC);
     volatile int* abort_flag = (volatile int*)(smem + OFF_MISC + 4);
 
@@ -89,7 +152,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             ptx::mbar_init(&empty[i], 1);
         }
         ptx::mbar_init(wbar, 1);
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NACC; ++i) {
             ptx::mbar_init(&tfull[i], 1);
             ptx::mbar_init(&tempty[i], 4);
         }
@@ -97,43 +160,51 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
-    if (warp == 0 && lane == 0) ptx::prefetch_tensormap(&tin);
+    if (warp == 0 && lane == 0 && !c.jobs) ptx::prefetch_tensormap(&job0.tin);
     if (warp == 2) {
-        ptx::tmem_alloc(tmem_slot, 128);
+        ptx::tmem_alloc(tmem_slot, TMEM_COLS);
         ptx::tmem_relinquish();
     }
-    if (threadIdx.x >= 64 && threadIdx.x < 64 + F) bias_s[threadIdx.x - 64] = a.bias[threadIdx.x - 64];
+    if (threadIdx.x >= 64 && threadIdx.x < 64 + F) bias_s[threadIdx.x - 64] = c.bias[threadIdx.x - 64];
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // accumulators always accumulate: start every slot at zero
+    if (warp >= 2) {
+        const uint32_t lane_base = tmem_base + ((uint32_t)((warp & 3) * 32) << 16);
+#pragma unroll 1
+        for (int sl = 0; sl < NACC; ++sl) ptx::tmem_st_zero_32x32b_x64(lane_base + sl * F);
+        ptx::tmem_st_wait();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
 
-    // this CTA's share of the (image, strip, row) stream
-    const int64_t g_begin = a.total_rows * blockIdx.x / gridDim.x;
-    const int64_t g_end = a.total_rows * (blockIdx.x + 1) / gridDim.x;
+    // this CTA's share of the concatenated row stream
+    const int64_t g_begin = c.total_rows * blockIdx.x / gridDim.x;
+    const int64_t g_end = c.total_rows * (blockIdx.x + 1) / gridDim.x;
 
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer
             ptx::mbar_arrive_expect_tx(wbar, W_BYTES);
-            for (int t = 0; t < 9; ++t)
-                ptx::bulk_load(wsm + t * TAP_W_BYTES, (const uint8_t*)a.wblob + t * TAP_W_BYTES,
-                               TAP_W_BYTES, wbar);
+            for (int t = 0; t < 3; ++t)
+                ptx::bulk_load(wsm + t * DX_W_BYTES, (const uint8_t*)c.wblob + t * DX_W_BYTES,
+                               DX_W_BYTES, wbar);
             uint32_t L = 0;
             bool ok = true;
+            int j = 0;
             for (int64_t g = g_begin; g < g_end && ok;) {
-                const int64_t q = g / a.ny;
-                const int y = (int)(g - q * a.ny);
-                const int s = (int)(q % a.strips), img = (int)(q / a.strips);
-                const int len = (int)imin64(g_end - g, (int64_t)a.ny - y);
-                for (int r = y - 1; r <= y + len && ok; ++r, ++L) {
+                const RowPos p = locate(job0, c, j, g, g_end);
+                for (int r = p.y - 1; r <= p.y + p.len && ok; ++r, ++L) {
                     const uint32_t slot = L % NS, u = L / NS;
                     if (!ptx::mbar_wait(&empty[slot], (u & 1) ^ 1, abort_flag, BUDGET)) { ok = false; break; }
                     ptx::mbar_arrive_expect_tx(&full[slot], ROW_BYTES);
-                    ptx::tma_load_5d(ring + slot * ROW_BYTES, &tin, &full[slot], 0,
-                                     s * (SEG / 8) - HALO_PX / 8, 0, r, img);
+                    ptx::tma_load_5d(ring + slot * ROW_BYTES, &p.J->tin, &full[slot], 0,
+                                     p.strip * (SEG / 8) - HALO_PX / 8, 0, r, p.img);
                 }
-                g += len;
+                g += p.len;
             }
             // wait for this thread's copies still in flight (only after an abort)
             if (!ok) {
@@ -143,52 +214,53 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---------------- MMA issuer
+            // ---------------- MMA issuer: one batch of MMAs per input row
             bool ok = ptx::mbar_wait(wbar, 0, abort_flag, BUDGET);
-            const uint32_t ring_a = ptx::smem_u32(ring), w_a = ptx::smem_u32(wsm);
-            uint32_t L = 0, R = 0;
+            const uint32_t ring_lo = (ptx::smem_u32(ring) >> 4) | A_LBO_FIELD;
+            const uint32_t w_lo = (ptx::smem_u32(wsm) >> 4) | B_LBO_FIELD;
+            uint32_t L = 0, Q = 0;
             bool issued = false;
+            int j = 0;
             for (int64_t g = g_begin; g < g_end && ok;) {
-                const int64_t q = g / a.ny;
-                const int y = (int)(g - q * a.ny);
-                const int len = (int)imin64(g_end - g, (int64_t)a.ny - y);
-                (void)y;
-                const uint32_t base = L;
-                for (uint32_t k = 0; k < 2 && ok; ++k)
-                    ok = ptx::mbar_wait(&full[(base + k) % NS], ((base + k) / NS) & 1, abort_flag, BUDGET);
-                for (int k = 0; k < len && ok; ++k) {
-                    const uint32_t Ln = base + k + 2;
-                    ok = ptx::mbar_wait(&full[Ln % NS], (Ln / NS) & 1, abort_flag, BUDGET);
-                    const uint32_t acc = R & 1, v = R >> 1;
-                    if (ok) ok = ptx::mbar_wait(&tempty[acc], (v & 1) ^ 1, abort_flag, BUDGET);
+                const RowPos p = locate(job0, c, j, g, g_end);
+                const int len = p.len;
+                // input rows y-1 .. y+len, ri = input row - y
+                for (int ri = -1; ri <= len && ok; ++ri) {
+                    const uint32_t Lc = L + (uint32_t)(ri + 1);
+                    ok = ptx::mbar_wait(&full[Lc % NS], (Lc / NS) & 1, abort_flag, BUDGET);
+                    // kernel rows dy contribute to output row ri+1-dy; keep those inside the item
+                    const int dy_lo = ri <= len - 2 ? 0 : (ri <= len - 1 ? 1 : 2);
+                    const int dy_hi = ri >= 1 ? 2 : (ri >= 0 ? 1 : 0);
+                    const uint32_t q_lo = Q + (uint32_t)(ri + 1 - dy_lo);   // output row of dy_lo
+                    if (ok && dy_lo == 0)   // first contribution to a new output row: claim its slot
+                        ok = ptx::mbar_wait(&tempty[slot_of(q_lo)], ((q_lo / NACC) & 1) ^ 1,
+                                            abort_flag, BUDGET);
                     if (!ok) break;
                     ptx::tc_fence_after();
-                    const uint32_t d_tmem = tmem_base + acc * F;
-#pragma unroll 1
-                    for (int dy = 0; dy < 3; ++dy) {
-                        const uint32_t slot_addr = ring_a + ((base + k + dy) % NS) * ROW_BYTES;
+                    const uint32_t s_lo = slot_of(q_lo);
+                    const int n = dy_hi - dy_lo + 1;
+                    const int n1 = min(n, NACC - (int)s_lo);   // run up to the end of the ring
+                    const uint32_t id1 = n1 == 3 ? IDESC192 : (n1 == 2 ? IDESC128 : IDESC64);
+                    const uint32_t id2 = (n - n1) == 2 ? IDESC128 : IDESC64;
+                    const uint32_t a_row = ring_lo + (Lc % NS) * (ROW_BYTES >> 4);
+                    const uint32_t b1 = w_lo + (uint32_t)dy_lo * (F * 16 >> 4);
+                    const uint32_t b2 = b1 + (uint32_t)n1 * (F * 16 >> 4);
+                    const uint32_t d1 = tmem_base + s_lo * F;
 #pragma unroll
-                        for (int dx = 0; dx < 3; ++dx) {
+                    for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
-                                const uint64_t ad = ptx::smem_desc_noswizzle(
-                                    slot_addr + kk * 2 * CG_BYTES + (HALO_PX - 1 + dx) * 16, CG_BYTES, 128);
-                                const uint64_t bd = ptx::smem_desc_noswizzle(
-                                    w_a + (dy * 3 + dx) * TAP_W_BYTES + kk * 2 * (F * 16), F * 16, 128);
-                                ptx::mma_bf16(d_tmem, ad, bd, IDESC, (dy | dx | kk) != 0);
-                            }
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint32_t a_lo = a_row + kk * 2 * (CG_BYTES >> 4) + (HALO_PX - 1 + dx);
+                            const uint32_t boff = dx * (DX_W_BYTES >> 4) + kk * 2 * (NB * 16 >> 4);
+                            mma_acc(d1, a_lo, b1 + boff, id1);
+                            if (n1 < n) mma_acc(tmem_base, a_lo, b2 + boff, id2);
                         }
-                    }
                     issued = true;
-                    ptx::mma_commit(&empty[(base + k) % NS]);   // row y+k-1 is no longer needed
-                    ptx::mma_commit(&tfull[acc]);
-                    ++R;
+                    ptx::mma_commit(&empty[Lc % NS]);          // input row fully consumed
+                    if (dy_hi == 2) ptx::mma_commit(&tfull[slot_of(Q + (uint32_t)(ri - 1))]);
                 }
-                if (ok) {
-                    ptx::mma_commit(&empty[(base + len) % NS]);
-                    ptx::mma_commit(&empty[(base + len + 1) % NS]);
-                }
-                L = base + len + 2;
+                L += (uint32_t)(len + 2);
+                Q += (uint32_t)len;
                 g += len;
             }
             if (issued) {
@@ -199,30 +271,33 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     } else {
         // ---------------- epilogue: warps 2..5 own TMEM lane quadrants 2,3,0,1
         const int quad = warp & 3;
-        const int j = quad * 32 + lane;
-        uint32_t R = 0;
+        const int jx = quad * 32 + lane;
+        const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
+        uint32_t Q = 0;
         bool ok = true;
+        int j = 0;
         for (int64_t g = g_begin; g < g_end && ok;) {
-            const int64_t q = g / a.ny;
-            const int y = (int)(g - q * a.ny);
-            const int s = (int)(q % a.strips), img = (int)(q / a.strips);
-            const int len = (int)imin64(g_end - g, (int64_t)a.ny - y);
-            const Rect rc = a.rects ? a.rects[img] : Rect{0, a.ny, 0, a.nx};
-            const int x = s * SEG + j;
-            for (int k = 0; k < len; ++k, ++R) {
-                const uint32_t acc = R & 1, v = R >> 1;
-                if (!ptx::mbar_wait(&tfull[acc], v & 1, abort_flag, BUDGET)) { ok = false; break; }
+            const RowPos p = locate(job0, c, j, g, g_end);
+            const TcJob* J = p.J;
+            const Rect rc = J->rects ? J->rects[p.img] : Rect{0, J->ny, 0, J->nx};
+            const int x = p.strip * SEG + jx;
+            const int nxp = J->nxp;
+            for (int k = 0; k < p.len; ++k, ++Q) {
+                const uint32_t sl = slot_of(Q);
+                if (!ptx::mbar_wait(&tfull[sl], (Q / NACC) & 1, abort_flag, BUDGET)) { ok = false; break; }
                 ptx::tc_fence_after();
                 uint32_t r[64];
-                ptx::tmem_ld_32x32b_x64(tmem_base + ((uint32_t)(quad * 32) << 16) + acc * F, r);
+                ptx::tmem_ld_32x32b_x64(lane_base + sl * F, r);
                 ptx::tmem_ld_wait();
+                ptx::tmem_st_zero_32x32b_x64(lane_base + sl * F);
+                ptx::tmem_st_wait();
                 ptx::tc_fence_before();
                 __syncwarp();
-                if (lane == 0) ptx::mbar_arrive(&tempty[acc]);
-                const int yy = y + k;
-                if (x < a.nxp) {
-                    const bool valid = x < a.nx && yy >= rc.y0 && yy < rc.y1 && x >= rc.x0 && x < rc.x1;
-                    __nv_bfloat16* o = a.out + ((((int64_t)img * a.ny + yy) * 8) * a.nxp + x) * 8;
+                if (lane == 0) ptx::mbar_arrive(&tempty[sl]);
+                const int yy = p.y + k;
+                if (x < nxp) {
+                    const bool valid = x < J->nx && yy >= rc.y0 && yy < rc.y1 && x >= rc.x0 && x < rc.x1;
+                    __nv_bfloat16* o = J->out + ((((int64_t)p.img * J->ny + yy) * 8) * nxp + x) * 8;
 #pragma unroll
                     for (int cg = 0; cg < 8; ++cg) {
                         uint32_t pk[4];
@@ -235,12 +310,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                             __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
                             pk[e] = *reinterpret_cast<uint32_t*>(&h2);
                         }
-                        *reinterpret_cast<uint4*>(o + (int64_t)cg * a.nxp * 8) =
+                        *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 8) =
                             make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     }
                 }
             }
-            g += len;
+            g += p.len;
         }
     }
 
@@ -248,25 +323,23 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     __syncthreads();
     if (warp == 2) {
         ptx::tc_fence_after();
-        ptx::tmem_dealloc(tmem_base, 128);
+        ptx::tmem_dealloc(tmem_base, TMEM_COLS);
     }
-    if (threadIdx.x == 0 && *abort_flag && a.err) atomicExch(a.err, (int)PNP_ETIMEOUT);
+    if (threadIdx.x == 0 && *abort_flag && c.err) atomicExch(c.err, (int)PNP_ETIMEOUT);
 }
 
 // ---------------------------------------------------------------------------
 // First layer 1 -> 64 (+bias, ReLU) from the FP32 image into the BF16
-// channel-group-planar layout; padding columns are written as zeros.
+// channel-group-planar layout; padding columns are written as zeros. One
+// pixel per thread; the weights are a by-value kernel parameter, so every FMA
+// reads its weight as a constant-bank operand (no load instruction). A warp's
+// store to one channel-group plane is 512 contiguous bytes.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_first_bf16(const float* __restrict__ x,
-                                                    const float* __restrict__ w,   // [9][64]
-                                                    const float* __restrict__ bias, int ny,
+                                                    const __grid_constant__ EdgeW W, int ny,
                                                     int nx, int nxp,
                                                     const Rect* __restrict__ rects,
                                                     __nv_bfloat16* __restrict__ out) {
-    __shared__ float ws[9 * 64 + 64];
-    for (int e = threadIdx.x; e < 9 * 64; e += blockDim.x) ws[e] = w[e];
-    for (int e = threadIdx.x; e < 64; e += blockDim.x) ws[9 * 64 + e] = bias[e];
-    __syncthreads();
     const int xx = blockIdx.x * blockDim.x + threadIdx.x;
     const int yy = blockIdx.y, img = blockIdx.z;
     if (xx >= nxp) return;
@@ -277,9 +350,8 @@ __global__ void __launch_bounds__(128) k_first_bf16(const float* __restrict__ x,
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
         const int sy = yy + t / 3 - 1, sx = xx + t % 3 - 1;
-        v[t] = (valid && sy >= 0 && sy < ny && sx >= 0 && sx < nx)
-                   ? __ldg(x + img * plane + (int64_t)sy * nx + sx)
-                   : 0.f;
+        v[t] = (sy >= 0 && sy < ny && sx >= 0 && sx < nx) ? __ldg(x + img * plane + (int64_t)sy * nx + sx)
+                                                          : 0.f;
     }
     __nv_bfloat16* o = out + ((((int64_t)img * ny + yy) * 8) * nxp + xx) * 8;
 #pragma unroll
@@ -291,9 +363,9 @@ __global__ void __launch_bounds__(128) k_first_bf16(const float* __restrict__ x,
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int co = cg * 8 + 2 * e + h;
-                float s = ws[9 * 64 + co];
+                float s = W.b[co];
 #pragma unroll
-                for (int t = 0; t < 9; ++t) s = fmaf(ws[t * 64 + co], v[t], s);
+                for (int t = 0; t < 9; ++t) s = fmaf(W.w[t][co], v[t], s);
                 r2[h] = valid ? fmaxf(s, 0.f) : 0.f;
             }
             __nv_bfloat162 h2 = __floats2bfloat162_rn(r2[0], r2[1]);
@@ -304,40 +376,57 @@ __global__ void __launch_bounds__(128) k_first_bf16(const float* __restrict__ x,
 }
 
 // ---------------------------------------------------------------------------
-// Last layer 64 -> 1 (no ReLU) fused with the residual d = x - G(x).
+// Last layer 64 -> 1 (no ReLU) fused with the residual d = x - G(x). Each
+// thread computes 4 consecutive pixels: it reads the 3 x 6 neighbourhood of
+// 64-channel vectors once (16-byte loads through L1) and reuses every vector
+// for all pixels it touches; weights are constant-bank operands.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_last_bf16(const __nv_bfloat16* __restrict__ act,
-                                                   const float* __restrict__ w,   // [9][64]
-                                                   const float* __restrict__ bias,
+                                                   const __grid_constant__ EdgeW W,
                                                    const float* __restrict__ x, int ny, int nx,
                                                    int nxp, float* __restrict__ d) {
-    __shared__ float ws[9 * 64];
-    for (int e = threadIdx.x; e < 9 * 64; e += blockDim.x) ws[e] = w[e];
-    __syncthreads();
-    const int xx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     const int yy = blockIdx.y, img = blockIdx.z;
-    if (xx >= nx) return;
-    float acc = 0.f;
-#pragma unroll 1
-    for (int t = 0; t < 9; ++t) {
-        const int sy = yy + t / 3 - 1, sx = xx + t % 3 - 1;
-        if (sy < 0 || sy >= ny || sx < 0 || sx >= nx) continue;
-        const __nv_bfloat16* p = act + ((((int64_t)img * ny + sy) * 8) * nxp + sx) * 8;
+    if (x0 >= nx) return;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) {
+        const int sy = yy + dy - 1;
+        if (sy < 0 || sy >= ny) continue;
+        const __nv_bfloat16* rowp = act + (((int64_t)img * ny + sy) * 8) * nxp * 8;
 #pragma unroll
         for (int cg = 0; cg < 8; ++cg) {
-            const uint4 q = __ldg(reinterpret_cast<const uint4*>(p + (int64_t)cg * nxp * 8));
-            const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&wd[e]);
-                const float2 f = __bfloat1622float2(h2);
-                acc = fmaf(ws[t * 64 + cg * 8 + 2 * e], f.x, acc);
-                acc = fmaf(ws[t * 64 + cg * 8 + 2 * e + 1], f.y, acc);
+            for (int q = 0; q < 6; ++q) {
+                const int sx = x0 + q - 1;
+                if (sx < 0 || sx >= nxp) continue;
+                const uint4 raw = __ldg(reinterpret_cast<const uint4*>(rowp + ((int64_t)cg * nxp + sx) * 8));
+                const uint32_t wd[4] = {raw.x, raw.y, raw.z, raw.w};
+                float f[8];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float2 t2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wd[e]));
+                    f[2 * e] = t2.x;
+                    f[2 * e + 1] = t2.y;
+                }
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const int dx = q - p;   // pixel x0+p reads column x0+p+dx-1
+                    if (dx < 0 || dx > 2) continue;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) acc[p] = fmaf(W.w[dy * 3 + dx][cg * 8 + e], f[e], acc[p]);
+                }
             }
         }
     }
-    const int64_t n = (int64_t)img * ny * nx + (int64_t)yy * nx + xx;
-    d[n] = x[n] - (acc + __ldg(bias));
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int xx = x0 + p;
+        if (xx < nx) {
+            const int64_t n = (int64_t)img * ny * nx + (int64_t)yy * nx + xx;
+            d[n] = x[n] - (acc[p] + W.b[0]);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -361,30 +450,42 @@ static PFN_encodeTiled get_encode() {
     return fn;
 }
 
-static inline int pad8(int n) { return (n + 7) & ~7; }
+int bf16_pad_width(int nx) { return (nx + 7) & ~7; }
 
 size_t denoise_bf16_scratch(const DenoiserDev& D, int ny, int nx, int nimg) {
     (void)D;
-    return 2 * (size_t)nimg * ny * pad8(nx) * 64 * sizeof(__nv_bfloat16) + 256;
+    return 2 * (size_t)nimg * ny * bf16_pad_width(nx) * 64 * sizeof(__nv_bfloat16) + 256;
 }
 
-static cudaError_t make_act_map(CUtensorMap* m, void* base, int ny, int nxp, int nimg) {
+cudaError_t tc_make_job(TcJob* J, const __nv_bfloat16* in, __nv_bfloat16* out, int ny, int nx,
+                        int nimg, const Rect* rects, int64_t row_begin) {
     PFN_encodeTiled enc = get_encode();
     if (!enc) return cudaErrorNotSupported;
+    memset(J, 0, sizeof(*J));
+    const int nxp = bf16_pad_width(nx);
     const cuuint64_t dims[5] = {64, (cuuint64_t)nxp / 8, 8, (cuuint64_t)ny, (cuuint64_t)nimg};
     const cuuint64_t strides[4] = {128, (cuuint64_t)nxp * 16, (cuuint64_t)nxp * 128,
                                    (cuuint64_t)nxp * 128 * ny};
     const cuuint32_t box[5] = {64, tc::ROW_PX / 8, 8, 1, 1};
     const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, strides, box, es,
+    CUresult r = enc(&J->tin, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)in, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    J->out = out;
+    J->rects = rects;
+    J->ny = ny;
+    J->nx = nx;
+    J->nxp = nxp;
+    J->nimg = nimg;
+    J->strips = ceil_div(nx, tc::SEG);
+    J->row_begin = row_begin;
+    J->rows = (int64_t)nimg * J->strips * ny;
+    return cudaSuccess;
 }
 
-cudaError_t conv_tc_layer(const __nv_bfloat16* in, const __nv_bfloat16* wblob, const float* bias,
-                          int ny, int nx, int nimg, const Rect* rects, __nv_bfloat16* out,
-                          int* err, cudaStream_t s) {
+cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64_t total_rows,
+                      const __nv_bfloat16* wblob, const float* bias, int* err, cudaStream_t s) {
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -392,42 +493,59 @@ cudaError_t conv_tc_layer(const __nv_bfloat16* in, const __nv_bfloat16* wblob, c
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const int nxp = pad8(nx);
-    CUtensorMap m;
-    cudaError_t e = make_act_map(&m, (void*)in, ny, nxp, nimg);
-    if (e != cudaSuccess) return e;
-    TcConvArgs a;
-    a.wblob = wblob;
-    a.bias = bias;
-    a.out = out;
-    a.rects = rects;
-    a.err = err;
-    a.ny = ny;
-    a.nx = nx;
-    a.nxp = nxp;
-    a.nimg = nimg;
-    a.strips = ceil_div(nx, tc::SEG);
-    a.total_rows = (int64_t)nimg * a.strips * ny;
-    const int grid = (int)std::min<int64_t>(num_sms(), a.total_rows);
+    if (total_rows <= 0) return cudaSuccess;
+    TcCommon c;
+    c.wblob = wblob;
+    c.bias = bias;
+    c.err = err;
+    c.jobs = jobs_dev;
+    c.njobs = jobs_dev ? njobs : 1;
+    c.total_rows = total_rows;
+    const int grid = (int)std::min<int64_t>(num_sms(), total_rows);
     timer_begin(T_CONV_TC, s);
-    k_conv_tc<<<grid, tc::THREADS, tc::SMEM, s>>>(m, a);
+    k_conv_tc<<<grid, tc::THREADS, tc::SMEM, s>>>(job0, c);
     timer_end(T_CONV_TC, s);
+    return cudaGetLastError();
+}
+
+cudaError_t conv_tc_layer(const __nv_bfloat16* in, const __nv_bfloat16* wblob, const float* bias,
+                          int ny, int nx, int nimg, const Rect* rects, __nv_bfloat16* out,
+                          int* err, cudaStream_t s) {
+    TcJob J;
+    cudaError_t e = tc_make_job(&J, in, out, ny, nx, nimg, rects, 0);
+    if (e != cudaSuccess) return e;
+    return tc_launch(J, nullptr, 1, J.rows, wblob, bias, err, s);
+}
+
+cudaError_t first_layer_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
+                             const Rect* rects, __nv_bfloat16* out, cudaStream_t s) {
+    const int nxp = bf16_pad_width(nx);
+    dim3 g1(ceil_div(nxp, 128), ny, nimg);
+    timer_begin(T_CONV_EDGE, s);
+    k_first_bf16<<<g1, 128, 0, s>>>(x, *D.h_first, ny, nx, nxp, rects, out);
+    timer_end(T_CONV_EDGE, s);
+    return cudaGetLastError();
+}
+
+cudaError_t last_layer_bf16(const DenoiserDev& D, const __nv_bfloat16* act, const float* x,
+                            int ny, int nx, int nimg, float* d, cudaStream_t s) {
+    const int nxp = bf16_pad_width(nx);
+    dim3 g2(ceil_div(nx, 4 * 128), ny, nimg);
+    timer_begin(T_CONV_EDGE, s);
+    k_last_bf16<<<g2, 128, 0, s>>>(act, *D.h_last, x, ny, nx, nxp, d);
+    timer_end(T_CONV_EDGE, s);
     return cudaGetLastError();
 }
 
 cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
                          const Rect* rects, float* d, void* scratch, cudaStream_t s) {
-    if (D.F != 64 || !D.wtc) return cudaErrorInvalidValue;
-    const int nxp = pad8(nx);
+    if (D.F != 64 || !D.wtc || !D.h_first || !D.h_last) return cudaErrorInvalidValue;
+    const int nxp = bf16_pad_width(nx);
     const size_t act = (size_t)nimg * ny * nxp * 64;
     __nv_bfloat16* A = (__nv_bfloat16*)scratch;
     __nv_bfloat16* B = A + act;
     int* err = (int*)(B + act);
-    dim3 g1(ceil_div(nxp, 128), ny, nimg);
-    timer_begin(T_CONV_EDGE, s);
-    k_first_bf16<<<g1, 128, 0, s>>>(x, D.wfirst, D.b32 + D.b_off[0], ny, nx, nxp, rects, A);
-    timer_end(T_CONV_EDGE, s);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = first_layer_bf16(D, x, ny, nx, nimg, rects, A, s);
     if (e != cudaSuccess) return e;
     for (int k = 1; k < D.K - 1; ++k) {
         e = conv_tc_layer(A, D.wtc + (size_t)(k - 1) * (tc::W_BYTES / 2), D.b32 + D.b_off[k], ny,
@@ -435,11 +553,7 @@ cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, i
         if (e != cudaSuccess) return e;
         __nv_bfloat16* t = A; A = B; B = t;
     }
-    dim3 g2(ceil_div(nx, 128), ny, nimg);
-    timer_begin(T_CONV_EDGE, s);
-    k_last_bf16<<<g2, 128, 0, s>>>(A, D.wlast, D.b32 + D.b_off[D.K - 1], x, ny, nx, nxp, d);
-    timer_end(T_CONV_EDGE, s);
-    return cudaGetLastError();
+    return last_layer_bf16(D, A, x, ny, nx, nimg, d, s);
 }
 
 }  // namespace pnp

@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libpnp.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -48,6 +49,13 @@ struct Rect {
     int y0, y1, x0, x1;
 };
 
+// First / last layer weights of the BF16 path, passed by value as kernel
+// parameters so that the FMAs read them as constant-bank operands.
+struct EdgeW {
+    float w[9][64];   // [tap][channel]: first layer = output channel, last = input channel
+    float b[64];      // first layer: per output channel; last layer: b[0]
+};
+
 // --------------------------------------------------------------------------
 // Denoiser parameters on the device.
 // --------------------------------------------------------------------------
@@ -59,8 +67,10 @@ struct DenoiserDev {
     float* b32 = nullptr;
     int64_t* w32_off = nullptr;   // host offsets per layer
     int64_t* b_off = nullptr;
-    // BF16 tensor-core layout of the F->F layers: per layer 9 taps x [8 cg][F co][8 ci]
+    // BF16 tensor-core layout of the F->F layers: per layer [dx 3][cg 8][dy 3 x co 64][8 ci]
     __nv_bfloat16* wtc = nullptr;
+    EdgeW* h_first = nullptr;   // host copies for the BF16 edge layers
+    EdgeW* h_last = nullptr;
     // FP32 first/last layer weights in tap-major order for the BF16 path
     float* wfirst = nullptr;  // [9][F]
     float* wlast = nullptr;   // [9][F]
@@ -118,6 +128,28 @@ cudaError_t launch_finalize_moments(const float* mean, const float* m2, int64_t 
 cudaError_t denoise_fp32(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
                          const Rect* rects, float* d, float* scratch, cudaStream_t s);
 size_t denoise_fp32_scratch(const DenoiserDev& D, int ny, int nx, int nimg);
+
+// One job of a tensor-core conv launch: the images of one size that share a
+// tensor map (input activations) and an output plane; row_begin/rows place
+// the job in the launch's concatenated row stream.
+struct TcJob {   // 256 B, 128-B aligned (the tensor map requires it)
+    CUtensorMap tin;
+    __nv_bfloat16* out;
+    const Rect* rects;
+    int64_t row_begin;
+    int64_t rows;
+    int ny, nx, nxp, strips, nimg, pad0, pad1, pad2;
+};
+int bf16_pad_width(int nx);
+cudaError_t tc_make_job(TcJob* J, const __nv_bfloat16* in, __nv_bfloat16* out, int ny, int nx,
+                        int nimg, const Rect* rects, int64_t row_begin);
+// jobs_dev == nullptr: run job0 alone (passed by value); else the device table.
+cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64_t total_rows,
+                      const __nv_bfloat16* wblob, const float* bias, int* err, cudaStream_t s);
+cudaError_t first_layer_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
+                             const Rect* rects, __nv_bfloat16* out, cudaStream_t s);
+cudaError_t last_layer_bf16(const DenoiserDev& D, const __nv_bfloat16* act, const float* x,
+                            int ny, int nx, int nimg, float* d, cudaStream_t s);
 
 // BF16 tcgen05 denoiser (F = 64). scratch must hold denoise_bf16_scratch() bytes.
 cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
