@@ -67,7 +67,7 @@ void timer_end(int id, cudaStream_t s) {
     ++t.used;
 }
 
-cudaError_t conv_tc_layer(const __nv_bfloat16* in, const __nv_bfloat16* wblob, const float* bias,
+cudaError_t conv_tc_layer(const __nv_bfloat16* in, const __nv_bfloat16* wblob, const float* bias_host,
                           int ny, int nx, int nimg, const Rect* rects, __nv_bfloat16* out,
                           int* err, cudaStream_t s);
 

@@ -15,16 +15,17 @@
 //
 // The GEMM is organised around input rows: input row i at column shift dx
 // (M = 128 pixels, K = 16 channels per MMA) is multiplied by the stacked
-// weights [W(dy=0,dx); W(dy=1,dx); W(dy=2,dx)] (N = 3 x 64), which adds its
-// contribution to output rows i+1, i and i-1 in one MMA. The output rows'
-// FP32 accumulators sit in adjacent 64-column TMEM slots (slot of output row
-// q = -q mod 8), so per input row 12 MMAs of 128 x 192 x 16 run (split in two
-// where the slot ring wraps) instead of 36 of 128 x 64 x 16, which the tensor
-// core executes at only ~60 % of its rate. Accumulators always accumulate;
-// the epilogue zeroes a slot right after draining it. Warp roles: warp 0 =
-// TMA producer, warp 1 = MMA issuer, warps 2-5 = epilogue (TMEM -> registers,
-// bias, ReLU, zero outside the valid rect, BF16, global store). Input rows
-// circulate through a 6-slot shared-memory ring.
+// weights [W(dy=0,dx); W(dy=1,dx); W(dy=2,dx)] (N = 3 x 64): 12 MMAs of
+// 128 x 192 x 16 give P_i = (P_i^0, P_i^1, P_i^2), the row's contributions to
+// output rows i+1, i and i-1. (A 128 x 64 x 16 MMA runs at only ~60 % of the
+// tensor rate; N = 192 runs at the full rate.) P_i goes to one of two fixed,
+// non-overlapping 192-column TMEM regions (alternating per input row: MMAs
+// whose accumulator ranges partially overlap the previous row's run ~40 %
+// slower). The epilogue sums output row r = P_{r-1}^0 + P_r^1 + P_{r+1}^2 in
+// registers, two partial rows at a time. Warp roles: warp 0 = TMA producer,
+// warp 1 = MMA issuer, warps 2-5 = epilogue (TMEM -> registers, sum, bias,
+// ReLU, zero outside the valid rect, BF16, global store). Input rows
+// circulate through an 8-slot shared-memory ring.
 //
 // One launch covers a table of jobs (images of possibly different sizes,
 // each with its own tensor map): every CTA walks a contiguous range of the
@@ -47,9 +48,9 @@ constexpr int HALO_PX = 8;                  // smem row starts 8 px left of the 
 constexpr int ROW_PX = SEG + 2 * HALO_PX;   // 144
 constexpr int CG_BYTES = ROW_PX * 16;       // 2304: one channel-group plane of a row
 constexpr int ROW_BYTES = 8 * CG_BYTES;     // 18432
-constexpr int NS = 6;                       // input-row ring slots
-constexpr int NACC = 8;                     // TMEM accumulator slots (64 columns each)
-constexpr int TMEM_COLS = NACC * F;         // 512
+constexpr int NS = 8;                       // input-row ring slots
+constexpr int NACC = 2;                     // TMEM regions of 192 columns (double buffer)
+constexpr int TMEM_COLS = 512;              // allocation (power of two >= 2 x 192)
 constexpr int NB = 3 * F;                   // stacked rows of one column shift (dy, co)
 constexpr int DX_W_BYTES = 8 * NB * 16;     // 24576: [cg][dy*64+co][8 ci] of one dx
 constexpr int W_BYTES = 3 * DX_W_BYTES;     // 73728
@@ -61,8 +62,6 @@ constexpr int OFF_BAR = OFF_BIAS + F * 4;
 constexpr int NBAR = 2 * NS + 1 + 2 * NACC + 1;   // full, empty, weights, tfull, tempty, drain
 constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
 constexpr int SMEM = OFF_MISC + 16 + 1024;        // + alignment slack
-constexpr uint32_t IDESC64 = ptx::idesc_bf16_f32(SEG, 64);
-constexpr uint32_t IDESC128 = ptx::idesc_bf16_f32(SEG, 128);
 constexpr uint32_t IDESC192 = ptx::idesc_bf16_f32(SEG, 192);
 constexpr long long BUDGET = 4000000000LL;        // ~2 s of SM clock per wait
 // descriptor words (no swizzle, K-major): low = start>>4 | (LBO>>4)<<16,
@@ -79,7 +78,7 @@ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ?
 
 struct TcCommon {
     const __nv_bfloat16* wblob;   // [3 dx][8 cg][3 dy x 64 co][8 ci]
-    const float* bias;            // [64]
+    float bias[64];               // by value: constant-bank operands in the epilogue
     int* err;
     const TcJob* jobs;            // device table, or nullptr: the single job parameter
     int njobs;
@@ -112,20 +111,38 @@ __device__ __forceinline__ RowPos locate(const TcJob& job0, const TcCommon& c, i
     return p;
 }
 
-// D[tmem] += A * B with both descriptors given by their low words (the high
-// words are the same constant); always accumulates.
-__device__ __forceinline__ void mma_acc(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo,
-                                        uint32_t idesc) {
+// D[tmem] (+)= A * B with both descriptors given by their low words (the
+// high words are the same constant).
+__device__ __forceinline__ void mma_lo(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo,
+                                       uint32_t idesc, uint32_t accumulate) {
     asm volatile(
-        "{\n.reg .b64 da, db;\n"
+        "{\n.reg .b64 da, db;\n.reg .pred p;\n"
         "mov.b64 da, {%1, %2};\n"
         "mov.b64 db, {%3, %2};\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, 1;\n}\n" ::"r"(d_tmem),
-        "r"(a_lo), "r"(tc::DESC_HI), "r"(b_lo), "r"(idesc)
+        "setp.ne.b32 p, %5, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_lo), "r"(tc::DESC_HI), "r"(b_lo), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
-__device__ __forceinline__ uint32_t slot_of(uint32_t q) { return (tc::NACC - (q % tc::NACC)) % tc::NACC; }
+// Epilogue helpers. TMEM column block `col` (64 columns) of this warp's lanes.
+__device__ __forceinline__ void tm_add64(uint32_t taddr, float* acc) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t t[16];
+        ptx::tmem_ld_32x32b_x16(taddr + q * 16, t);
+        ptx::tmem_ld_wait();
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[q * 16 + e] += __uint_as_float(t[e]);
+    }
+}
+__device__ __forceinline__ void tm_load64(uint32_t taddr, float* acc) {
+    uint32_t t[64];
+    ptx::tmem_ld_32x32b_x64(taddr, t);
+    ptx::tmem_ld_wait();
+#pragma unroll
+    for (int e = 0; e < 64; ++e) acc[e] = __uint_as_float(t[e]);
+}
 
 __global__ void __launch_bounds__(tc::THREADS, 1)
     k_conv_tc(const __grid_constant__ TcJob job0, const TcCommon c) {
@@ -134,7 +151,6 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* ring = smem + OFF_RING;
     uint8_t* wsm = smem + OFF_W;
-    float* bias_s = (float*)(smem + OFF_BIAS);
     uint64_t* bars = (uint64_t*)(smem + OFF_BAR);
     uint64_t* full = bars;
     uint64_t* empty = bars + NS;
@@ -165,21 +181,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         ptx::tmem_alloc(tmem_slot, TMEM_COLS);
         ptx::tmem_relinquish();
     }
-    if (threadIdx.x >= 64 && threadIdx.x < 64 + F) bias_s[threadIdx.x - 64] = c.bias[threadIdx.x - 64];
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    // accumulators always accumulate: start every slot at zero
-    if (warp >= 2) {
-        const uint32_t lane_base = tmem_base + ((uint32_t)((warp & 3) * 32) << 16);
-#pragma unroll 1
-        for (int sl = 0; sl < NACC; ++sl) ptx::tmem_st_zero_32x32b_x64(lane_base + sl * F);
-        ptx::tmem_st_wait();
-    }
-    ptx::tc_fence_before();
-    __syncthreads();
-    ptx::tc_fence_after();
 
     // this CTA's share of the concatenated row stream
     const int64_t g_begin = c.total_rows * blockIdx.x / gridDim.x;
@@ -214,54 +219,35 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---------------- MMA issuer: one batch of MMAs per input row
+            // ---------------- MMA issuer: 12 MMAs (N = 192) per input row
             bool ok = ptx::mbar_wait(wbar, 0, abort_flag, BUDGET);
             const uint32_t ring_lo = (ptx::smem_u32(ring) >> 4) | A_LBO_FIELD;
             const uint32_t w_lo = (ptx::smem_u32(wsm) >> 4) | B_LBO_FIELD;
-            uint32_t L = 0, Q = 0;
+            uint32_t L = 0;
             bool issued = false;
             int j = 0;
             for (int64_t g = g_begin; g < g_end && ok;) {
                 const RowPos p = locate(job0, c, j, g, g_end);
-                const int len = p.len;
-                // input rows y-1 .. y+len, ri = input row - y
-                for (int ri = -1; ri <= len && ok; ++ri) {
-                    const uint32_t Lc = L + (uint32_t)(ri + 1);
-                    ok = ptx::mbar_wait(&full[Lc % NS], (Lc / NS) & 1, abort_flag, BUDGET);
-                    // kernel rows dy contribute to output row ri+1-dy; keep those inside the item
-                    const int dy_lo = ri <= len - 2 ? 0 : (ri <= len - 1 ? 1 : 2);
-                    const int dy_hi = ri >= 1 ? 2 : (ri >= 0 ? 1 : 0);
-                    const uint32_t q_lo = Q + (uint32_t)(ri + 1 - dy_lo);   // output row of dy_lo
-                    if (ok && dy_lo == 0)   // first contribution to a new output row: claim its slot
-                        ok = ptx::mbar_wait(&tempty[slot_of(q_lo)], ((q_lo / NACC) & 1) ^ 1,
-                                            abort_flag, BUDGET);
+                for (int ri = -1; ri <= p.len && ok; ++ri, ++L) {
+                    const uint32_t reg = L & 1, u = L >> 1;
+                    ok = ptx::mbar_wait(&full[L % NS], (L / NS) & 1, abort_flag, BUDGET);
+                    if (ok) ok = ptx::mbar_wait(&tempty[reg], (u & 1) ^ 1, abort_flag, BUDGET);
                     if (!ok) break;
                     ptx::tc_fence_after();
-                    const uint32_t s_lo = slot_of(q_lo);
-                    const int n = dy_hi - dy_lo + 1;
-                    const int n1 = min(n, NACC - (int)s_lo);   // run up to the end of the ring
-                    const uint32_t id1 = n1 == 3 ? IDESC192 : (n1 == 2 ? IDESC128 : IDESC64);
-                    const uint32_t id2 = (n - n1) == 2 ? IDESC128 : IDESC64;
-                    const uint32_t a_row = ring_lo + (Lc % NS) * (ROW_BYTES >> 4);
-                    const uint32_t b1 = w_lo + (uint32_t)dy_lo * (F * 16 >> 4);
-                    const uint32_t b2 = b1 + (uint32_t)n1 * (F * 16 >> 4);
-                    const uint32_t d1 = tmem_base + s_lo * F;
+                    const uint32_t a_row = ring_lo + (L % NS) * (ROW_BYTES >> 4);
+                    const uint32_t d = tmem_base + reg * NB;
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const uint32_t a_lo = a_row + kk * 2 * (CG_BYTES >> 4) + (HALO_PX - 1 + dx);
-                            const uint32_t boff = dx * (DX_W_BYTES >> 4) + kk * 2 * (NB * 16 >> 4);
-                            mma_acc(d1, a_lo, b1 + boff, id1);
-                            if (n1 < n) mma_acc(tmem_base, a_lo, b2 + boff, id2);
-                        }
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_lo(d, a_row + kk * 2 * (CG_BYTES >> 4) + (HALO_PX - 1 + dx),
+                                   w_lo + dx * (DX_W_BYTES >> 4) + kk * 2 * (NB * 16 >> 4), IDESC192,
+                                   (dx | kk) != 0);
                     issued = true;
-                    ptx::mma_commit(&empty[Lc % NS]);          // input row fully consumed
-                    if (dy_hi == 2) ptx::mma_commit(&tfull[slot_of(Q + (uint32_t)(ri - 1))]);
+                    ptx::mma_commit(&empty[L % NS]);   // input row consumed
+                    ptx::mma_commit(&tfull[reg]);      // P_i ready
                 }
-                L += (uint32_t)(len + 2);
-                Q += (uint32_t)len;
-                g += len;
+                g += p.len;
             }
             if (issued) {
                 ptx::mma_commit(drain);
@@ -273,47 +259,59 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         const int quad = warp & 3;
         const int jx = quad * 32 + lane;
         const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
-        uint32_t Q = 0;
+        uint32_t L = 0;
         bool ok = true;
         int j = 0;
+        float X0[64], X1[64];   // partial sums of the output rows of even / odd index
         for (int64_t g = g_begin; g < g_end && ok;) {
             const RowPos p = locate(job0, c, j, g, g_end);
             const TcJob* J = p.J;
             const Rect rc = J->rects ? J->rects[p.img] : Rect{0, J->ny, 0, J->nx};
             const int x = p.strip * SEG + jx;
             const int nxp = J->nxp;
-            for (int k = 0; k < p.len; ++k, ++Q) {
-                const uint32_t sl = slot_of(Q);
-                if (!ptx::mbar_wait(&tfull[sl], (Q / NACC) & 1, abort_flag, BUDGET)) { ok = false; break; }
+            const bool col_ok = x < nxp;
+            const bool x_valid = x < J->nx && x >= rc.x0 && x < rc.x1;
+            __nv_bfloat16* obase = J->out + ((((int64_t)p.img * J->ny) * 8) * nxp + x) * 8;
+            auto store_row = [&](const float* acc, int yy) {
+                if (!col_ok) return;
+                const bool valid = x_valid && yy >= rc.y0 && yy < rc.y1;
+                __nv_bfloat16* o = obase + (int64_t)yy * 8 * nxp * 8;
+#pragma unroll
+                for (int cg = 0; cg < 8; ++cg) {
+                    uint32_t pk[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int c0 = cg * 8 + 2 * e;
+                        float v0 = fmaxf(acc[c0] + c.bias[c0], 0.f);
+                        float v1 = fmaxf(acc[c0 + 1] + c.bias[c0 + 1], 0.f);
+                        if (!valid) v0 = v1 = 0.f;
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+                        pk[e] = *reinterpret_cast<uint32_t*>(&h2);
+                    }
+                    *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                }
+            };
+            // input row ri adds P^2 to output row ri-1 (then complete), P^1 to
+            // output row ri, and starts output row ri+1 with P^0
+            auto step = [&](float* Xprev, float* Xcur, int ri, uint32_t taddr) {
+                if (ri >= 1) {
+                    tm_add64(taddr + 2 * F, Xprev);
+                    store_row(Xprev, p.y + ri - 1);
+                }
+                if (ri >= 0 && ri < p.len) tm_add64(taddr + F, Xcur);
+                if (ri + 1 < p.len) tm_load64(taddr, Xprev);
+            };
+            for (int ri = -1; ri <= p.len; ++ri, ++L) {
+                const uint32_t reg = L & 1, u = L >> 1;
+                if (!ptx::mbar_wait(&tfull[reg], u & 1, abort_flag, BUDGET)) { ok = false; break; }
                 ptx::tc_fence_after();
-                uint32_t r[64];
-                ptx::tmem_ld_32x32b_x64(lane_base + sl * F, r);
-                ptx::tmem_ld_wait();
-                ptx::tmem_st_zero_32x32b_x64(lane_base + sl * F);
-                ptx::tmem_st_wait();
+                const uint32_t taddr = lane_base + reg * NB;
+                // output row k lives in X[k & 1]: prev = X[(ri-1) & 1], cur = X[ri & 1]
+                if ((ri + 1) & 1) step(X1, X0, ri, taddr);
+                else step(X0, X1, ri, taddr);
                 ptx::tc_fence_before();
                 __syncwarp();
-                if (lane == 0) ptx::mbar_arrive(&tempty[sl]);
-                const int yy = p.y + k;
-                if (x < nxp) {
-                    const bool valid = x < J->nx && yy >= rc.y0 && yy < rc.y1 && x >= rc.x0 && x < rc.x1;
-                    __nv_bfloat16* o = J->out + ((((int64_t)p.img * J->ny + yy) * 8) * nxp + x) * 8;
-#pragma unroll
-                    for (int cg = 0; cg < 8; ++cg) {
-                        uint32_t pk[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int c0 = cg * 8 + 2 * e;
-                            float v0 = fmaxf(__uint_as_float(r[c0]) + bias_s[c0], 0.f);
-                            float v1 = fmaxf(__uint_as_float(r[c0 + 1]) + bias_s[c0 + 1], 0.f);
-                            if (!valid) v0 = v1 = 0.f;
-                            __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
-                            pk[e] = *reinterpret_cast<uint32_t*>(&h2);
-                        }
-                        *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 8) =
-                            make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                    }
-                }
+                if (lane == 0) ptx::mbar_arrive(&tempty[reg]);
             }
             g += p.len;
         }
@@ -485,7 +483,8 @@ cudaError_t tc_make_job(TcJob* J, const __nv_bfloat16* in, __nv_bfloat16* out, i
 }
 
 cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64_t total_rows,
-                      const __nv_bfloat16* wblob, const float* bias, int* err, cudaStream_t s) {
+                      const __nv_bfloat16* wblob, const float* bias_host, int* err, cudaStream_t s) {
+    const float* bias = bias_host;   // 64 floats in host memory, copied into the launch
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -496,7 +495,7 @@ cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64
     if (total_rows <= 0) return cudaSuccess;
     TcCommon c;
     c.wblob = wblob;
-    c.bias = bias;
+    memcpy(c.bias, bias, sizeof(c.bias));
     c.err = err;
     c.jobs = jobs_dev;
     c.njobs = jobs_dev ? njobs : 1;
@@ -508,13 +507,13 @@ cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64
     return cudaGetLastError();
 }
 
-cudaError_t conv_tc_layer(const __nv_bfloat16* in, const __nv_bfloat16* wblob, const float* bias,
+cudaError_t conv_tc_layer(const __nv_bfloat16* in, const __nv_bfloat16* wblob, const float* bias_host,
                           int ny, int nx, int nimg, const Rect* rects, __nv_bfloat16* out,
                           int* err, cudaStream_t s) {
     TcJob J;
     cudaError_t e = tc_make_job(&J, in, out, ny, nx, nimg, rects, 0);
     if (e != cudaSuccess) return e;
-    return tc_launch(J, nullptr, 1, J.rows, wblob, bias, err, s);
+    return tc_launch(J, nullptr, 1, J.rows, wblob, bias_host, err, s);
 }
 
 cudaError_t first_layer_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
@@ -548,7 +547,8 @@ cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, i
     cudaError_t e = first_layer_bf16(D, x, ny, nx, nimg, rects, A, s);
     if (e != cudaSuccess) return e;
     for (int k = 1; k < D.K - 1; ++k) {
-        e = conv_tc_layer(A, D.wtc + (size_t)(k - 1) * (tc::W_BYTES / 2), D.b32 + D.b_off[k], ny,
+        // host copy of the layer's biases (layers before k all have 64 outputs)
+        e = conv_tc_layer(A, D.wtc + (size_t)(k - 1) * (tc::W_BYTES / 2), D.hb + 64 * k, ny,
                           nx, nimg, rects, B, err, s);
         if (e != cudaSuccess) return e;
         __nv_bfloat16* t = A; A = B; B = t;

@@ -8,7 +8,7 @@
 
 #include <string>
 
-#include "../../include/pnp.h"
+#include "pnp.h"
 
 namespace pnp {
 
@@ -144,8 +144,9 @@ int bf16_pad_width(int nx);
 cudaError_t tc_make_job(TcJob* J, const __nv_bfloat16* in, __nv_bfloat16* out, int ny, int nx,
                         int nimg, const Rect* rects, int64_t row_begin);
 // jobs_dev == nullptr: run job0 alone (passed by value); else the device table.
+// bias_host: the layer's 64 biases in host memory (passed by value to the kernel).
 cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64_t total_rows,
-                      const __nv_bfloat16* wblob, const float* bias, int* err, cudaStream_t s);
+                      const __nv_bfloat16* wblob, const float* bias_host, int* err, cudaStream_t s);
 cudaError_t first_layer_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
                              const Rect* rects, __nv_bfloat16* out, cudaStream_t s);
 cudaError_t last_layer_bf16(const DenoiserDev& D, const __nv_bfloat16* act, const float* x,
