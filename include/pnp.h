@@ -212,6 +212,59 @@ float* pnp_problem_x_device(pnp_problem* p);
 pnp_status pnp_set_graph_mode(int enable);
 
 /* ------------------------------------------------------------------------
+ * Batch: independent problems of different sizes stepped together (all with
+ * the same denoiser and precision, halo = 0). One batch iteration = one
+ * iteration of every job; the denoiser's tensor-core layers run as one launch
+ * per layer over the rows of all jobs, and the iteration is replayed as one
+ * CUDA graph. Each job's chain is identical to the same problem run alone
+ * (Algorithm 1 applied to each posterior independently).
+ * ------------------------------------------------------------------------ */
+pnp_status pnp_batch_create(const pnp_problem_desc* descs, int njobs, void* stream,
+                            pnp_batch** out);
+void pnp_batch_destroy(pnp_batch* b);
+/* Enqueue n_iters iterations of every job (asynchronous). */
+pnp_status pnp_batch_step(pnp_batch* b, int n_iters);
+/* Set every job's burn-in, run T iterations and wait. */
+pnp_status pnp_batch_run(pnp_batch* b, int T, int burn_in);
+pnp_status pnp_batch_sync(pnp_batch* b);
+/* Borrowed handle of job `job` (for pnp_get_moments / pnp_get_state); owned by the batch. */
+pnp_status pnp_batch_job(pnp_batch* b, int job, pnp_problem** p);
+int pnp_batch_size(const pnp_batch* b);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of sampling jobs. A worker thread admits
+ * queued jobs in arrival order while their device footprint (chain state,
+ * observation, denoiser scratch) fits hbm_budget_bytes, steps all admitted
+ * jobs together with the batch engine, and between rounds of a few
+ * iterations retires finished jobs: FP64 MMSE and std maps are copied to host
+ * memory and the job's device memory is freed. Jobs that arrive while others
+ * run join at the next round. Each job's chain is independent of which other
+ * jobs share its steps. All served jobs use the server's denoiser and
+ * precision; desc.halo must be 0; desc.stream is ignored. Thread-safe: submit,
+ * poll, wait and cancel may be called from any host thread.
+ * Job states: 0 queued, 1 running, 2 done, 3 failed, 4 cancelled.
+ * ------------------------------------------------------------------------ */
+pnp_status pnp_server_create(const pnp_denoiser* D, pnp_precision prec, size_t hbm_budget_bytes,
+                             void* stream, pnp_server** out);
+/* Copies the job's inputs. PNP_EBUSY if the job alone exceeds the budget. */
+pnp_status pnp_server_submit(pnp_server* s, const pnp_problem_desc* desc, int T, int burn_in,
+                             int64_t* job_id);
+/* State of a job; when done, copies MMSE / std (host [ny*nx], either may be NULL). */
+pnp_status pnp_server_poll(pnp_server* s, int64_t job_id, double* mmse, double* std, int* state);
+/* Wait up to timeout_s seconds for the job to end; PNP_ETIMEOUT if it did not. */
+pnp_status pnp_server_wait(pnp_server* s, int64_t job_id, double timeout_s, int* state);
+/* Host-side cancellation of a queued or running job; other jobs are unaffected. */
+pnp_status pnp_server_cancel(pnp_server* s, int64_t job_id);
+/* Seconds since server creation at submission, admission and completion (-1: not yet). */
+pnp_status pnp_server_job_times(pnp_server* s, int64_t job_id, double* t_submit, double* t_admit,
+                                double* t_done);
+pnp_status pnp_server_stats(pnp_server* s, int64_t* pixel_iters, int* active, int* queued,
+                            size_t* used_bytes);
+/* Iterations per round between retire/admit points (default 8). */
+pnp_status pnp_server_set_round(pnp_server* s, int iters);
+void pnp_server_destroy(pnp_server* s);
+
+/* ------------------------------------------------------------------------
  * Instrumentation: CUDA events around every launch of the hot kernels
  * ("blur", "update", "conv_fp32", "conv_tc", "conv_edge"). Enabling resets
  * the counters and forces eager launches (no graph replay). Reading

@@ -14,7 +14,7 @@ import numpy as np
 
 from ._lib import (PNP_BF16, PNP_FP8, PNP_FP32, PnpError, ProblemDesc, check, load)  # noqa: F401
 
-__all__ = ["Denoiser", "Problem", "PnpError", "load", "version"]
+__all__ = ["Denoiser", "Problem", "Batch", "Server", "PnpError", "load", "version"]
 
 PRECISIONS = {"fp32": PNP_FP32, "bf16": PNP_BF16, "fp8": PNP_FP8}
 
@@ -153,36 +153,54 @@ class Denoiser:
 
 # ------------------------------------------------------------------ problem
 
+def make_desc(y, h, sigma, denoiser=None, *, alpha=-1.0, eps=0.0, lam=0.0, gamma=0.0,
+              step_c=0.0, hnorm=0.0, blocks=(1, 1), halo=0, nchain=1, seed=0, burn_in=0,
+              precision="fp32", x0=None, stream=None):
+    """Fill a pnp_problem_desc; returns (desc, keep-alive host arrays)."""
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    h = np.ascontiguousarray(h, dtype=np.float32)
+    d = ProblemDesc()
+    d.ny, d.nx = y.shape
+    d.y = _f32p(y)
+    d.kh, d.kw = h.shape
+    d.h = _f32p(h)
+    d.sigma, d.alpha, d.eps = float(sigma), float(alpha), float(eps)
+    d.lam, d.gamma, d.step_c, d.hnorm = float(lam), float(gamma), float(step_c), float(hnorm)
+    d.blocks_y, d.blocks_x = int(blocks[0]), int(blocks[1])
+    d.halo, d.nchain, d.seed, d.burn_in = int(halo), int(nchain), int(seed), int(burn_in)
+    d.precision = _prec(precision)
+    d.D = denoiser.handle if denoiser is not None else None
+    keep = [y, h]
+    if x0 is not None:
+        x0a = np.ascontiguousarray(np.broadcast_to(x0, (nchain,) + y.shape), dtype=np.float32)
+        d.x0 = _f32p(x0a)
+        keep.append(x0a)
+    d.stream = C.c_void_p(int(stream)) if stream is not None else None
+    return d, keep
+
+
 class Problem:
     """One posterior and its chains resident on the GPU (pnp_create_problem)."""
 
-    def __init__(self, y, h, sigma, denoiser: Denoiser | None = None, *, alpha=-1.0, eps=0.0,
-                 lam=0.0, gamma=0.0, step_c=0.0, hnorm=0.0, blocks=(1, 1), halo=0, nchain=1,
-                 seed=0, burn_in=0, precision="fp32", x0=None, stream=None):
-        y = np.ascontiguousarray(y, dtype=np.float32)
-        h = np.ascontiguousarray(h, dtype=np.float32)
-        self.shape = y.shape
-        self.nchain = nchain
-        d = ProblemDesc()
-        d.ny, d.nx = y.shape
-        d.y = _f32p(y)
-        d.kh, d.kw = h.shape
-        d.h = _f32p(h)
-        d.sigma, d.alpha, d.eps = float(sigma), float(alpha), float(eps)
-        d.lam, d.gamma, d.step_c, d.hnorm = float(lam), float(gamma), float(step_c), float(hnorm)
-        d.blocks_y, d.blocks_x = int(blocks[0]), int(blocks[1])
-        d.halo, d.nchain, d.seed, d.burn_in = int(halo), int(nchain), int(seed), int(burn_in)
-        d.precision = _prec(precision)
-        d.D = denoiser.handle if denoiser is not None else None
-        x0a = None
-        if x0 is not None:
-            x0a = np.ascontiguousarray(np.broadcast_to(x0, (nchain,) + y.shape), dtype=np.float32)
-            d.x0 = _f32p(x0a)
-        d.stream = C.c_void_p(int(stream)) if stream is not None else None
+    def __init__(self, y, h, sigma, denoiser: Denoiser | None = None, **kw):
+        d, keep = make_desc(y, h, sigma, denoiser, **kw)
+        self.shape = (d.ny, d.nx)
+        self.nchain = d.nchain
         hdl = C.c_void_p()
         check(load().pnp_create_problem(C.byref(d), C.byref(hdl)))
         self.handle = hdl
+        self._owned = True
         self._denoiser = denoiser   # keep alive
+
+    @classmethod
+    def _borrow(cls, handle, shape, nchain, owner):
+        obj = cls.__new__(cls)
+        obj.handle = handle
+        obj.shape = shape
+        obj.nchain = nchain
+        obj._owned = False
+        obj._owner = owner
+        return obj
 
     def params(self):
         lam, gam, al, ep = C.c_double(), C.c_double(), C.c_double(), C.c_double()
@@ -223,8 +241,130 @@ class Problem:
         return load().pnp_problem_x_device(self.handle)
 
     def close(self):
-        if getattr(self, "handle", None):
+        if getattr(self, "handle", None) and getattr(self, "_owned", True):
             load().pnp_destroy_problem(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ batch
+
+class Batch:
+    """Independent problems stepped together (pnp_batch_create); each job is a
+    dict of make_desc keyword arguments plus y, h, sigma."""
+
+    def __init__(self, jobs, denoiser: Denoiser, precision="bf16", stream=None):
+        descs = (ProblemDesc * len(jobs))()
+        self._keep = []
+        self.shapes = []
+        for k, jb in enumerate(jobs):
+            jb = dict(jb)
+            d, keep = make_desc(jb.pop("y"), jb.pop("h"), jb.pop("sigma"), denoiser,
+                                precision=precision, **jb)
+            descs[k] = d
+            self._keep.append(keep)
+            self.shapes.append(((d.ny, d.nx), d.nchain))
+        hdl = C.c_void_p()
+        check(load().pnp_batch_create(descs, len(jobs), C.c_void_p(int(stream)) if stream else None,
+                                      C.byref(hdl)))
+        self.handle = hdl
+        self._denoiser = denoiser
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def step(self, n=1):
+        check(load().pnp_batch_step(self.handle, int(n)))
+
+    def run(self, T, burn_in):
+        check(load().pnp_batch_run(self.handle, int(T), int(burn_in)))
+
+    def sync(self):
+        check(load().pnp_batch_sync(self.handle))
+
+    def job(self, j) -> Problem:
+        h = C.c_void_p()
+        check(load().pnp_batch_job(self.handle, int(j), C.byref(h)))
+        shape, nchain = self.shapes[j]
+        return Problem._borrow(h, shape, nchain, self)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pnp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ serving
+
+JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled"}
+
+
+class Server:
+    """Continuous-batching sampler service (pnp_server_create)."""
+
+    def __init__(self, denoiser: Denoiser, precision="bf16", hbm_budget_bytes=64 << 30,
+                 stream=None, round_iters=8):
+        hdl = C.c_void_p()
+        check(load().pnp_server_create(denoiser.handle if denoiser else None, _prec(precision),
+                                       int(hbm_budget_bytes),
+                                       C.c_void_p(int(stream)) if stream else None, C.byref(hdl)))
+        self.handle = hdl
+        self._denoiser = denoiser
+        self._shapes = {}
+        check(load().pnp_server_set_round(self.handle, int(round_iters)))
+
+    def submit(self, y, h, sigma, T, burn_in, **kw):
+        d, keep = make_desc(y, h, sigma, None, burn_in=burn_in, **kw)
+        jid = C.c_int64()
+        check(load().pnp_server_submit(self.handle, C.byref(d), int(T), int(burn_in), C.byref(jid)))
+        self._shapes[jid.value] = (d.ny, d.nx)
+        return jid.value
+
+    def poll(self, job_id, fetch=True):
+        """-> (state name, mmse or None, std or None)."""
+        ny, nx = self._shapes[job_id]
+        st = C.c_int()
+        mm = np.empty((ny, nx)) if fetch else None
+        sd = np.empty((ny, nx)) if fetch else None
+        check(load().pnp_server_poll(self.handle, int(job_id),
+                                     mm.ctypes.data_as(C.POINTER(C.c_double)) if fetch else None,
+                                     sd.ctypes.data_as(C.POINTER(C.c_double)) if fetch else None,
+                                     C.byref(st)))
+        name = JOB_STATES[st.value]
+        return (name, mm, sd) if name == "done" else (name, None, None)
+
+    def wait(self, job_id, timeout=600.0):
+        st = C.c_int()
+        check(load().pnp_server_wait(self.handle, int(job_id), float(timeout), C.byref(st)))
+        return JOB_STATES[st.value]
+
+    def cancel(self, job_id):
+        check(load().pnp_server_cancel(self.handle, int(job_id)))
+
+    def times(self, job_id):
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        check(load().pnp_server_job_times(self.handle, int(job_id), C.byref(a), C.byref(b), C.byref(c)))
+        return dict(submit=a.value, admit=b.value, done=c.value)
+
+    def stats(self):
+        px, act, q, used = C.c_int64(), C.c_int(), C.c_int(), C.c_size_t()
+        check(load().pnp_server_stats(self.handle, C.byref(px), C.byref(act), C.byref(q), C.byref(used)))
+        return dict(pixel_iters=px.value, active=act.value, queued=q.value, used_bytes=used.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pnp_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

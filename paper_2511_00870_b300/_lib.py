@@ -66,6 +66,22 @@ SIGNATURES = {
     "pnp_set_state": ([vp, fp, i64], i32),
     "pnp_problem_x_device": ([vp], vp),
     "pnp_set_graph_mode": ([i32], i32),
+    "pnp_batch_create": ([C.POINTER(ProblemDesc), i32, vp, C.POINTER(vp)], i32),
+    "pnp_batch_destroy": ([vp], None),
+    "pnp_batch_step": ([vp, i32], i32),
+    "pnp_batch_run": ([vp, i32, i32], i32),
+    "pnp_batch_sync": ([vp], i32),
+    "pnp_batch_job": ([vp, i32, C.POINTER(vp)], i32),
+    "pnp_batch_size": ([vp], i32),
+    "pnp_server_create": ([vp, i32, C.c_size_t, vp, C.POINTER(vp)], i32),
+    "pnp_server_submit": ([vp, C.POINTER(ProblemDesc), i32, i32, C.POINTER(i64)], i32),
+    "pnp_server_poll": ([vp, i64, dp, dp, C.POINTER(i32)], i32),
+    "pnp_server_wait": ([vp, i64, f64, C.POINTER(i32)], i32),
+    "pnp_server_cancel": ([vp, i64], i32),
+    "pnp_server_job_times": ([vp, i64, dp, dp, dp], i32),
+    "pnp_server_stats": ([vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_size_t)], i32),
+    "pnp_server_set_round": ([vp, i32], i32),
+    "pnp_server_destroy": ([vp], None),
     "pnp_kernel_timer": ([i32], i32),
     "pnp_kernel_timer_read": ([C.c_char_p, dp, C.POINTER(i64)], i32),
 }

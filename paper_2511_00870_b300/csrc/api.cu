@@ -71,49 +71,17 @@ cudaError_t conv_tc_layer(const __nv_bfloat16* in, const __nv_bfloat16* wblob, c
                           int ny, int nx, int nimg, const Rect* rects, __nv_bfloat16* out,
                           int* err, cudaStream_t s);
 
-// Step counter read by the update kernel during graph replay.
-struct StepState {
-    uint32_t t;
-    int32_t burn_in;
-};
-
 __global__ void k_advance(StepState* st) { st->t += 1; }
+
+cudaError_t launch_advance(StepState* st, cudaStream_t s) {
+    k_advance<<<1, 1, 0, s>>>(st);
+    return cudaGetLastError();
+}
 
 }  // namespace pnp
 
 using namespace pnp;
 
-struct pnp_problem {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int ny = 0, nx = 0, nchain = 1, kh = 0, kw = 0;
-    int64_t N = 0;
-    float* y = nullptr;
-    float* h = nullptr;
-    float* x = nullptr;
-    float* r = nullptr;
-    float* d = nullptr;
-    float* mean = nullptr;
-    float* m2 = nullptr;
-    double sigma = 0, alpha = 0, eps = 0, lambda = 0, gamma = 0, hnorm = 0;
-    uint64_t seed = 0;
-    int burn_in = 0;
-    pnp_precision prec = PNP_FP32;
-    const pnp_denoiser* D = nullptr;
-    int by = 1, bx = 1, halo = 0;
-    // block + halo mode
-    BlockDesc* blocks = nullptr;
-    int nblocks = 0, ty = 0, tx = 0;
-    float* tiles = nullptr;
-    float* dtiles = nullptr;
-    Rect* rects = nullptr;
-    void* scratch = nullptr;
-    size_t scratch_bytes = 0;
-    StepState* st = nullptr;
-    int64_t t = 0;
-    cudaGraphExec_t graph = nullptr;
-};
 
 // ------------------------------------------------------------------ helpers
 
@@ -241,6 +209,19 @@ extern "C" pnp_status pnp_create_denoiser(int K, int F, const float* weights, co
                                 blob[(((((size_t)m * 3 + dx) * 8 + cg) * 192 + dy * 64 + co) * 8) + c8] =
                                     f32_to_bf16_rne(W[((int64_t)co * 64 + cg * 8 + c8) * 9 + dy * 3 + dx]);
         }
+        // last layer: [dx][cg][16 rows][8 ci], row dy = kernel row dy, rows 3..15 zero
+        std::vector<uint16_t> blob_last(3 * 8 * 16 * 8, 0);
+        for (int dx = 0; dx < 3; ++dx)
+            for (int cg = 0; cg < 8; ++cg)
+                for (int dy = 0; dy < 3; ++dy)
+                    for (int c8 = 0; c8 < 8; ++c8)
+                        blob_last[(((size_t)dx * 8 + cg) * 16 + dy) * 8 + c8] =
+                            f32_to_bf16_rne(weights[src_off[K - 1] + (int64_t)(cg * 8 + c8) * 9 + dy * 3 + dx]);
+        if ((st = dalloc(&D.wtc_last, blob_last.size())) != PNP_OK) {
+            pnp_destroy_denoiser(den);
+            return st;
+        }
+        cudaMemcpy(D.wtc_last, blob_last.data(), blob_last.size() * 2, cudaMemcpyHostToDevice);
         D.h_first = new EdgeW();
         D.h_last = new EdgeW();
         memset(D.h_first, 0, sizeof(EdgeW));
@@ -284,6 +265,7 @@ extern "C" void pnp_destroy_denoiser(pnp_denoiser* den) {
     dfree(D.w32);
     dfree(D.b32);
     dfree(D.wtc);
+    dfree(D.wtc_last);
     dfree(D.wfirst);
     dfree(D.wlast);
     dfree(den->scratch);
@@ -499,9 +481,33 @@ extern "C" void pnp_destroy_problem(pnp_problem* p) {
     delete p;
 }
 
+namespace pnp {
+
+pnp_status problem_pre(pnp_problem* p, cudaStream_t s) {
+    PNP_CUDA_TRY(launch_blur(p->x, p->y, p->h, p->kh, p->kw, p->ny, p->nx, p->nchain, p->r, s));
+    return PNP_OK;
+}
+
+pnp_status problem_post(pnp_problem* p, cudaStream_t s) {
+    const bool prior = p->D && p->alpha != 0.0;
+    UpdateParams u;
+    PNP_TRY(fill_update_params(u, p->x, p->r, prior ? p->d : nullptr, p->h, p->kh, p->kw, p->ny,
+                               p->nx, p->nchain, p->sigma, p->alpha, p->eps, p->lambda, p->gamma,
+                               p->seed, 1));
+    u.t_dev = &p->st->t;
+    u.burn_dev = &p->st->burn_in;
+    u.mean = p->mean;
+    u.m2 = p->m2;
+    PNP_CUDA_TRY(launch_langevin_update(u, s));
+    PNP_CUDA_TRY(launch_advance(p->st, s));
+    return PNP_OK;
+}
+
+}  // namespace pnp
+
 static pnp_status enqueue_iteration(pnp_problem* p) {
     cudaStream_t s = p->stream;
-    PNP_CUDA_TRY(launch_blur(p->x, p->y, p->h, p->kh, p->kw, p->ny, p->nx, p->nchain, p->r, s));
+    PNP_TRY(problem_pre(p, s));
     const bool prior = p->D && p->alpha != 0.0;
     if (prior) {
         const DenoiserDev& D = p->D->dev;
@@ -517,18 +523,7 @@ static pnp_status enqueue_iteration(pnp_problem* p) {
                                                p->halo, p->ty, p->tx, p->d, s));
         }
     }
-    UpdateParams u;
-    PNP_TRY(fill_update_params(u, p->x, p->r, prior ? p->d : nullptr, p->h, p->kh, p->kw, p->ny,
-                               p->nx, p->nchain, p->sigma, p->alpha, p->eps, p->lambda, p->gamma,
-                               p->seed, 1));
-    u.t_dev = &p->st->t;
-    u.burn_dev = &p->st->burn_in;
-    u.mean = p->mean;
-    u.m2 = p->m2;
-    PNP_CUDA_TRY(launch_langevin_update(u, s));
-    k_advance<<<1, 1, 0, s>>>(p->st);
-    PNP_CUDA_TRY(cudaGetLastError());
-    return PNP_OK;
+    return problem_post(p, s);
 }
 
 extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_problem** out) {

@@ -1,0 +1,235 @@
+// Batched sampling: many independent posteriors (jobs) of different image
+// sizes stepped together. One iteration of the batch runs, for every job,
+// r = H x - y and the BF16 first layer, then ONE tensor-core launch per F -> F
+// layer and one for the last layer over the rows of all jobs (a device table
+// of per-job tensor maps, balanced across the SMs to within a row), then every
+// job's fused Langevin update. The whole iteration is captured once as a CUDA
+// graph and replayed. Jobs never interact: each one's result is the same as
+// when it runs alone (same kernels, same per-pixel summation order, its own
+// Philox stream and step counter).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "pnp_internal.h"
+
+namespace pnp {
+
+size_t BatchPlan::table_bytes(int n) { return (size_t)3 * n * sizeof(TcJob); }
+
+// Activation planes of a BF16 problem (layout of denoise_bf16's scratch).
+static void bf16_planes(const pnp_problem* p, __nv_bfloat16** A, __nv_bfloat16** B, int** err) {
+    const size_t act = (size_t)p->nchain * p->ny * bf16_pad_width(p->nx) * 64;
+    *A = (__nv_bfloat16*)p->scratch;
+    *B = *A + act;
+    *err = (int*)(*B + act);
+}
+
+pnp_status plan_build(BatchPlan& plan, const std::vector<pnp_problem*>& jobs, cudaStream_t s) {
+    plan.n = (int)jobs.size();
+    plan.total_rows = 0;
+    if (plan.n == 0) return PNP_OK;
+    const pnp_problem* p0 = jobs[0];
+    plan.bf16 = p0->prec == PNP_BF16 && p0->D && p0->alpha != 0.0;
+    if (!plan.bf16) return PNP_OK;
+    const int K = p0->D->dev.K;
+    const size_t need = BatchPlan::table_bytes(plan.n);
+    if (plan.cap < need) {
+        if (plan.tables) cudaFree(plan.tables);
+        plan.tables = nullptr;
+        plan.cap = 0;
+        PNP_CUDA_TRY(cudaMalloc((void**)&plan.tables, need));
+        plan.cap = need;
+    }
+    std::vector<TcJob> host(3 * (size_t)plan.n);
+    int64_t row = 0;
+    for (int j = 0; j < plan.n; ++j) {
+        const pnp_problem* p = jobs[j];
+        __nv_bfloat16 *A, *B;
+        int* err;
+        bf16_planes(p, &A, &B, &err);
+        if (j == 0) plan.err = err;
+        TcJob* ab = &host[j];
+        TcJob* ba = &host[plan.n + j];
+        TcJob* last = &host[2 * (size_t)plan.n + j];
+        PNP_CUDA_TRY(tc_make_job(ab, A, B, p->ny, p->nx, p->nchain, nullptr, row));
+        PNP_CUDA_TRY(tc_make_job(ba, B, A, p->ny, p->nx, p->nchain, nullptr, row));
+        // after K-2 F -> F layers starting in A the activations are in B if K-2 is odd
+        __nv_bfloat16* fin = ((K - 2) % 2 == 1) ? B : A;
+        PNP_CUDA_TRY(tc_make_job(last, fin, nullptr, p->ny, p->nx, p->nchain, nullptr, row));
+        last->xin = p->x;
+        last->dout = p->d;
+        row += ab->rows;
+    }
+    plan.total_rows = row;
+    PNP_CUDA_TRY(cudaMemcpyAsync(plan.tables, host.data(), need, cudaMemcpyHostToDevice, s));
+    PNP_CUDA_TRY(cudaStreamSynchronize(s));
+    return PNP_OK;
+}
+
+void plan_free(BatchPlan& plan) {
+    if (plan.tables) cudaFree(plan.tables);
+    plan.tables = nullptr;
+    plan.cap = 0;
+}
+
+pnp_status plan_enqueue_step(const BatchPlan& plan, const std::vector<pnp_problem*>& jobs,
+                             cudaStream_t s) {
+    if (jobs.empty()) return PNP_OK;
+    for (pnp_problem* p : jobs) PNP_TRY(problem_pre(p, s));
+    const pnp_problem* p0 = jobs[0];
+    if (p0->D && p0->alpha != 0.0) {
+        const DenoiserDev& D = p0->D->dev;
+        if (plan.bf16) {
+            for (pnp_problem* p : jobs) {
+                __nv_bfloat16 *A, *B;
+                int* err;
+                bf16_planes(p, &A, &B, &err);
+                PNP_CUDA_TRY(first_layer_bf16(D, p->x, p->ny, p->nx, p->nchain, nullptr, A, s));
+            }
+            TcJob dummy;
+            memset(&dummy, 0, sizeof(dummy));
+            for (int k = 1; k < D.K - 1; ++k) {
+                const TcJob* tab = plan.tables + ((k % 2 == 1) ? 0 : plan.n);   // A->B, B->A, ...
+                PNP_CUDA_TRY(tc_launch(dummy, tab, plan.n, plan.total_rows,
+                                       D.wtc + (size_t)(k - 1) * (3 * 8 * 192 * 8), D.hb + 64 * k,
+                                       plan.err, false, s));
+            }
+            PNP_CUDA_TRY(tc_launch(dummy, plan.tables + 2 * (size_t)plan.n, plan.n, plan.total_rows,
+                                   D.wtc_last, &D.h_last->b[0], plan.err, true, s));
+        } else {
+            for (pnp_problem* p : jobs)
+                PNP_CUDA_TRY(denoise_fp32(D, p->x, p->ny, p->nx, p->nchain, nullptr, p->d,
+                                          (float*)p->scratch, s));
+        }
+    }
+    for (pnp_problem* p : jobs) PNP_TRY(problem_post(p, s));
+    return PNP_OK;
+}
+
+}  // namespace pnp
+
+using namespace pnp;
+
+struct pnp_batch {
+    std::vector<pnp_problem*> jobs;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    BatchPlan plan;
+    cudaGraphExec_t graph = nullptr;
+    bool eager_done = false;
+};
+
+extern "C" void pnp_batch_destroy(pnp_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (pnp_problem* p : b->jobs) pnp_destroy_problem(p);
+    plan_free(b->plan);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+extern "C" pnp_status pnp_batch_create(const pnp_problem_desc* descs, int njobs, void* stream,
+                                       pnp_batch** out) {
+    if (!out || !descs || njobs < 1) return fail(PNP_EINVAL, "pnp_batch_create: bad arguments");
+    *out = nullptr;
+    const pnp_denoiser* D = descs[0].D;
+    const pnp_precision prec = descs[0].precision;
+    for (int j = 0; j < njobs; ++j) {
+        if (descs[j].D != D || descs[j].precision != prec)
+            return fail(PNP_EINVAL, "pnp_batch_create: all jobs must share the denoiser and precision");
+        if (descs[j].halo != 0)
+            return fail(PNP_EINVAL, "pnp_batch_create: batched jobs use the direct layout (halo = 0)");
+    }
+    pnp_batch* b = new pnp_batch();
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete b;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        b->own_stream = true;
+    }
+    for (int j = 0; j < njobs; ++j) {
+        pnp_problem_desc d = descs[j];
+        d.stream = b->stream;
+        pnp_problem* p = nullptr;
+        pnp_status st = pnp_create_problem(&d, &p);
+        if (st != PNP_OK) {
+            const std::string msg = pnp_last_error();
+            pnp_batch_destroy(b);
+            return fail(st, "job " + std::to_string(j) + ": " + msg);
+        }
+        b->jobs.push_back(p);
+    }
+    pnp_status st = plan_build(b->plan, b->jobs, b->stream);
+    if (st != PNP_OK) {
+        pnp_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_batch_step(pnp_batch* b, int n_iters) {
+    if (!b || n_iters < 0) return fail(PNP_EINVAL, "pnp_batch_step: bad arguments");
+    for (int i = 0; i < n_iters; ++i) {
+        if (!b->eager_done || timer_enabled()) {
+            // first iteration eagerly: performs the kernels' one-time setup outside capture
+            PNP_TRY(plan_enqueue_step(b->plan, b->jobs, b->stream));
+            b->eager_done = true;
+        } else {
+            if (!b->graph) {
+                cudaGraph_t g = nullptr;
+                PNP_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+                pnp_status st = plan_enqueue_step(b->plan, b->jobs, b->stream);
+                cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+                if (st != PNP_OK) {
+                    if (g) cudaGraphDestroy(g);
+                    return st;
+                }
+                if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+                e = cudaGraphInstantiate(&b->graph, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) {
+                    b->graph = nullptr;
+                    return cuda_fail(e, "cudaGraphInstantiate");
+                }
+            }
+            PNP_CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
+        }
+        for (pnp_problem* p : b->jobs) p->t += 1;
+    }
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_batch_sync(pnp_batch* b) {
+    if (!b) return fail(PNP_EINVAL, "batch is NULL");
+    PNP_CUDA_TRY(cudaStreamSynchronize(b->stream));
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_batch_run(pnp_batch* b, int T, int burn_in) {
+    if (!b || T < 0 || burn_in < 0) return fail(PNP_EINVAL, "pnp_batch_run: bad arguments");
+    for (pnp_problem* p : b->jobs) {
+        if (p->burn_in != burn_in) {
+            p->burn_in = burn_in;
+            PNP_CUDA_TRY(cudaMemcpyAsync(&p->st->burn_in, &burn_in, 4, cudaMemcpyHostToDevice, b->stream));
+            PNP_CUDA_TRY(cudaStreamSynchronize(b->stream));
+        }
+    }
+    PNP_TRY(pnp_batch_step(b, T));
+    return pnp_batch_sync(b);
+}
+
+extern "C" pnp_status pnp_batch_job(pnp_batch* b, int job, pnp_problem** p) {
+    if (!b || !p || job < 0 || job >= (int)b->jobs.size())
+        return fail(PNP_EINVAL, "pnp_batch_job: bad arguments");
+    *p = b->jobs[job];
+    return PNP_OK;
+}
+
+extern "C" int pnp_batch_size(const pnp_batch* b) { return b ? (int)b->jobs.size() : 0; }

@@ -72,6 +72,19 @@ constexpr uint32_t DESC_HI = (128u >> 4) | (1u << 14);
 }  // namespace tc
 
 static_assert(sizeof(TcJob) == 256 && alignof(TcJob) == 128, "TcJob layout");
+
+// F -> F layers (LAST = false): N = 3 x 64, kernel row dy in columns
+// [64 dy, 64 dy + 64). Last layer (LAST = true): its single output channel for
+// kernel rows dy = 0, 1, 2 in B rows 0, 1, 2 of one 16-row block (N = 16).
+template <bool LAST>
+struct TcMode {
+    static constexpr int NROW = LAST ? 1 : 64;
+    static constexpr int NB = LAST ? 16 : 3 * NROW;
+    static constexpr int DX_W = 8 * NB * 16;
+    static constexpr int WB = 3 * DX_W;
+    static constexpr uint32_t IDESC = ptx::idesc_bf16_f32(tc::SEG, NB);
+    static constexpr uint32_t B_LBO = (uint32_t)((NB * 16) >> 4) << 16;
+};
 static_assert(tc::SMEM <= 232448, "shared memory budget");
 
 __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -144,9 +157,11 @@ __device__ __forceinline__ void tm_load64(uint32_t taddr, float* acc) {
     for (int e = 0; e < 64; ++e) acc[e] = __uint_as_float(t[e]);
 }
 
+template <bool LAST>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     k_conv_tc(const __grid_constant__ TcJob job0, const TcCommon c) {
     using namespace tc;
+    using Mode = TcMode<LAST>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* ring = smem + OFF_RING;
@@ -193,10 +208,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer
-            ptx::mbar_arrive_expect_tx(wbar, W_BYTES);
+            ptx::mbar_arrive_expect_tx(wbar, Mode::WB);
             for (int t = 0; t < 3; ++t)
-                ptx::bulk_load(wsm + t * DX_W_BYTES, (const uint8_t*)c.wblob + t * DX_W_BYTES,
-                               DX_W_BYTES, wbar);
+                ptx::bulk_load(wsm + t * Mode::DX_W, (const uint8_t*)c.wblob + t * Mode::DX_W,
+                               Mode::DX_W, wbar);
             uint32_t L = 0;
             bool ok = true;
             int j = 0;
@@ -222,7 +237,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             // ---------------- MMA issuer: 12 MMAs (N = 192) per input row
             bool ok = ptx::mbar_wait(wbar, 0, abort_flag, BUDGET);
             const uint32_t ring_lo = (ptx::smem_u32(ring) >> 4) | A_LBO_FIELD;
-            const uint32_t w_lo = (ptx::smem_u32(wsm) >> 4) | B_LBO_FIELD;
+            const uint32_t w_lo = (ptx::smem_u32(wsm) >> 4) | Mode::B_LBO;
             uint32_t L = 0;
             bool issued = false;
             int j = 0;
@@ -241,8 +256,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)
                             mma_lo(d, a_row + kk * 2 * (CG_BYTES >> 4) + (HALO_PX - 1 + dx),
-                                   w_lo + dx * (DX_W_BYTES >> 4) + kk * 2 * (NB * 16 >> 4), IDESC192,
-                                   (dx | kk) != 0);
+                                   w_lo + dx * (Mode::DX_W >> 4) + kk * 2 * (Mode::NB * 16 >> 4),
+                                   Mode::IDESC, (dx | kk) != 0);
                     issued = true;
                     ptx::mma_commit(&empty[L % NS]);   // input row consumed
                     ptx::mma_commit(&tfull[reg]);      // P_i ready
@@ -256,6 +271,50 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         }
     } else {
         // ---------------- epilogue: warps 2..5 own TMEM lane quadrants 2,3,0,1
+        if constexpr (LAST) {
+            // last layer: output row r = P_{r-1}[col 0] + P_r[col 1] + P_{r+1}[col 2];
+            // d = x - (G + b) in FP32
+            const int quad = warp & 3;
+            const int jx = quad * 32 + lane;
+            const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
+            uint32_t L = 0;
+            bool ok = true;
+            int j = 0;
+            float X0 = 0.f, X1 = 0.f;
+            for (int64_t g = g_begin; g < g_end && ok;) {
+                const RowPos p = locate(job0, c, j, g, g_end);
+                const TcJob* J = p.J;
+                const int x = p.strip * SEG + jx;
+                const bool in_img = x < J->nx;
+                const int64_t plane = (int64_t)J->ny * J->nx;
+                const float* xin = J->xin + p.img * plane;
+                float* dout = J->dout + p.img * plane;
+                auto step = [&](float& Xprev, float& Xcur, int ri, uint32_t taddr, float xv) {
+                    float pr[4];
+                    ptx::tmem_ld4(taddr, pr);
+                    if (ri >= 1) {
+                        Xprev += pr[2];
+                        if (in_img) dout[(int64_t)(p.y + ri - 1) * J->nx + x] = xv - (Xprev + c.bias[0]);
+                    }
+                    if (ri >= 0 && ri < p.len) Xcur += pr[1];
+                    if (ri + 1 < p.len) Xprev = pr[0];
+                };
+                for (int ri = -1; ri <= p.len; ++ri, ++L) {
+                    const uint32_t reg = L & 1, u = L >> 1;
+                    // x of the output row this step completes, loaded before the wait
+                    const float xv = (ri >= 1 && in_img) ? __ldg(xin + (int64_t)(p.y + ri - 1) * J->nx + x) : 0.f;
+                    if (!ptx::mbar_wait(&tfull[reg], u & 1, abort_flag, BUDGET)) { ok = false; break; }
+                    ptx::tc_fence_after();
+                    const uint32_t taddr = lane_base + reg * NB;
+                    if ((ri + 1) & 1) step(X1, X0, ri, taddr, xv);
+                    else step(X0, X1, ri, taddr, xv);
+                    ptx::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&tempty[reg]);
+                }
+                g += p.len;
+            }
+        } else {
         const int quad = warp & 3;
         const int jx = quad * 32 + lane;
         const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
@@ -314,6 +373,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 if (lane == 0) ptx::mbar_arrive(&tempty[reg]);
             }
             g += p.len;
+        }
+    
         }
     }
 
@@ -374,60 +435,6 @@ __global__ void __launch_bounds__(128) k_first_bf16(const float* __restrict__ x,
 }
 
 // ---------------------------------------------------------------------------
-// Last layer 64 -> 1 (no ReLU) fused with the residual d = x - G(x). Each
-// thread computes 4 consecutive pixels: it reads the 3 x 6 neighbourhood of
-// 64-channel vectors once (16-byte loads through L1) and reuses every vector
-// for all pixels it touches; weights are constant-bank operands.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_last_bf16(const __nv_bfloat16* __restrict__ act,
-                                                   const __grid_constant__ EdgeW W,
-                                                   const float* __restrict__ x, int ny, int nx,
-                                                   int nxp, float* __restrict__ d) {
-    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    const int yy = blockIdx.y, img = blockIdx.z;
-    if (x0 >= nx) return;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int dy = 0; dy < 3; ++dy) {
-        const int sy = yy + dy - 1;
-        if (sy < 0 || sy >= ny) continue;
-        const __nv_bfloat16* rowp = act + (((int64_t)img * ny + sy) * 8) * nxp * 8;
-#pragma unroll
-        for (int cg = 0; cg < 8; ++cg) {
-#pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                const int sx = x0 + q - 1;
-                if (sx < 0 || sx >= nxp) continue;
-                const uint4 raw = __ldg(reinterpret_cast<const uint4*>(rowp + ((int64_t)cg * nxp + sx) * 8));
-                const uint32_t wd[4] = {raw.x, raw.y, raw.z, raw.w};
-                float f[8];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float2 t2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wd[e]));
-                    f[2 * e] = t2.x;
-                    f[2 * e + 1] = t2.y;
-                }
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    const int dx = q - p;   // pixel x0+p reads column x0+p+dx-1
-                    if (dx < 0 || dx > 2) continue;
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) acc[p] = fmaf(W.w[dy * 3 + dx][cg * 8 + e], f[e], acc[p]);
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        const int xx = x0 + p;
-        if (xx < nx) {
-            const int64_t n = (int64_t)img * ny * nx + (int64_t)yy * nx + xx;
-            d[n] = x[n] - (acc[p] + W.b[0]);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -483,27 +490,32 @@ cudaError_t tc_make_job(TcJob* J, const __nv_bfloat16* in, __nv_bfloat16* out, i
 }
 
 cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64_t total_rows,
-                      const __nv_bfloat16* wblob, const float* bias_host, int* err, cudaStream_t s) {
-    const float* bias = bias_host;   // 64 floats in host memory, copied into the launch
+                      const __nv_bfloat16* wblob, const float* bias_host, int* err, bool last,
+                      cudaStream_t s) {
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             tc::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_conv_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     tc::SMEM);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     if (total_rows <= 0) return cudaSuccess;
     TcCommon c;
     c.wblob = wblob;
-    memcpy(c.bias, bias, sizeof(c.bias));
+    memset(c.bias, 0, sizeof(c.bias));
+    memcpy(c.bias, bias_host, (last ? 1 : 64) * sizeof(float));
     c.err = err;
     c.jobs = jobs_dev;
     c.njobs = jobs_dev ? njobs : 1;
     c.total_rows = total_rows;
     const int grid = (int)std::min<int64_t>(num_sms(), total_rows);
-    timer_begin(T_CONV_TC, s);
-    k_conv_tc<<<grid, tc::THREADS, tc::SMEM, s>>>(job0, c);
-    timer_end(T_CONV_TC, s);
+    timer_begin(last ? T_CONV_EDGE : T_CONV_TC, s);
+    if (last) k_conv_tc<true><<<grid, tc::THREADS, tc::SMEM, s>>>(job0, c);
+    else k_conv_tc<false><<<grid, tc::THREADS, tc::SMEM, s>>>(job0, c);
+    timer_end(last ? T_CONV_EDGE : T_CONV_TC, s);
     return cudaGetLastError();
 }
 
@@ -513,7 +525,7 @@ cudaError_t conv_tc_layer(const __nv_bfloat16* in, const __nv_bfloat16* wblob, c
     TcJob J;
     cudaError_t e = tc_make_job(&J, in, out, ny, nx, nimg, rects, 0);
     if (e != cudaSuccess) return e;
-    return tc_launch(J, nullptr, 1, J.rows, wblob, bias_host, err, s);
+    return tc_launch(J, nullptr, 1, J.rows, wblob, bias_host, err, false, s);
 }
 
 cudaError_t first_layer_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
@@ -527,18 +539,18 @@ cudaError_t first_layer_bf16(const DenoiserDev& D, const float* x, int ny, int n
 }
 
 cudaError_t last_layer_bf16(const DenoiserDev& D, const __nv_bfloat16* act, const float* x,
-                            int ny, int nx, int nimg, float* d, cudaStream_t s) {
-    const int nxp = bf16_pad_width(nx);
-    dim3 g2(ceil_div(nx, 4 * 128), ny, nimg);
-    timer_begin(T_CONV_EDGE, s);
-    k_last_bf16<<<g2, 128, 0, s>>>(act, *D.h_last, x, ny, nx, nxp, d);
-    timer_end(T_CONV_EDGE, s);
-    return cudaGetLastError();
+                            int ny, int nx, int nimg, float* d, int* err, cudaStream_t s) {
+    TcJob J;
+    cudaError_t e = tc_make_job(&J, act, nullptr, ny, nx, nimg, nullptr, 0);
+    if (e != cudaSuccess) return e;
+    J.xin = x;
+    J.dout = d;
+    return tc_launch(J, nullptr, 1, J.rows, D.wtc_last, &D.h_last->b[0], err, true, s);
 }
 
 cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
                          const Rect* rects, float* d, void* scratch, cudaStream_t s) {
-    if (D.F != 64 || !D.wtc || !D.h_first || !D.h_last) return cudaErrorInvalidValue;
+    if (D.F != 64 || !D.wtc || !D.wtc_last || !D.h_first || !D.h_last) return cudaErrorInvalidValue;
     const int nxp = bf16_pad_width(nx);
     const size_t act = (size_t)nimg * ny * nxp * 64;
     __nv_bfloat16* A = (__nv_bfloat16*)scratch;
@@ -553,7 +565,7 @@ cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, i
         if (e != cudaSuccess) return e;
         __nv_bfloat16* t = A; A = B; B = t;
     }
-    return last_layer_bf16(D, A, x, ny, nx, nimg, d, s);
+    return last_layer_bf16(D, A, x, ny, nx, nimg, d, err, s);
 }
 
 }  // namespace pnp

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "pnp.h"
 
@@ -69,6 +70,8 @@ struct DenoiserDev {
     int64_t* b_off = nullptr;
     // BF16 tensor-core layout of the F->F layers: per layer [dx 3][cg 8][dy 3 x co 64][8 ci]
     __nv_bfloat16* wtc = nullptr;
+    // last layer (F -> 1): [dx 3][cg 8][16 rows: kernel row dy in row dy][8 ci]
+    __nv_bfloat16* wtc_last = nullptr;
     EdgeW* h_first = nullptr;   // host copies for the BF16 edge layers
     EdgeW* h_last = nullptr;
     // FP32 first/last layer weights in tap-major order for the BF16 path
@@ -77,6 +80,12 @@ struct DenoiserDev {
     // host copies (FP32, OIHW) for reference / re-packing
     float* hw = nullptr;
     float* hb = nullptr;
+};
+
+// Step counter read by the update kernel during graph replay.
+struct StepState {
+    uint32_t t;
+    int32_t burn_in;
 };
 
 }  // namespace pnp
@@ -134,8 +143,10 @@ size_t denoise_fp32_scratch(const DenoiserDev& D, int ny, int nx, int nimg);
 // the job in the launch's concatenated row stream.
 struct TcJob {   // 256 B, 128-B aligned (the tensor map requires it)
     CUtensorMap tin;
-    __nv_bfloat16* out;
+    __nv_bfloat16* out;       // F -> F layers: BF16 activations out
     const Rect* rects;
+    const float* xin;         // last layer: x (FP32 [img][ny][nx]) ...
+    float* dout;              // ... and d = x - G(x) out
     int64_t row_begin;
     int64_t rows;
     int ny, nx, nxp, strips, nimg, pad0, pad1, pad2;
@@ -144,13 +155,15 @@ int bf16_pad_width(int nx);
 cudaError_t tc_make_job(TcJob* J, const __nv_bfloat16* in, __nv_bfloat16* out, int ny, int nx,
                         int nimg, const Rect* rects, int64_t row_begin);
 // jobs_dev == nullptr: run job0 alone (passed by value); else the device table.
-// bias_host: the layer's 64 biases in host memory (passed by value to the kernel).
+// bias_host: the layer's biases in host memory (passed by value to the kernel).
+// last: the F -> 1 layer fused with d = x - G(x) (wblob = last-layer blob).
 cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64_t total_rows,
-                      const __nv_bfloat16* wblob, const float* bias_host, int* err, cudaStream_t s);
+                      const __nv_bfloat16* wblob, const float* bias_host, int* err, bool last,
+                      cudaStream_t s);
 cudaError_t first_layer_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
                              const Rect* rects, __nv_bfloat16* out, cudaStream_t s);
 cudaError_t last_layer_bf16(const DenoiserDev& D, const __nv_bfloat16* act, const float* x,
-                            int ny, int nx, int nimg, float* d, cudaStream_t s);
+                            int ny, int nx, int nimg, float* d, int* err, cudaStream_t s);
 
 // BF16 tcgen05 denoiser (F = 64). scratch must hold denoise_bf16_scratch() bytes.
 cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
@@ -170,4 +183,64 @@ cudaError_t launch_scatter_blocks(const float* dtiles, int ny, int nx, const Blo
                                   int nblocks, int halo, int ty, int tx, float* d,
                                   cudaStream_t s);
 
+}  // namespace pnp
+
+// A problem's device state (one posterior, nchain chains). Defined here so
+// the batch and serving engines can drive problems directly.
+struct pnp_problem {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int ny = 0, nx = 0, nchain = 1, kh = 0, kw = 0;
+    int64_t N = 0;
+    float* y = nullptr;
+    float* h = nullptr;
+    float* x = nullptr;
+    float* r = nullptr;
+    float* d = nullptr;
+    float* mean = nullptr;
+    float* m2 = nullptr;
+    double sigma = 0, alpha = 0, eps = 0, lambda = 0, gamma = 0, hnorm = 0;
+    uint64_t seed = 0;
+    int burn_in = 0;
+    pnp_precision prec = PNP_FP32;
+    const pnp_denoiser* D = nullptr;
+    int by = 1, bx = 1, halo = 0;
+    // block + halo mode
+    pnp::BlockDesc* blocks = nullptr;
+    int nblocks = 0, ty = 0, tx = 0;
+    float* tiles = nullptr;
+    float* dtiles = nullptr;
+    pnp::Rect* rects = nullptr;
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    pnp::StepState* st = nullptr;
+    int64_t t = 0;
+    cudaGraphExec_t graph = nullptr;
+};
+
+namespace pnp {
+cudaError_t launch_advance(StepState* st, cudaStream_t s);
+// The two halves of one iteration around the denoiser: r = H x - y, and the
+// fused update (+ step counter advance).
+pnp_status problem_pre(pnp_problem* p, cudaStream_t s);
+pnp_status problem_post(pnp_problem* p, cudaStream_t s);
+}  // namespace pnp
+
+namespace pnp {
+// Device job tables of a batch step: [F->F A->B][F->F B->A][last], one entry per job.
+struct BatchPlan {
+    TcJob* tables = nullptr;
+    size_t cap = 0;
+    int n = 0;
+    int64_t total_rows = 0;
+    bool bf16 = false;
+    int* err = nullptr;
+    static size_t table_bytes(int n);
+};
+pnp_status plan_build(BatchPlan& plan, const std::vector<pnp_problem*>& jobs, cudaStream_t s);
+void plan_free(BatchPlan& plan);
+// One iteration of every job (all share denoiser and precision).
+pnp_status plan_enqueue_step(const BatchPlan& plan, const std::vector<pnp_problem*>& jobs,
+                             cudaStream_t s);
 }  // namespace pnp
