@@ -10,7 +10,8 @@ headline value is the BF16 denoiser form, with the FP32 plain form and the
 MMSE PSNR of both reported beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload deconv1024|deconv8192|deconv128] [--no-quality]
+                       [--workload deconv1024|deconv8192|deconv128|batch48|serve]
+                       [--no-quality] [--jobs M]
 Multi-GPU (torchrun): every rank runs an independent replica of the workload
 (independent chains, no data-path collective); value = all ranks' pixel-
 iterations / max time over ranks.
@@ -41,6 +42,8 @@ WORKLOADS = {
     "deconv1024": 2,   # 1024^2, uniform 9x9, 20 dB, K=8 F=64, 4x4 blocks, 2000 it (500 burn-in)
     "deconv8192": 3,   # 8192^2, Gaussian 13x13 s=3, 30 dB, K=8 F=64, 16x16 blocks
     "deconv128": 1,    # 128^2, Gaussian 7x7 s=1.5, 30 dB, K=4 F=16, 2x2 blocks
+    "batch48": 4,      # 48 problems, sizes log-uniform 256..2048, blur/BSNR mix, BF16
+    "serve": 5,        # Poisson arrivals (20/s), sizes {512..4096}^2, 200 + 800 iterations
 }
 
 
@@ -110,7 +113,13 @@ def dist_setup():
 
 def _oracle_setup(cfg_id, crop):
     import oracle
-    prob = synth.workload_problem(cfg_id)
+    if cfg_id == 4:
+        prob = synth.batched_problems(1, seed=4000)[0]
+    elif cfg_id == 5:
+        sp = synth.serving_jobs(1, seed=5000)[0]
+        prob = synth.make_problem(sp["size"], sp["size"], sp["h"], sp["bsnr"], sp["gt_seed"])
+    else:
+        prob = synth.workload_problem(cfg_id)
     dw = synth.workload_denoiser(cfg_id)
     crop = min(crop, prob.shape[0], prob.shape[1])
     y = prob.y[:crop, :crop]
@@ -174,6 +183,182 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _percentile(v, q):
+    v = sorted(v)
+    if not v:
+        return None
+    k = (len(v) - 1) * q / 100.0
+    lo, hi = int(math.floor(k)), int(math.ceil(k))
+    return v[lo] + (v[hi] - v[lo]) * (k - lo)
+
+
+def _fp32_iter_time(P, torch, den, prob, stream, iters=5):
+    """Device time of one FP32 plain iteration (eager, CUDA events)."""
+    gp = P.Problem(prob.y, prob.h, prob.sigma, den, seed=prob.seed, precision="fp32",
+                   stream=stream.cuda_stream)
+    gp.step(2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    gp.step(iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gp.close()
+    return e0.elapsed_time(e1) / iters / 1e3
+
+
+def run_batch(args, P, torch, stream, ws, rank, local):
+    """Batched form: 48 independent problems, one tensor-core launch per layer
+    over all of them, one CUDA graph per iteration."""
+    peaks = load_peaks()
+    probs = synth.batched_problems(48, seed=4000 + 17 * rank)
+    den = P.Denoiser.from_weights(synth.workload_denoiser(2))
+    jobs = [dict(y=p.y, h=p.h, sigma=p.sigma, seed=p.seed, burn_in=200) for p in probs]
+    npix = sum(p.y.size for p in probs)
+    out = {}
+    for prec in ("bf16", "fp32"):
+        steps = args.steps if prec == "bf16" else min(args.steps, 20)
+        b = P.Batch(jobs, den, precision=prec, stream=stream.cuda_stream)
+        b.step(args.warmup)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ck = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        out[prec] = dict(ms=ms, steps=steps, value=npix * steps / (ms * 1e3), clocks=ck)
+        if prec == "bf16":
+            P.pnp_kernel_timer(True)
+            b.step(10)
+            torch.cuda.synchronize()
+            kms, kn = P.pnp_kernel_timer_read("conv_tc")
+            P.pnp_kernel_timer(False)
+            out[prec]["conv_tc_avg_ms"] = kms / max(kn, 1)
+        b.close()
+    if rank != 0:
+        return
+    achieved = 2.0 * 64 * 64 * 9 * npix / (out["bf16"]["conv_tc_avg_ms"] * 1e-3) / 1e12
+    sizes = [p.y.shape[0] for p in probs]
+    line = dict(
+        metric=METRIC, value=round(out["bf16"]["value"] * ws, 3), unit=UNIT, n_gpus=ws,
+        steps=args.steps, warmup=args.warmup, ms_per_step=round(out["bf16"]["ms"] / args.steps, 4),
+        higher_is_better=True, scaling="weak", vs_baseline=None, dtype="bf16", data="synthetic",
+        config=dict(workload=f"batch48: 48 problems, sizes log-uniform 256..2048 (min {min(sizes)}, "
+                             f"max {max(sizes)}, {npix / 1e6:.1f} Mpixel total), blur mix, BSNR "
+                             f"15-40 dB, K=8 F=64 BF16, one launch per layer over all jobs",
+                    precision="bf16", graph="one CUDA graph per batch iteration",
+                    l2="working set per step > 126 MB L2"),
+        roofline=dict(bound="tensor", achieved=round(achieved, 2), peak=peaks["bf16_sus"],
+                      unit="TFLOP/s", frac=round(achieved / peaks["bf16_sus"], 4), traffic=None,
+                      kernel="k_conv_tc (48-job table)", peak_kind=f"bf16 sustained ({peaks['src']})"),
+        fp32_plain=dict(value=round(out["fp32"]["value"], 3), unit=UNIT, steps=out["fp32"]["steps"],
+                        speedup_bf16=round(out["bf16"]["value"] / out["fp32"]["value"], 3)),
+        gpu_launches=(48 * 5 + 7) * args.steps,
+        clocks=out["bf16"]["clocks"],
+        latency=dict(p50_s=None, p99_s=None, note="batch of 48 jobs stepped together"),
+    )
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args, P, torch, stream, ws, rank, local):
+    """Serving form: a seeded Poisson stream of sampling jobs (20 jobs/s), each
+    200 burn-in + 800 kept iterations, continuously batched by the server; a
+    bounded run of the first --jobs arrivals. The FP32 one-job-at-a-time
+    baseline is measured per image size and applied to the same arrivals."""
+    import threading as th
+    peaks = load_peaks()
+    n = args.jobs
+    specs = synth.serving_jobs(n, seed=5000 + 31 * rank)
+    arrivals = synth.poisson_arrivals(n, 20.0, seed=5000 + 31 * rank)
+    probs = []
+    for sp in specs:
+        probs.append(synth.make_problem(sp["size"], sp["size"], sp["h"], sp["bsnr"], sp["gt_seed"]))
+    den = P.Denoiser.from_weights(synth.workload_denoiser(2))
+    T, TB = 1000, 200
+    free, total = torch.cuda.mem_get_info()
+    srv = P.Server(den, precision="bf16", hbm_budget_bytes=int(0.8 * free), round_iters=8)
+    ids = [None] * n
+    t_start = time.perf_counter()
+
+    def submitter():
+        for k in range(n):
+            dt = arrivals[k] - (time.perf_counter() - t_start)
+            if dt > 0:
+                time.sleep(dt)
+            p = probs[k]
+            ids[k] = srv.submit(p.y, p.h, p.sigma, T, TB, seed=p.seed)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    thr = th.Thread(target=submitter)
+    thr.start()
+    thr.join()
+    for jid in ids:
+        srv.wait(jid, 3600)
+    ck = sampler.stop()
+    times = [srv.times(j) for j in ids]
+    lat = [t["done"] - t["submit"] for t in times]
+    span = max(t["done"] for t in times) - min(t["submit"] for t in times)
+    pix_iters = sum(p.y.size for p in probs) * T
+    value = pix_iters / span / 1e6
+    # quality at equal PSNR on the first (smallest-index) job: BF16 served vs FP32 plain chain
+    q = probs[0]
+    _, mm16, _ = srv.poll(ids[0])
+    srv.close()
+    g32 = P.Problem(q.y, q.h, q.sigma, den, seed=q.seed, burn_in=TB, precision="fp32",
+                    stream=stream.cuda_stream)
+    g32.run_chain(T, TB)
+    mm32, _, _ = g32.moments()
+    g32.close()
+    psnr = lambda m: 10 * math.log10(1.0 / float(np.mean((m - q.xbar) ** 2)))
+    # FP32 one-job-at-a-time: measured per-size iteration time, FIFO over the same arrivals
+    per_size = {}
+    for p in probs:
+        s = p.y.shape[0]
+        if s not in per_size:
+            per_size[s] = _fp32_iter_time(P, torch, den, p, stream)
+    finish, lat32 = 0.0, []
+    for k, p in enumerate(probs):
+        start = max(arrivals[k], finish)
+        finish = start + T * per_size[p.y.shape[0]]
+        lat32.append(finish - arrivals[k])
+    value32 = pix_iters / (finish - arrivals[0]) / 1e6
+    if rank != 0:
+        return
+    sizes = [p.y.shape[0] for p in probs]
+    h2d = sum(p.y.size * 4 + p.h.size * 4 for p in probs)
+    d2h = sum(2 * p.y.size * 8 for p in probs)
+    iters = n * T
+    line = dict(
+        metric=METRIC, value=round(value * ws, 3), unit=UNIT, n_gpus=ws, steps=T, warmup=0,
+        ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="bf16",
+        data="synthetic",
+        config=dict(workload=f"serve: first {n} jobs of a Poisson stream at 20 jobs/s, sizes "
+                             f"{sorted(set(sizes))}, 200 burn-in + 800 kept iterations, MMSE + std, "
+                             f"K=8 F=64 BF16; continuous batching, HBM-budget admission",
+                    precision="bf16", l2="working set > 126 MB L2"),
+        latency=dict(p50_s=round(_percentile(lat, 50), 3), p99_s=round(_percentile(lat, 99), 3),
+                     unit="s", definition="completion - submission"),
+        fp32_plain=dict(value=round(value32, 3), unit=UNIT,
+                        p50_s=round(_percentile(lat32, 50), 3), p99_s=round(_percentile(lat32, 99), 3),
+                        note="one job at a time, FIFO; per-size FP32 iteration time measured here "
+                             "(5 iterations each) times T"),
+        speedup_bf16=round(value / value32, 3),
+        quality=dict(job=f"{q.y.shape[0]}x{q.y.shape[1]}", psnr_bf16_served_db=round(psnr(mm16), 4),
+                     psnr_fp32_plain_db=round(psnr(mm32), 4),
+                     delta_db=round(psnr(mm16) - psnr(mm32), 4)),
+        e2e=dict(value=round(value * ws, 3), unit=UNIT, h2d_bytes_per_step=h2d / iters,
+                 d2h_bytes_per_step=d2h / iters,
+                 note="the served path is end to end: host inputs in, host MMSE/std out"),
+        clocks=ck,
+    )
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,6 +369,7 @@ def main():
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precisions", default="bf16,fp32")
+    ap.add_argument("--jobs", type=int, default=16, help="serve: number of arrivals")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -202,6 +388,15 @@ def main():
         build.build()
     if ws > 1:
         torch.distributed.barrier()
+
+    if args.workload in ("batch48", "serve"):
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        fn = run_batch if args.workload == "batch48" else run_serve
+        fn(args, P, torch, stream, ws, rank, local)
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
 
     cfg_id = WORKLOADS[args.workload]
     w = synth.WORKLOADS[cfg_id]
