@@ -260,8 +260,11 @@ pnp_status pnp_server_job_times(pnp_server* s, int64_t job_id, double* t_submit,
                                 double* t_done);
 pnp_status pnp_server_stats(pnp_server* s, int64_t* pixel_iters, int* active, int* queued,
                             size_t* used_bytes);
-/* Iterations per round between retire/admit points (default 8). */
-pnp_status pnp_server_set_round(pnp_server* s, int iters);
+/* Scheduling: in each round (between retire/admit points) a job runs
+ * iters x min(max_boost, largest active job's pixels / its pixels) iterations
+ * (never past its T), so small jobs finish early while large ones keep the
+ * batch full. Defaults 8 and 16; max_boost = 1 steps every job equally. */
+pnp_status pnp_server_set_round(pnp_server* s, int iters, int max_boost);
 void pnp_server_destroy(pnp_server* s);
 
 /* ------------------------------------------------------------------------

@@ -314,7 +314,7 @@ class Server:
     """Continuous-batching sampler service (pnp_server_create)."""
 
     def __init__(self, denoiser: Denoiser, precision="bf16", hbm_budget_bytes=64 << 30,
-                 stream=None, round_iters=8):
+                 stream=None, round_iters=8, max_boost=16):
         hdl = C.c_void_p()
         check(load().pnp_server_create(denoiser.handle if denoiser else None, _prec(precision),
                                        int(hbm_budget_bytes),
@@ -322,7 +322,7 @@ class Server:
         self.handle = hdl
         self._denoiser = denoiser
         self._shapes = {}
-        check(load().pnp_server_set_round(self.handle, int(round_iters)))
+        check(load().pnp_server_set_round(self.handle, int(round_iters), int(max_boost)))
 
     def submit(self, y, h, sigma, T, burn_in, **kw):
         d, keep = make_desc(y, h, sigma, None, burn_in=burn_in, **kw)

@@ -80,7 +80,7 @@ SIGNATURES = {
     "pnp_server_cancel": ([vp, i64], i32),
     "pnp_server_job_times": ([vp, i64, dp, dp, dp], i32),
     "pnp_server_stats": ([vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_size_t)], i32),
-    "pnp_server_set_round": ([vp, i32], i32),
+    "pnp_server_set_round": ([vp, i32, i32], i32),
     "pnp_server_destroy": ([vp], None),
     "pnp_kernel_timer": ([i32], i32),
     "pnp_kernel_timer_read": ([C.c_char_p, dp, C.POINTER(i64)], i32),

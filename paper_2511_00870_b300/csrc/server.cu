@@ -62,7 +62,9 @@ struct pnp_server {
     std::deque<ServerJob*> queue;
     std::map<int64_t, ServerJob*> jobs;
     std::vector<ServerJob*> active;
-    BatchPlan plan;
+    BatchPlan plan;                                          // all active jobs
+    std::map<std::vector<int64_t>, BatchPlan> subset_plans;  // rounds' smaller subsets
+    int max_boost = 16;
     bool stop = false;
     int64_t next_id = 1;
     int64_t pixel_iters = 0;
@@ -160,6 +162,8 @@ static void worker_loop(pnp_server* s) {
         std::vector<pnp_problem*> probs;
         for (ServerJob* j : s->active) probs.push_back(j->p);
         if (changed) {
+            for (auto& kv : s->subset_plans) plan_free(kv.second);
+            s->subset_plans.clear();
             pnp_status st = plan_build(s->plan, probs, s->stream);
             if (st != PNP_OK) {
                 // fail every active job; the server keeps serving new ones
@@ -178,17 +182,56 @@ static void worker_loop(pnp_server* s) {
             }
             changed = false;
         }
-        // a round: as many iterations as the closest job needs, at most round_iters
-        int k = s->round_iters;
-        for (ServerJob* j : s->active) k = (int)std::min<int64_t>(k, j->T - j->p->t);
-        k = std::max(k, 1);
+        // a round, pixel-fair: every job gets round_iters iterations scaled by
+        // (largest active job's pixels / its pixels), at most max_boost times more,
+        // and never past its T. Small jobs thus finish early while large ones keep
+        // the batch full; iteration i of the round steps the jobs with k_j > i.
+        std::vector<int64_t> kj(s->active.size());
+        int64_t pxmax = 1, kmax = 0;
+        for (ServerJob* j : s->active)
+            pxmax = std::max<int64_t>(pxmax, (int64_t)j->desc.ny * j->desc.nx * std::max(1, j->desc.nchain));
+        for (size_t q = 0; q < s->active.size(); ++q) {
+            ServerJob* j = s->active[q];
+            const int64_t px = (int64_t)j->desc.ny * j->desc.nx * std::max(1, j->desc.nchain);
+            int64_t k = s->round_iters * std::min<int64_t>(s->max_boost, std::max<int64_t>(1, pxmax / px));
+            k = std::max<int64_t>(1, std::min<int64_t>(k, j->T - j->p->t));
+            kj[q] = k;
+            kmax = std::max(kmax, k);
+        }
         pnp_status st = PNP_OK;
-        for (int i = 0; i < k && st == PNP_OK; ++i) st = plan_enqueue_step(s->plan, probs, s->stream);
+        std::vector<int64_t> prev_key;
+        const BatchPlan* cur = nullptr;
+        std::vector<pnp_problem*> sub;
+        for (int64_t i = 0; i < kmax && st == PNP_OK; ++i) {
+            std::vector<int64_t> key;
+            std::vector<pnp_problem*> members;
+            for (size_t q = 0; q < s->active.size(); ++q)
+                if (kj[q] > i) {
+                    key.push_back(s->active[q]->id);
+                    members.push_back(s->active[q]->p);
+                }
+            if (key != prev_key) {
+                if (key.size() == s->active.size()) {
+                    cur = &s->plan;
+                } else {
+                    auto it = s->subset_plans.find(key);
+                    if (it == s->subset_plans.end()) {
+                        it = s->subset_plans.emplace(key, BatchPlan()).first;
+                        st = plan_build(it->second, members, s->stream);
+                    }
+                    cur = &it->second;
+                }
+                prev_key = key;
+                sub = members;
+            }
+            if (st == PNP_OK) st = plan_enqueue_step(*cur, sub, s->stream);
+        }
         cudaError_t e = cudaStreamSynchronize(s->stream);
         int64_t pix = 0;
-        for (ServerJob* j : s->active) {
-            j->p->t += k;
-            pix += (int64_t)j->desc.ny * j->desc.nx * std::max(1, j->desc.nchain) * k;
+        for (size_t q = 0; q < s->active.size(); ++q) {
+            ServerJob* j = s->active[q];
+            j->p->t += kj[q];
+            pix += (int64_t)j->desc.ny * j->desc.nx * std::max(1, j->desc.nchain) * kj[q];
         }
         {
             std::lock_guard<std::mutex> g(s->mu);
@@ -368,10 +411,11 @@ extern "C" pnp_status pnp_server_stats(pnp_server* s, int64_t* pixel_iters, int*
     return PNP_OK;
 }
 
-extern "C" pnp_status pnp_server_set_round(pnp_server* s, int iters) {
-    if (!s || iters < 1) return fail(PNP_EINVAL, "pnp_server_set_round: bad arguments");
+extern "C" pnp_status pnp_server_set_round(pnp_server* s, int iters, int max_boost) {
+    if (!s || iters < 1 || max_boost < 1) return fail(PNP_EINVAL, "pnp_server_set_round: bad arguments");
     std::lock_guard<std::mutex> g(s->mu);
     s->round_iters = iters;
+    s->max_boost = max_boost;
     return PNP_OK;
 }
 
@@ -384,6 +428,7 @@ extern "C" void pnp_server_destroy(pnp_server* s) {
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
     plan_free(s->plan);
+    for (auto& kv : s->subset_plans) plan_free(kv.second);
     for (auto& kv : s->jobs) delete kv.second;
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
