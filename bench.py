@@ -368,7 +368,7 @@ def main():
     ap.add_argument("--workload", default="deconv1024", choices=sorted(WORKLOADS))
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precisions", default="bf16,fp32")
+    ap.add_argument("--precisions", default="bf16,fp32,fp8")
     ap.add_argument("--jobs", type=int, default=16, help="serve: number of arrivals")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -453,7 +453,7 @@ def main():
         P.pnp_kernel_timer(True)
         gp.step(max(5, min(args.steps, 20)))
         torch.cuda.synchronize()
-        name = "conv_tc" if prec == "bf16" else "conv_fp32"
+        name = "conv_fp32" if prec == "fp32" else "conv_tc"
         kms, kn = P.pnp_kernel_timer_read(name)
         tot = {k: P.pnp_kernel_timer_read(k) for k in ("blur", "update", "conv_fp32", "conv_tc",
                                                         "conv_edge")}
@@ -492,6 +492,8 @@ def main():
             gq.close()
         if "bf16" in precs and "fp32" in precs:
             quality["delta_db"] = round(quality["psnr_bf16_db"] - quality["psnr_fp32_db"], 4)
+        if "fp8" in precs and "fp32" in precs:
+            quality["delta_fp8_db"] = round(quality["psnr_fp8_db"] - quality["psnr_fp32_db"], 4)
         quality["chain"] = f"{w['T']} iterations, {w['burn_in']} burn-in"
 
     if rank != 0:
@@ -506,10 +508,12 @@ def main():
     if kern["name"] == "conv_tc":
         flop = 2.0 * F * F * 9 * pix_per_launch
         achieved = flop / (kern["avg_ms"] * 1e-3) / 1e12
+        pk = peaks["bf16_sus"] * (2 if precs[0] == "fp8" else 1)
         roof = dict(bound="tensor", achieved=round(achieved, 2),
-                    peak=peaks["bf16_sus"], unit="TFLOP/s",
-                    frac=round(achieved / peaks["bf16_sus"], 4), traffic=None,
-                    kernel="k_conv_tc", peak_kind=f"bf16 sustained ({peaks['src']})")
+                    peak=pk, unit="TFLOP/s",
+                    frac=round(achieved / pk, 4), traffic=None,
+                    kernel="k_conv_tc", peak_kind=f"{precs[0]} sustained ({peaks['src']}"
+                                                  + (", bf16 x nominal ratio 2)" if precs[0] == "fp8" else ")"))
     else:
         flop = 2.0 * F * F * 9 * pix_per_launch
         achieved = flop / (kern["avg_ms"] * 1e-3) / 1e12
@@ -547,6 +551,15 @@ def main():
                                   ms_per_step=round(results["fp32"]["ms"] / results["fp32"]["steps"], 4),
                                   steps=results["fp32"]["steps"],
                                   speedup_bf16=round(head["value"] / results["fp32"]["value"], 3))
+    if "fp8" in results and precs[0] != "fp8":
+        r8 = results["fp8"]
+        a8 = 2.0 * F * F * 9 * npix / (r8["kernel"]["avg_ms"] * 1e-3) / 1e12
+        line["fp8_variant"] = dict(
+            value=round(r8["value"], 3), unit=UNIT, ms_per_step=round(r8["ms"] / r8["steps"], 4),
+            steps=r8["steps"], speedup_vs_bf16=round(r8["value"] / head["value"], 3),
+            conv_tc_tflops=round(a8, 2), conv_tc_frac=round(a8 / (2 * peaks["bf16_sus"]), 4),
+            peak_kind="fp8 = measured bf16 sustained x nominal ratio 2",
+            note="E4M3 weights (per-output-channel scales) and activations (per-layer static scales)")
     if quality:
         line["quality"] = quality
     line["latency"] = dict(p50_s=None, p99_s=None, note="single-job workload; see --workload serve")

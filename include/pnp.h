@@ -78,6 +78,15 @@ pnp_status pnp_create_denoiser(int K, int F, const float* weights, const float* 
                                double lipschitz_eps, pnp_denoiser** out);
 void pnp_destroy_denoiser(pnp_denoiser* d);
 
+/* Static activation scales of the FP8 (E4M3) variant: runs the FP32 network
+ * on x (device [nimg][ny][nx]) and sets the scale of every layer's input to
+ * twice its largest activation / 448. Weights are quantised per output
+ * channel (amax / 448) at creation. pnp_denoise with PNP_FP8 calibrates on its
+ * own input and pnp_create_problem on the observation y if this was not
+ * called before. Synchronous; allocates temporary scratch. */
+pnp_status pnp_denoiser_calibrate_fp8(pnp_denoiser* d, const float* x, int ny, int nx, int nimg,
+                                      void* stream);
+
 /* ------------------------------------------------------------------------
  * Operator entry points (device pointers, asynchronous on `stream`).
  * ------------------------------------------------------------------------ */
@@ -213,7 +222,7 @@ pnp_status pnp_set_graph_mode(int enable);
 
 /* ------------------------------------------------------------------------
  * Batch: independent problems of different sizes stepped together (all with
- * the same denoiser and precision, halo = 0). One batch iteration = one
+ * the same denoiser and precision, FP32 or BF16, halo = 0). One batch iteration = one
  * iteration of every job; the denoiser's tensor-core layers run as one launch
  * per layer over the rows of all jobs, and the iteration is replayed as one
  * CUDA graph. Each job's chain is identical to the same problem run alone
@@ -240,7 +249,7 @@ int pnp_batch_size(const pnp_batch* b);
  * memory and the job's device memory is freed. Jobs that arrive while others
  * run join at the next round. Each job's chain is independent of which other
  * jobs share its steps. All served jobs use the server's denoiser and
- * precision; desc.halo must be 0; desc.stream is ignored. Thread-safe: submit,
+ * precision (FP32 or BF16); desc.halo must be 0; desc.stream is ignored. Thread-safe: submit,
  * poll, wait and cancel may be called from any host thread.
  * Job states: 0 queued, 1 running, 2 done, 3 failed, 4 cancelled.
  * ------------------------------------------------------------------------ */

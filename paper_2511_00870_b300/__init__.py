@@ -131,6 +131,11 @@ class Denoiser:
                                  blocks[1], halo, _ptr(out), _stream(stream)))
         return out
 
+    def calibrate_fp8(self, x, stream=None):
+        """pnp_denoiser_calibrate_fp8 on x [n, ny, nx] (CUDA float32)."""
+        n, ny, nx = x.shape
+        check(load().pnp_denoiser_calibrate_fp8(self.handle, _ptr(x), ny, nx, n, _stream(stream)))
+
     def denoise_noalloc(self, x, out, precision="fp32", stream=None):
         """pnp_denoise_noalloc: same result as denoise() with halo = 0, computed in
         the library's fixed scratch area instead of allocating; `out` is caller-owned."""

@@ -222,6 +222,50 @@ extern "C" pnp_status pnp_create_denoiser(int K, int F, const float* weights, co
             return st;
         }
         cudaMemcpy(D.wtc_last, blob_last.data(), blob_last.size() * 2, cudaMemcpyHostToDevice);
+        // E4M3 variant: per-output-channel scales amax / 448, same stacking with
+        // 16-channel groups: [dx][4 cg][rows][16 ci]
+        D.w8_scale = new float[(size_t)K * 64];
+        for (size_t i = 0; i < (size_t)K * 64; ++i) D.w8_scale[i] = 1.f;
+        for (int k = 1; k < K; ++k) {
+            const float* W = weights + src_off[k];
+            for (int co = 0; co < cout[k]; ++co) {
+                float m = 0.f;
+                for (int i = 0; i < 64 * 9; ++i) m = std::max(m, std::fabs(W[(int64_t)co * 64 * 9 + i]));
+                D.w8_scale[k * 64 + co] = m > 0.f ? m / 448.f : 1.f;
+            }
+        }
+        std::vector<float> st8((size_t)std::max(nmid, 1) * 3 * 4 * 192 * 16, 0.f);
+        for (int m = 0; m < nmid; ++m) {
+            const float* W = weights + src_off[m + 1];
+            for (int dx = 0; dx < 3; ++dx)
+                for (int cg = 0; cg < 4; ++cg)
+                    for (int dy = 0; dy < 3; ++dy)
+                        for (int co = 0; co < 64; ++co)
+                            for (int c16 = 0; c16 < 16; ++c16)
+                                st8[((((size_t)m * 3 + dx) * 4 + cg) * 192 + dy * 64 + co) * 16 + c16] =
+                                    W[((int64_t)co * 64 + cg * 16 + c16) * 9 + dy * 3 + dx] /
+                                    D.w8_scale[(m + 1) * 64 + co];
+        }
+        std::vector<float> st8l(3 * 4 * 16 * 16, 0.f);
+        for (int dx = 0; dx < 3; ++dx)
+            for (int cg = 0; cg < 4; ++cg)
+                for (int dy = 0; dy < 3; ++dy)
+                    for (int c16 = 0; c16 < 16; ++c16)
+                        st8l[(((size_t)dx * 4 + cg) * 16 + dy) * 16 + c16] =
+                            weights[src_off[K - 1] + (int64_t)(cg * 16 + c16) * 9 + dy * 3 + dx] /
+                            D.w8_scale[(K - 1) * 64];
+        float* stage = nullptr;
+        if ((st = dalloc(&D.wtc8, st8.size())) != PNP_OK || (st = dalloc(&D.wtc8_last, st8l.size())) != PNP_OK ||
+            (st = dalloc(&stage, st8.size())) != PNP_OK) {
+            pnp_destroy_denoiser(den);
+            return st;
+        }
+        cudaMemcpy(stage, st8.data(), st8.size() * 4, cudaMemcpyHostToDevice);
+        convert_e4m3(stage, D.wtc8, st8.size(), 0);
+        cudaMemcpy(stage, st8l.data(), st8l.size() * 4, cudaMemcpyHostToDevice);
+        convert_e4m3(stage, D.wtc8_last, st8l.size(), 0);
+        cudaDeviceSynchronize();
+        cudaFree(stage);
         D.h_first = new EdgeW();
         D.h_last = new EdgeW();
         memset(D.h_first, 0, sizeof(EdgeW));
@@ -266,6 +310,9 @@ extern "C" void pnp_destroy_denoiser(pnp_denoiser* den) {
     dfree(D.b32);
     dfree(D.wtc);
     dfree(D.wtc_last);
+    dfree(D.wtc8);
+    dfree(D.wtc8_last);
+    delete[] D.w8_scale;
     dfree(D.wfirst);
     dfree(D.wlast);
     dfree(den->scratch);
@@ -328,14 +375,16 @@ static std::vector<BlockDesc> make_blocks(int ny, int nx, int by, int bx, int ni
 
 static size_t denoise_scratch_bytes(const DenoiserDev& D, pnp_precision prec, int ny, int nx,
                                     int nimg) {
-    return prec == PNP_FP32 ? denoise_fp32_scratch(D, ny, nx, nimg)
-                            : denoise_bf16_scratch(D, ny, nx, nimg);
+    if (prec == PNP_FP32) return denoise_fp32_scratch(D, ny, nx, nimg);
+    if (prec == PNP_FP8) return denoise_fp8_scratch(D, ny, nx, nimg);
+    return denoise_bf16_scratch(D, ny, nx, nimg);
 }
 
 static cudaError_t run_denoise(const DenoiserDev& D, pnp_precision prec, const float* x, int ny,
                                int nx, int nimg, const Rect* rects, float* d, void* scratch,
                                cudaStream_t s) {
     if (prec == PNP_FP32) return denoise_fp32(D, x, ny, nx, nimg, rects, d, (float*)scratch, s);
+    if (prec == PNP_FP8) return denoise_fp8(D, x, ny, nx, nimg, rects, d, scratch, s);
     return denoise_bf16(D, x, ny, nx, nimg, rects, d, scratch, s);
 }
 
@@ -343,12 +392,48 @@ static pnp_status check_denoise_args(const pnp_denoiser* den, pnp_precision prec
                                      int nimg, int by, int bx, int halo) {
     if (!den) return fail(PNP_EINVAL, "denoiser is NULL");
     if (ny < 1 || nx < 1 || nimg < 1) return fail(PNP_EINVAL, "empty image");
-    if (prec != PNP_FP32 && prec != PNP_BF16)
-        return fail(PNP_ENOTSUP, "precision not supported by this build");
-    if (prec == PNP_BF16 && den->dev.F != 64) return fail(PNP_EINVAL, "BF16 path needs F = 64");
+    if (prec != PNP_FP32 && prec != PNP_BF16 && prec != PNP_FP8)
+        return fail(PNP_ENOTSUP, "unknown precision");
+    if (prec != PNP_FP32 && den->dev.F != 64) return fail(PNP_EINVAL, "BF16/FP8 paths need F = 64");
     if (halo < 0) return fail(PNP_EINVAL, "halo must be >= 0");
     if (halo > 0 && (by < 1 || bx < 1 || by > ny || bx > nx))
         return fail(PNP_EINVAL, "blocks must be >= 1 and <= the image size");
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_denoiser_calibrate_fp8(pnp_denoiser* den, const float* x, int ny, int nx,
+                                                 int nimg, void* stream) {
+    if (!den || !x || ny < 1 || nx < 1 || nimg < 1)
+        return fail(PNP_EINVAL, "pnp_denoiser_calibrate_fp8: bad arguments");
+    DenoiserDev& D = den->dev;
+    if (D.F != 64 || !D.wtc8) return fail(PNP_EINVAL, "FP8 variant needs F = 64");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t need = denoise_fp32_scratch(D, ny, nx, nimg);
+    float* scratch = nullptr;
+    float* dtmp = nullptr;
+    unsigned* amax = nullptr;
+    PNP_TRY(dalloc(&scratch, need / 4));
+    pnp_status st = dalloc(&dtmp, (size_t)nimg * ny * nx);
+    if (st == PNP_OK) st = dalloc(&amax, (size_t)D.K);
+    std::vector<unsigned> h(D.K, 0);
+    cudaError_t e = cudaSuccess;
+    if (st == PNP_OK) {
+        e = denoise_fp32_amax(D, x, ny, nx, nimg, dtmp, scratch, amax, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), amax, 4 * D.K, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    dfree(scratch);
+    dfree(dtmp);
+    dfree(amax);
+    if (st != PNP_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "pnp_denoiser_calibrate_fp8");
+    // input of layer k = output of layer k-1; headroom x2 over the calibration maximum
+    for (int k = 1; k < D.K; ++k) {
+        float m;
+        memcpy(&m, &h[k - 1], 4);
+        D.a8_scale[k] = (m > 0.f ? 2.f * m : 1.f) / 448.f;
+    }
+    D.fp8_calibrated = true;
     return PNP_OK;
 }
 
@@ -357,6 +442,8 @@ extern "C" pnp_status pnp_denoise(const pnp_denoiser* den, pnp_precision prec, c
                                   float* d, void* stream) {
     PNP_TRY(check_denoise_args(den, prec, ny, nx, nimg, blocks_y, blocks_x, halo));
     if (!x || !d) return fail(PNP_EINVAL, "pnp_denoise: NULL pointer");
+    if (prec == PNP_FP8 && !den->dev.fp8_calibrated)
+        PNP_TRY(pnp_denoiser_calibrate_fp8(const_cast<pnp_denoiser*>(den), x, ny, nx, nimg, stream));
     pnp_denoiser* dn = const_cast<pnp_denoiser*>(den);
     const DenoiserDev& D = den->dev;
     cudaStream_t s = (cudaStream_t)stream;
@@ -539,10 +626,10 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
     if (q.halo < 0) return fail(PNP_EINVAL, "halo must be >= 0");
     if (q.D && q.halo > 0 && q.halo < q.D->dev.K)
         return fail(PNP_EINVAL, "halo must cover the receptive field (halo >= K)");
-    if (q.precision != PNP_FP32 && q.precision != PNP_BF16)
-        return fail(PNP_ENOTSUP, "precision not supported by this build");
-    if (q.D && q.precision == PNP_BF16 && q.D->dev.F != 64)
-        return fail(PNP_EINVAL, "BF16 denoiser needs F = 64");
+    if (q.precision != PNP_FP32 && q.precision != PNP_BF16 && q.precision != PNP_FP8)
+        return fail(PNP_ENOTSUP, "unknown precision");
+    if (q.D && q.precision != PNP_FP32 && q.D->dev.F != 64)
+        return fail(PNP_EINVAL, "BF16/FP8 denoiser needs F = 64");
     const int64_t N = (int64_t)q.ny * q.nx;
     for (int64_t i = 0; i < N; ++i)
         if (!std::isfinite(q.y[i])) return fail(PNP_EINVAL, "y contains NaN or Inf");
@@ -654,6 +741,15 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
     cudaMemset(p->d, 0, NC * 4);
     StepState s0{0u, (int32_t)q.burn_in};
     cudaMemcpy(p->st, &s0, sizeof(s0), cudaMemcpyHostToDevice);
+    if (q.D && q.precision == PNP_FP8 && !q.D->dev.fp8_calibrated) {
+        // static activation scales from the observation y (x = y)
+        pnp_status cs = pnp_denoiser_calibrate_fp8(const_cast<pnp_denoiser*>(q.D), p->y, q.ny, q.nx, 1,
+                                                   p->stream);
+        if (cs != PNP_OK) {
+            pnp_destroy_problem(p);
+            return cs;
+        }
+    }
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         pnp_destroy_problem(p);

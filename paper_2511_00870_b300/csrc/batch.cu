@@ -93,10 +93,10 @@ pnp_status plan_enqueue_step(const BatchPlan& plan, const std::vector<pnp_proble
                 const TcJob* tab = plan.tables + ((k % 2 == 1) ? 0 : plan.n);   // A->B, B->A, ...
                 PNP_CUDA_TRY(tc_launch(dummy, tab, plan.n, plan.total_rows,
                                        D.wtc + (size_t)(k - 1) * (3 * 8 * 192 * 8), D.hb + 64 * k,
-                                       plan.err, false, s));
+                                       plan.err, false, s, false, nullptr, 1.f));
             }
             PNP_CUDA_TRY(tc_launch(dummy, plan.tables + 2 * (size_t)plan.n, plan.n, plan.total_rows,
-                                   D.wtc_last, &D.h_last->b[0], plan.err, true, s));
+                                   D.wtc_last, &D.h_last->b[0], plan.err, true, s, false, nullptr, 1.f));
         } else {
             for (pnp_problem* p : jobs)
                 PNP_CUDA_TRY(denoise_fp32(D, p->x, p->ny, p->nx, p->nchain, nullptr, p->d,
@@ -141,6 +141,8 @@ extern "C" pnp_status pnp_batch_create(const pnp_problem_desc* descs, int njobs,
             return fail(PNP_EINVAL, "pnp_batch_create: all jobs must share the denoiser and precision");
         if (descs[j].halo != 0)
             return fail(PNP_EINVAL, "pnp_batch_create: batched jobs use the direct layout (halo = 0)");
+        if (descs[j].precision != PNP_FP32 && descs[j].precision != PNP_BF16)
+            return fail(PNP_ENOTSUP, "pnp_batch_create: batches run FP32 or BF16 denoisers");
     }
     pnp_batch* b = new pnp_batch();
     if (stream) {

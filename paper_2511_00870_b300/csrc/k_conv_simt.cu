@@ -243,6 +243,50 @@ static cudaError_t denoise_fp32_F(const DenoiserDev& D, const float* x, int ny, 
     return cudaGetLastError();
 }
 
+// Largest value of a non-negative array (post-ReLU activations): the float
+// bit patterns of non-negative numbers order like unsigned integers.
+__global__ void k_amax(const float* __restrict__ a, size_t n, unsigned* __restrict__ out) {
+    float m = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, a[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+template <int F>
+static cudaError_t denoise_fp32_amax_F(const DenoiserDev& D, const float* x, int ny, int nx,
+                                       int nimg, float* d, float* scratch, unsigned* amax,
+                                       cudaStream_t s) {
+    const size_t act = (size_t)nimg * F * ny * nx;
+    float* A = scratch;
+    float* B = scratch + act;
+    const int grid = 4 * num_sms();
+    cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(unsigned) * D.K, s);
+    if (e == cudaSuccess)
+        e = launch_layer<1, F, true>(x, D.w32 + D.w32_off[0], D.b32 + D.b_off[0], ny, nx, nimg,
+                                     nullptr, A, s);
+    if (e != cudaSuccess) return e;
+    k_amax<<<grid, 256, 0, s>>>(A, act, amax + 0);
+    for (int k = 1; k < D.K - 1; ++k) {
+        e = launch_layer<F, F, true>(A, D.w32 + D.w32_off[k], D.b32 + D.b_off[k], ny, nx, nimg,
+                                     nullptr, B, s);
+        if (e != cudaSuccess) return e;
+        k_amax<<<grid, 256, 0, s>>>(B, act, amax + k);
+        float* t = A; A = B; B = t;
+    }
+    const int L = D.K - 1;
+    dim3 g(ceil_div(nx, CV_TX), ceil_div(ny, CV_TY), nimg);
+    k_conv3x3_last<F><<<g, CV_THREADS, 0, s>>>(A, D.w32 + D.w32_off[L], D.b32 + D.b_off[L], x, ny,
+                                               nx, d);
+    return cudaGetLastError();
+}
+
+cudaError_t denoise_fp32_amax(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
+                              float* d, float* scratch, unsigned* amax, cudaStream_t s) {
+    if (D.F != 64) return cudaErrorInvalidValue;
+    return denoise_fp32_amax_F<64>(D, x, ny, nx, nimg, d, scratch, amax, s);
+}
+
 size_t denoise_fp32_scratch(const DenoiserDev& D, int ny, int nx, int nimg) {
     return sizeof(float) * 2 * (size_t)nimg * D.F * ny * nx;
 }

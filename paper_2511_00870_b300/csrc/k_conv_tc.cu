@@ -36,6 +36,8 @@
 #include <algorithm>
 #include <cstring>
 
+#include <cuda_fp8.h>
+
 #include "pnp_internal.h"
 #include "tc_ptx.cuh"
 
@@ -76,13 +78,21 @@ static_assert(sizeof(TcJob) == 256 && alignof(TcJob) == 128, "TcJob layout");
 // F -> F layers (LAST = false): N = 3 x 64, kernel row dy in columns
 // [64 dy, 64 dy + 64). Last layer (LAST = true): its single output channel for
 // kernel rows dy = 0, 1, 2 in B rows 0, 1, 2 of one 16-row block (N = 16).
-template <bool LAST>
+// BF16 (FP8 = false): 8 channel groups of 8 per pixel, K = 16 per MMA.
+// E4M3 (FP8 = true): 4 channel groups of 16, K = 32 per MMA (kind::f8f6f4);
+// the shared-memory geometry (16-byte core-matrix rows, 2304-byte planes) is
+// the same, with half the planes.
+template <bool LAST, bool FP8>
 struct TcMode {
     static constexpr int NROW = LAST ? 1 : 64;
     static constexpr int NB = LAST ? 16 : 3 * NROW;
-    static constexpr int DX_W = 8 * NB * 16;
+    static constexpr int NCG = FP8 ? 4 : 8;             // 16-byte channel-group planes
+    static constexpr int KK = NCG / 2;                  // MMAs per column shift
+    static constexpr int ROWB = NCG * tc::CG_BYTES;     // bytes of one input row in smem
+    static constexpr int DX_W = NCG * NB * 16;
     static constexpr int WB = 3 * DX_W;
-    static constexpr uint32_t IDESC = ptx::idesc_bf16_f32(tc::SEG, NB);
+    static constexpr uint32_t IDESC = FP8 ? ptx::idesc_e4m3_f32(tc::SEG, NB)
+                                          : ptx::idesc_bf16_f32(tc::SEG, NB);
     static constexpr uint32_t B_LBO = (uint32_t)((NB * 16) >> 4) << 16;
 };
 static_assert(tc::SMEM <= 232448, "shared memory budget");
@@ -90,8 +100,10 @@ static_assert(tc::SMEM <= 232448, "shared memory budget");
 __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 
 struct TcCommon {
-    const __nv_bfloat16* wblob;   // [3 dx][8 cg][3 dy x 64 co][8 ci]
+    const void* wblob;            // [3 dx][cg][3 dy x 64 co][16 B of input channels]
     float bias[64];               // by value: constant-bank operands in the epilogue
+    float scale[64];              // E4M3: dequantisation scale per output channel
+    float inv_out;                // E4M3: 1 / scale of the output activations
     int* err;
     const TcJob* jobs;            // device table, or nullptr: the single job parameter
     int njobs;
@@ -126,16 +138,28 @@ __device__ __forceinline__ RowPos locate(const TcJob& job0, const TcCommon& c, i
 
 // D[tmem] (+)= A * B with both descriptors given by their low words (the
 // high words are the same constant).
+template <bool FP8>
 __device__ __forceinline__ void mma_lo(uint32_t d_tmem, uint32_t a_lo, uint32_t b_lo,
                                        uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n.reg .b64 da, db;\n.reg .pred p;\n"
-        "mov.b64 da, {%1, %2};\n"
-        "mov.b64 db, {%3, %2};\n"
-        "setp.ne.b32 p, %5, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n}\n" ::"r"(d_tmem),
-        "r"(a_lo), "r"(tc::DESC_HI), "r"(b_lo), "r"(idesc), "r"(accumulate)
-        : "memory");
+    if constexpr (FP8) {
+        asm volatile(
+            "{\n.reg .b64 da, db;\n.reg .pred p;\n"
+            "mov.b64 da, {%1, %2};\n"
+            "mov.b64 db, {%3, %2};\n"
+            "setp.ne.b32 p, %5, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], da, db, %4, p;\n}\n" ::"r"(d_tmem),
+            "r"(a_lo), "r"(tc::DESC_HI), "r"(b_lo), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n.reg .b64 da, db;\n.reg .pred p;\n"
+            "mov.b64 da, {%1, %2};\n"
+            "mov.b64 db, {%3, %2};\n"
+            "setp.ne.b32 p, %5, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n}\n" ::"r"(d_tmem),
+            "r"(a_lo), "r"(tc::DESC_HI), "r"(b_lo), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
 }
 
 // Epilogue helpers. TMEM column block `col` (64 columns) of this warp's lanes.
@@ -157,11 +181,11 @@ __device__ __forceinline__ void tm_load64(uint32_t taddr, float* acc) {
     for (int e = 0; e < 64; ++e) acc[e] = __uint_as_float(t[e]);
 }
 
-template <bool LAST>
+template <bool LAST, bool FP8>
 __global__ void __launch_bounds__(tc::THREADS, 1)
-    k_conv_tc(const __grid_constant__ TcJob job0, const TcCommon c) {
+    k_conv_tc(const __grid_constant__ TcJob job0, const __grid_constant__ TcCommon c) {
     using namespace tc;
-    using Mode = TcMode<LAST>;
+    using Mode = TcMode<LAST, FP8>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* ring = smem + OFF_RING;
@@ -220,7 +244,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 for (int r = p.y - 1; r <= p.y + p.len && ok; ++r, ++L) {
                     const uint32_t slot = L % NS, u = L / NS;
                     if (!ptx::mbar_wait(&empty[slot], (u & 1) ^ 1, abort_flag, BUDGET)) { ok = false; break; }
-                    ptx::mbar_arrive_expect_tx(&full[slot], ROW_BYTES);
+                    ptx::mbar_arrive_expect_tx(&full[slot], Mode::ROWB);
                     ptx::tma_load_5d(ring + slot * ROW_BYTES, &p.J->tin, &full[slot], 0,
                                      p.strip * (SEG / 8) - HALO_PX / 8, 0, r, p.img);
                 }
@@ -254,8 +278,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            mma_lo(d, a_row + kk * 2 * (CG_BYTES >> 4) + (HALO_PX - 1 + dx),
+                        for (int kk = 0; kk < Mode::KK; ++kk)
+                            mma_lo<FP8>(d, a_row + kk * 2 * (CG_BYTES >> 4) + (HALO_PX - 1 + dx),
                                    w_lo + dx * (Mode::DX_W >> 4) + kk * 2 * (Mode::NB * 16 >> 4),
                                    Mode::IDESC, (dx | kk) != 0);
                     issued = true;
@@ -294,7 +318,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     ptx::tmem_ld4(taddr, pr);
                     if (ri >= 1) {
                         Xprev += pr[2];
-                        if (in_img) dout[(int64_t)(p.y + ri - 1) * J->nx + x] = xv - (Xprev + c.bias[0]);
+                        const float G = FP8 ? fmaf(Xprev, c.scale[0], c.bias[0]) : Xprev + c.bias[0];
+                        if (in_img) dout[(int64_t)(p.y + ri - 1) * J->nx + x] = xv - G;
                     }
                     if (ri >= 0 && ri < p.len) Xcur += pr[1];
                     if (ri + 1 < p.len) Xprev = pr[0];
@@ -334,20 +359,44 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             auto store_row = [&](const float* acc, int yy) {
                 if (!col_ok) return;
                 const bool valid = x_valid && yy >= rc.y0 && yy < rc.y1;
-                __nv_bfloat16* o = obase + (int64_t)yy * 8 * nxp * 8;
+                if constexpr (FP8) {
+                    // E4M3 activations: [img][y][4 cg][xp][16]
+                    uint8_t* o = reinterpret_cast<uint8_t*>(J->out) +
+                                 (((int64_t)p.img * J->ny + yy) * 4 * nxp + x) * 16;
 #pragma unroll
-                for (int cg = 0; cg < 8; ++cg) {
-                    uint32_t pk[4];
+                    for (int cg = 0; cg < 4; ++cg) {
+                        uint32_t pk[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int c0 = cg * 8 + 2 * e;
-                        float v0 = fmaxf(acc[c0] + c.bias[c0], 0.f);
-                        float v1 = fmaxf(acc[c0 + 1] + c.bias[c0 + 1], 0.f);
-                        if (!valid) v0 = v1 = 0.f;
-                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
-                        pk[e] = *reinterpret_cast<uint32_t*>(&h2);
+                        for (int e = 0; e < 4; ++e) {
+                            float v[4];
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) {
+                                const int ch = cg * 16 + 4 * e + h;
+                                const float t = fmaxf(fmaf(acc[ch], c.scale[ch], c.bias[ch]), 0.f);
+                                v[h] = valid ? t * c.inv_out : 0.f;
+                            }
+                            const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[0], v[1]), __NV_SATFINITE, __NV_E4M3);
+                            const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v[2], v[3]), __NV_SATFINITE, __NV_E4M3);
+                            pk[e] = lo | (hi << 16);
+                        }
+                        *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     }
-                    *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                } else {
+                    __nv_bfloat16* o = obase + (int64_t)yy * 8 * nxp * 8;
+#pragma unroll
+                    for (int cg = 0; cg < 8; ++cg) {
+                        uint32_t pk[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int c0 = cg * 8 + 2 * e;
+                            float v0 = fmaxf(acc[c0] + c.bias[c0], 0.f);
+                            float v1 = fmaxf(acc[c0 + 1] + c.bias[c0 + 1], 0.f);
+                            if (!valid) v0 = v1 = 0.f;
+                            __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+                            pk[e] = *reinterpret_cast<uint32_t*>(&h2);
+                        }
+                        *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    }
                 }
             };
             // input row ri adds P^2 to output row ri-1 (then complete), P^1 to
@@ -394,11 +443,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 // reads its weight as a constant-bank operand (no load instruction). A warp's
 // store to one channel-group plane is 512 contiguous bytes.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_first_bf16(const float* __restrict__ x,
-                                                    const __grid_constant__ EdgeW W, int ny,
-                                                    int nx, int nxp,
-                                                    const Rect* __restrict__ rects,
-                                                    __nv_bfloat16* __restrict__ out) {
+template <bool FP8>
+__global__ void __launch_bounds__(128) k_first(const float* __restrict__ x,
+                                               const __grid_constant__ EdgeW W, int ny, int nx,
+                                               int nxp, const Rect* __restrict__ rects,
+                                               void* __restrict__ out_, float inv_out) {
     const int xx = blockIdx.x * blockDim.x + threadIdx.x;
     const int yy = blockIdx.y, img = blockIdx.z;
     if (xx >= nxp) return;
@@ -412,25 +461,49 @@ __global__ void __launch_bounds__(128) k_first_bf16(const float* __restrict__ x,
         v[t] = (sy >= 0 && sy < ny && sx >= 0 && sx < nx) ? __ldg(x + img * plane + (int64_t)sy * nx + sx)
                                                           : 0.f;
     }
-    __nv_bfloat16* o = out + ((((int64_t)img * ny + yy) * 8) * nxp + xx) * 8;
+    if constexpr (FP8) {
+        uint8_t* o = reinterpret_cast<uint8_t*>(out_) + (((int64_t)img * ny + yy) * 4 * nxp + xx) * 16;
 #pragma unroll
-    for (int cg = 0; cg < 8; ++cg) {
-        uint32_t pk[4];
+        for (int cg = 0; cg < 4; ++cg) {
+            uint32_t pk[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            float r2[2];
+            for (int e = 0; e < 4; ++e) {
+                float r4[4];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int co = cg * 8 + 2 * e + h;
-                float s = W.b[co];
+                for (int h = 0; h < 4; ++h) {
+                    const int co = cg * 16 + 4 * e + h;
+                    float s = W.b[co];
 #pragma unroll
-                for (int t = 0; t < 9; ++t) s = fmaf(W.w[t][co], v[t], s);
-                r2[h] = valid ? fmaxf(s, 0.f) : 0.f;
+                    for (int t = 0; t < 9; ++t) s = fmaf(W.w[t][co], v[t], s);
+                    r4[h] = valid ? fmaxf(s, 0.f) * inv_out : 0.f;
+                }
+                const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(r4[0], r4[1]), __NV_SATFINITE, __NV_E4M3);
+                const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(r4[2], r4[3]), __NV_SATFINITE, __NV_E4M3);
+                pk[e] = lo | (hi << 16);
             }
-            __nv_bfloat162 h2 = __floats2bfloat162_rn(r2[0], r2[1]);
-            pk[e] = *reinterpret_cast<uint32_t*>(&h2);
+            *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
-        *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    } else {
+        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out_) + ((((int64_t)img * ny + yy) * 8) * nxp + xx) * 8;
+#pragma unroll
+        for (int cg = 0; cg < 8; ++cg) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                float r2[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int co = cg * 8 + 2 * e + h;
+                    float s = W.b[co];
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) s = fmaf(W.w[t][co], v[t], s);
+                    r2[h] = valid ? fmaxf(s, 0.f) : 0.f;
+                }
+                __nv_bfloat162 h2 = __floats2bfloat162_rn(r2[0], r2[1]);
+                pk[e] = *reinterpret_cast<uint32_t*>(&h2);
+            }
+            *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
     }
 }
 
@@ -462,22 +535,27 @@ size_t denoise_bf16_scratch(const DenoiserDev& D, int ny, int nx, int nimg) {
     return 2 * (size_t)nimg * ny * bf16_pad_width(nx) * 64 * sizeof(__nv_bfloat16) + 256;
 }
 
-cudaError_t tc_make_job(TcJob* J, const __nv_bfloat16* in, __nv_bfloat16* out, int ny, int nx,
-                        int nimg, const Rect* rects, int64_t row_begin) {
+cudaError_t tc_make_job(TcJob* J, const void* in, void* out, int ny, int nx, int nimg,
+                        const Rect* rects, int64_t row_begin, bool fp8) {
     PFN_encodeTiled enc = get_encode();
     if (!enc) return cudaErrorNotSupported;
     memset(J, 0, sizeof(*J));
     const int nxp = bf16_pad_width(nx);
-    const cuuint64_t dims[5] = {64, (cuuint64_t)nxp / 8, 8, (cuuint64_t)ny, (cuuint64_t)nimg};
-    const cuuint64_t strides[4] = {128, (cuuint64_t)nxp * 16, (cuuint64_t)nxp * 128,
-                                   (cuuint64_t)nxp * 128 * ny};
-    const cuuint32_t box[5] = {64, tc::ROW_PX / 8, 8, 1, 1};
+    // dim0 = 8 pixels x one 16-byte channel group (128 B), dim1 = pixel octets,
+    // dim2 = channel groups (8 of BF16 x 8, or 4 of E4M3 x 16), dim3 = rows, dim4 = images
+    const int ncg = fp8 ? 4 : 8;
+    const cuuint64_t dims[5] = {(cuuint64_t)(fp8 ? 128 : 64), (cuuint64_t)nxp / 8, (cuuint64_t)ncg,
+                                (cuuint64_t)ny, (cuuint64_t)nimg};
+    const cuuint64_t strides[4] = {128, (cuuint64_t)nxp * 16, (cuuint64_t)nxp * 16 * ncg,
+                                   (cuuint64_t)nxp * 16 * ncg * ny};
+    const cuuint32_t box[5] = {(cuuint32_t)(fp8 ? 128 : 64), tc::ROW_PX / 8, (cuuint32_t)ncg, 1, 1};
     const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    CUresult r = enc(&J->tin, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)in, dims, strides, box, es,
+    CUresult r = enc(&J->tin, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                     5, (void*)in, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    J->out = out;
+    J->out = (__nv_bfloat16*)out;
     J->rects = rects;
     J->ny = ny;
     J->nx = nx;
@@ -490,15 +568,15 @@ cudaError_t tc_make_job(TcJob* J, const __nv_bfloat16* in, __nv_bfloat16* out, i
 }
 
 cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64_t total_rows,
-                      const __nv_bfloat16* wblob, const float* bias_host, int* err, bool last,
-                      cudaStream_t s) {
+                      const void* wblob, const float* bias_host, int* err, bool last,
+                      cudaStream_t s, bool fp8, const float* scale_host, float inv_out) {
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv_tc<false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_conv_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     tc::SMEM);
+        cudaError_t e = cudaSuccess;
+        for (auto f : {k_conv_tc<false, false>, k_conv_tc<true, false>, k_conv_tc<false, true>,
+                       k_conv_tc<true, true>})
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM);
         if (e != cudaSuccess) return e;
         configured = true;
     }
@@ -507,14 +585,22 @@ cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64
     c.wblob = wblob;
     memset(c.bias, 0, sizeof(c.bias));
     memcpy(c.bias, bias_host, (last ? 1 : 64) * sizeof(float));
+    memset(c.scale, 0, sizeof(c.scale));
+    if (scale_host) memcpy(c.scale, scale_host, (last ? 1 : 64) * sizeof(float));
+    c.inv_out = inv_out;
     c.err = err;
     c.jobs = jobs_dev;
     c.njobs = jobs_dev ? njobs : 1;
     c.total_rows = total_rows;
     const int grid = (int)std::min<int64_t>(num_sms(), total_rows);
     timer_begin(last ? T_CONV_EDGE : T_CONV_TC, s);
-    if (last) k_conv_tc<true><<<grid, tc::THREADS, tc::SMEM, s>>>(job0, c);
-    else k_conv_tc<false><<<grid, tc::THREADS, tc::SMEM, s>>>(job0, c);
+    if (fp8) {
+        if (last) k_conv_tc<true, true><<<grid, tc::THREADS, tc::SMEM, s>>>(job0, c);
+        else k_conv_tc<false, true><<<grid, tc::THREADS, tc::SMEM, s>>>(job0, c);
+    } else {
+        if (last) k_conv_tc<true, false><<<grid, tc::THREADS, tc::SMEM, s>>>(job0, c);
+        else k_conv_tc<false, false><<<grid, tc::THREADS, tc::SMEM, s>>>(job0, c);
+    }
     timer_end(last ? T_CONV_EDGE : T_CONV_TC, s);
     return cudaGetLastError();
 }
@@ -525,7 +611,7 @@ cudaError_t conv_tc_layer(const __nv_bfloat16* in, const __nv_bfloat16* wblob, c
     TcJob J;
     cudaError_t e = tc_make_job(&J, in, out, ny, nx, nimg, rects, 0);
     if (e != cudaSuccess) return e;
-    return tc_launch(J, nullptr, 1, J.rows, wblob, bias_host, err, false, s);
+    return tc_launch(J, nullptr, 1, J.rows, wblob, bias_host, err, false, s, false, nullptr, 1.f);
 }
 
 cudaError_t first_layer_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
@@ -533,7 +619,7 @@ cudaError_t first_layer_bf16(const DenoiserDev& D, const float* x, int ny, int n
     const int nxp = bf16_pad_width(nx);
     dim3 g1(ceil_div(nxp, 128), ny, nimg);
     timer_begin(T_CONV_EDGE, s);
-    k_first_bf16<<<g1, 128, 0, s>>>(x, *D.h_first, ny, nx, nxp, rects, out);
+    k_first<false><<<g1, 128, 0, s>>>(x, *D.h_first, ny, nx, nxp, rects, out, 1.f);
     timer_end(T_CONV_EDGE, s);
     return cudaGetLastError();
 }
@@ -545,7 +631,8 @@ cudaError_t last_layer_bf16(const DenoiserDev& D, const __nv_bfloat16* act, cons
     if (e != cudaSuccess) return e;
     J.xin = x;
     J.dout = d;
-    return tc_launch(J, nullptr, 1, J.rows, D.wtc_last, &D.h_last->b[0], err, true, s);
+    return tc_launch(J, nullptr, 1, J.rows, D.wtc_last, &D.h_last->b[0], err, true, s, false,
+                     nullptr, 1.f);
 }
 
 cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
@@ -566,6 +653,58 @@ cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, i
         __nv_bfloat16* t = A; A = B; B = t;
     }
     return last_layer_bf16(D, A, x, ny, nx, nimg, d, err, s);
+}
+
+__global__ void k_to_e4m3(const float* __restrict__ src, uint8_t* __restrict__ dst, size_t n) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (uint8_t)__nv_cvt_float_to_fp8(src[i], __NV_SATFINITE, __NV_E4M3);
+}
+
+cudaError_t convert_e4m3(const float* src, uint8_t* dst, size_t n, cudaStream_t s) {
+    k_to_e4m3<<<ceil_div((int64_t)n, 256), 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+size_t denoise_fp8_scratch(const DenoiserDev& D, int ny, int nx, int nimg) {
+    (void)D;
+    return 2 * (size_t)nimg * ny * bf16_pad_width(nx) * 64 + 256;
+}
+
+// E4M3 denoiser: activations quantised with the per-layer static scales
+// D.a8_scale (input of layer k), weights with per-output-channel scales.
+cudaError_t denoise_fp8(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
+                        const Rect* rects, float* d, void* scratch, cudaStream_t s) {
+    if (D.F != 64 || !D.wtc8 || !D.wtc8_last || !D.fp8_calibrated) return cudaErrorInvalidValue;
+    const int nxp = bf16_pad_width(nx);
+    const size_t act = (size_t)nimg * ny * nxp * 64;
+    uint8_t* A = (uint8_t*)scratch;
+    uint8_t* B = A + act;
+    int* err = (int*)(B + act);
+    dim3 g1(ceil_div(nxp, 128), ny, nimg);
+    timer_begin(T_CONV_EDGE, s);
+    k_first<true><<<g1, 128, 0, s>>>(x, *D.h_first, ny, nx, nxp, rects, A, 1.f / D.a8_scale[1]);
+    timer_end(T_CONV_EDGE, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t blob = 3 * 4 * 192 * 16;   // bytes of one F -> F layer
+    for (int k = 1; k < D.K - 1; ++k) {
+        TcJob J;
+        e = tc_make_job(&J, A, B, ny, nx, nimg, rects, 0, true);
+        if (e != cudaSuccess) return e;
+        float sc[64];
+        for (int c = 0; c < 64; ++c) sc[c] = D.a8_scale[k] * D.w8_scale[k * 64 + c];
+        e = tc_launch(J, nullptr, 1, J.rows, D.wtc8 + (size_t)(k - 1) * blob, D.hb + 64 * k, err,
+                      false, s, true, sc, 1.f / D.a8_scale[k + 1]);
+        if (e != cudaSuccess) return e;
+        uint8_t* t = A; A = B; B = t;
+    }
+    TcJob J;
+    e = tc_make_job(&J, A, nullptr, ny, nx, nimg, nullptr, 0, true);
+    if (e != cudaSuccess) return e;
+    J.xin = x;
+    J.dout = d;
+    const float sl = D.a8_scale[D.K - 1] * D.w8_scale[(D.K - 1) * 64];
+    return tc_launch(J, nullptr, 1, J.rows, D.wtc8_last, &D.h_last->b[0], err, true, s, true, &sl, 1.f);
 }
 
 }  // namespace pnp

@@ -72,6 +72,14 @@ struct DenoiserDev {
     __nv_bfloat16* wtc = nullptr;
     // last layer (F -> 1): [dx 3][cg 8][16 rows: kernel row dy in row dy][8 ci]
     __nv_bfloat16* wtc_last = nullptr;
+    // E4M3 variant: same blobs with 16-channel groups ([dx][4 cg][rows][16 ci]),
+    // per-output-channel weight scales (host, [K][64]) and per-layer static
+    // activation scales (host; a8_scale[k] = scale of layer k's input)
+    uint8_t* wtc8 = nullptr;
+    uint8_t* wtc8_last = nullptr;
+    float* w8_scale = nullptr;
+    float a8_scale[32] = {0};
+    bool fp8_calibrated = false;
     EdgeW* h_first = nullptr;   // host copies for the BF16 edge layers
     EdgeW* h_last = nullptr;
     // FP32 first/last layer weights in tap-major order for the BF16 path
@@ -152,14 +160,17 @@ struct TcJob {   // 256 B, 128-B aligned (the tensor map requires it)
     int ny, nx, nxp, strips, nimg, pad0, pad1, pad2;
 };
 int bf16_pad_width(int nx);
-cudaError_t tc_make_job(TcJob* J, const __nv_bfloat16* in, __nv_bfloat16* out, int ny, int nx,
-                        int nimg, const Rect* rects, int64_t row_begin);
+cudaError_t tc_make_job(TcJob* J, const void* in, void* out, int ny, int nx, int nimg,
+                        const Rect* rects, int64_t row_begin, bool fp8 = false);
 // jobs_dev == nullptr: run job0 alone (passed by value); else the device table.
 // bias_host: the layer's biases in host memory (passed by value to the kernel).
 // last: the F -> 1 layer fused with d = x - G(x) (wblob = last-layer blob).
+// fp8: E4M3 operands; scale_host = per-output-channel dequantisation scales,
+// inv_out = 1 / scale of the output activations.
 cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64_t total_rows,
-                      const __nv_bfloat16* wblob, const float* bias_host, int* err, bool last,
-                      cudaStream_t s);
+                      const void* wblob, const float* bias_host, int* err, bool last,
+                      cudaStream_t s, bool fp8 = false, const float* scale_host = nullptr,
+                      float inv_out = 1.f);
 cudaError_t first_layer_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
                              const Rect* rects, __nv_bfloat16* out, cudaStream_t s);
 cudaError_t last_layer_bf16(const DenoiserDev& D, const __nv_bfloat16* act, const float* x,
@@ -169,6 +180,14 @@ cudaError_t last_layer_bf16(const DenoiserDev& D, const __nv_bfloat16* act, cons
 cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
                          const Rect* rects, float* d, void* scratch, cudaStream_t s);
 size_t denoise_bf16_scratch(const DenoiserDev& D, int ny, int nx, int nimg);
+cudaError_t denoise_fp8(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
+                        const Rect* rects, float* d, void* scratch, cudaStream_t s);
+size_t denoise_fp8_scratch(const DenoiserDev& D, int ny, int nx, int nimg);
+// FP32 denoiser that also records the largest activation of every layer's
+// output (amax_dev[k], k < K-1; activations are >= 0 after ReLU).
+cudaError_t denoise_fp32_amax(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
+                              float* d, float* scratch, unsigned* amax_dev, cudaStream_t s);
+cudaError_t convert_e4m3(const float* src, uint8_t* dst, size_t n, cudaStream_t s);
 
 // Block-with-halo gather / scatter (Sec. II-B2 receptive-field variant).
 struct BlockDesc {

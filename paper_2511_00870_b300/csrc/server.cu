@@ -275,7 +275,8 @@ static void worker_loop(pnp_server* s) {
 extern "C" pnp_status pnp_server_create(const pnp_denoiser* D, pnp_precision prec,
                                         size_t hbm_budget_bytes, void* stream, pnp_server** out) {
     if (!out || hbm_budget_bytes == 0) return fail(PNP_EINVAL, "pnp_server_create: bad arguments");
-    if (prec != PNP_FP32 && prec != PNP_BF16) return fail(PNP_ENOTSUP, "precision not supported");
+    if (prec != PNP_FP32 && prec != PNP_BF16)
+        return fail(PNP_ENOTSUP, "the server runs FP32 or BF16 denoisers");
     if (D && prec == PNP_BF16 && D->dev.F != 64) return fail(PNP_EINVAL, "BF16 serving needs F = 64");
     pnp_server* s = new pnp_server();
     s->D = D;
