@@ -47,6 +47,18 @@ WORKLOADS = {
 }
 
 
+def ncu_traffic(kernel, workload, precision):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split()
+        if len(f) == 5 and not f[0].startswith("#") and f[:3] == [kernel, workload, precision]:
+            return int(f[3]) + int(f[4])
+    return None
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -509,10 +521,11 @@ def main():
         flop = 2.0 * F * F * 9 * pix_per_launch
         achieved = flop / (kern["avg_ms"] * 1e-3) / 1e12
         pk = peaks["bf16_sus"] * (2 if precs[0] == "fp8" else 1)
+        ktag = "k_conv_tc<0,1>" if precs[0] == "fp8" else "k_conv_tc<0,0>"
         roof = dict(bound="tensor", achieved=round(achieved, 2),
                     peak=pk, unit="TFLOP/s",
-                    frac=round(achieved / pk, 4), traffic=None,
-                    kernel="k_conv_tc", peak_kind=f"{precs[0]} sustained ({peaks['src']}"
+                    frac=round(achieved / pk, 4), traffic=ncu_traffic(ktag, args.workload, precs[0]),
+                    kernel=ktag, peak_kind=f"{precs[0]} sustained ({peaks['src']}"
                                                   + (", bf16 x nominal ratio 2)" if precs[0] == "fp8" else ")"))
     else:
         flop = 2.0 * F * F * 9 * pix_per_launch

@@ -380,12 +380,12 @@ static size_t denoise_scratch_bytes(const DenoiserDev& D, pnp_precision prec, in
     return denoise_bf16_scratch(D, ny, nx, nimg);
 }
 
-static cudaError_t run_denoise(const DenoiserDev& D, pnp_precision prec, const float* x, int ny,
+static cudaError_t run_denoise(const DenoiserDev& D, pnp_precision prec, bool residual, const float* x, int ny,
                                int nx, int nimg, const Rect* rects, float* d, void* scratch,
                                cudaStream_t s) {
     if (prec == PNP_FP32) return denoise_fp32(D, x, ny, nx, nimg, rects, d, (float*)scratch, s);
-    if (prec == PNP_FP8) return denoise_fp8(D, x, ny, nx, nimg, rects, d, scratch, s);
-    return denoise_bf16(D, x, ny, nx, nimg, rects, d, scratch, s);
+    if (prec == PNP_FP8) return denoise_fp8(D, x, ny, nx, nimg, rects, d, scratch, s, residual);
+    return denoise_bf16(D, x, ny, nx, nimg, rects, d, scratch, s, residual);
 }
 
 static pnp_status check_denoise_args(const pnp_denoiser* den, pnp_precision prec, int ny, int nx,
@@ -458,7 +458,7 @@ extern "C" pnp_status pnp_denoise(const pnp_denoiser* den, pnp_precision prec, c
             PNP_CUDA_TRY(cudaMemset(dn->scratch, 0, need));
             dn->scratch_bytes = need;
         }
-        PNP_CUDA_TRY(run_denoise(D, prec, x, ny, nx, nimg, nullptr, d, dn->scratch, s));
+        PNP_CUDA_TRY(run_denoise(D, prec, false, x, ny, nx, nimg, nullptr, d, dn->scratch, s));
         return PNP_OK;
     }
     // block + halo: gather extended blocks, run the network per tile, scatter interiors
@@ -489,7 +489,7 @@ extern "C" pnp_status pnp_denoise(const pnp_denoiser* den, pnp_precision prec, c
     BlockDesc* blocks = (BlockDesc*)p;
     PNP_CUDA_TRY(cudaMemcpyAsync(blocks, bl.data(), nb * sizeof(BlockDesc), cudaMemcpyHostToDevice, s));
     PNP_CUDA_TRY(launch_gather_blocks(x, ny, nx, blocks, nb, halo, ty, tx, tiles, rects, s));
-    PNP_CUDA_TRY(run_denoise(D, prec, tiles, ty, tx, nb, rects, dtiles, net_scratch, s));
+    PNP_CUDA_TRY(run_denoise(D, prec, false, tiles, ty, tx, nb, rects, dtiles, net_scratch, s));
     PNP_CUDA_TRY(launch_scatter_blocks(dtiles, ny, nx, blocks, nb, halo, ty, tx, d, s));
     PNP_CUDA_TRY(cudaStreamSynchronize(s));   // the host block table must outlive the copy
     return PNP_OK;
@@ -523,6 +523,7 @@ static pnp_status fill_update_params(UpdateParams& u, float* x, const float* r, 
     u.m2 = nullptr;
     u.inv_n = 0.f;
     u.burn_dev = nullptr;
+    u.d_residual = 0;
     return PNP_OK;
 }
 
@@ -585,6 +586,7 @@ pnp_status problem_post(pnp_problem* p, cudaStream_t s) {
     u.burn_dev = &p->st->burn_in;
     u.mean = p->mean;
     u.m2 = p->m2;
+    u.d_residual = p->prec != PNP_FP32;   // the tensor-core denoisers hand over G = x - D(x)
     PNP_CUDA_TRY(launch_langevin_update(u, s));
     PNP_CUDA_TRY(launch_advance(p->st, s));
     return PNP_OK;
@@ -599,12 +601,12 @@ static pnp_status enqueue_iteration(pnp_problem* p) {
     if (prior) {
         const DenoiserDev& D = p->D->dev;
         if (p->halo == 0) {
-            PNP_CUDA_TRY(run_denoise(D, p->prec, p->x, p->ny, p->nx, p->nchain, nullptr, p->d,
+            PNP_CUDA_TRY(run_denoise(D, p->prec, p->prec != PNP_FP32, p->x, p->ny, p->nx, p->nchain, nullptr, p->d,
                                      p->scratch, s));
         } else {
             PNP_CUDA_TRY(launch_gather_blocks(p->x, p->ny, p->nx, p->blocks, p->nblocks, p->halo,
                                               p->ty, p->tx, p->tiles, p->rects, s));
-            PNP_CUDA_TRY(run_denoise(D, p->prec, p->tiles, p->ty, p->tx, p->nblocks, p->rects,
+            PNP_CUDA_TRY(run_denoise(D, p->prec, p->prec != PNP_FP32, p->tiles, p->ty, p->tx, p->nblocks, p->rects,
                                      p->dtiles, p->scratch, s));
             PNP_CUDA_TRY(launch_scatter_blocks(p->dtiles, p->ny, p->nx, p->blocks, p->nblocks,
                                                p->halo, p->ty, p->tx, p->d, s));

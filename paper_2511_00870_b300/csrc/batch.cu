@@ -57,7 +57,7 @@ pnp_status plan_build(BatchPlan& plan, const std::vector<pnp_problem*>& jobs, cu
         // after K-2 F -> F layers starting in A the activations are in B if K-2 is odd
         __nv_bfloat16* fin = ((K - 2) % 2 == 1) ? B : A;
         PNP_CUDA_TRY(tc_make_job(last, fin, nullptr, p->ny, p->nx, p->nchain, nullptr, row));
-        last->xin = p->x;
+        last->xin = nullptr;   // the chain's update takes the residual G = x - D(x)
         last->dout = p->d;
         row += ab->rows;
     }

@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 const int x = p.strip * SEG + jx;
                 const bool in_img = x < J->nx;
                 const int64_t plane = (int64_t)J->ny * J->nx;
-                const float* xin = J->xin + p.img * plane;
+                const float* xin = J->xin ? J->xin + p.img * plane : nullptr;
                 float* dout = J->dout + p.img * plane;
                 auto step = [&](float& Xprev, float& Xcur, int ri, uint32_t taddr, float xv) {
                     float pr[4];
@@ -319,7 +319,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     if (ri >= 1) {
                         Xprev += pr[2];
                         const float G = FP8 ? fmaf(Xprev, c.scale[0], c.bias[0]) : Xprev + c.bias[0];
-                        if (in_img) dout[(int64_t)(p.y + ri - 1) * J->nx + x] = xv - G;
+                        // d = x - G, or the residual G itself when no x is given
+                        if (in_img) dout[(int64_t)(p.y + ri - 1) * J->nx + x] = xin ? xv - G : G;
                     }
                     if (ri >= 0 && ri < p.len) Xcur += pr[1];
                     if (ri + 1 < p.len) Xprev = pr[0];
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 for (int ri = -1; ri <= p.len; ++ri, ++L) {
                     const uint32_t reg = L & 1, u = L >> 1;
                     // x of the output row this step completes, loaded before the wait
-                    const float xv = (ri >= 1 && in_img) ? __ldg(xin + (int64_t)(p.y + ri - 1) * J->nx + x) : 0.f;
+                    const float xv = (xin && ri >= 1 && in_img) ? __ldg(xin + (int64_t)(p.y + ri - 1) * J->nx + x) : 0.f;
                     if (!ptx::mbar_wait(&tfull[reg], u & 1, abort_flag, BUDGET)) { ok = false; break; }
                     ptx::tc_fence_after();
                     const uint32_t taddr = lane_base + reg * NB;
@@ -629,14 +630,14 @@ cudaError_t last_layer_bf16(const DenoiserDev& D, const __nv_bfloat16* act, cons
     TcJob J;
     cudaError_t e = tc_make_job(&J, act, nullptr, ny, nx, nimg, nullptr, 0);
     if (e != cudaSuccess) return e;
-    J.xin = x;
+    J.xin = x;   // nullptr: write the residual G instead of d = x - G
     J.dout = d;
     return tc_launch(J, nullptr, 1, J.rows, D.wtc_last, &D.h_last->b[0], err, true, s, false,
                      nullptr, 1.f);
 }
 
 cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
-                         const Rect* rects, float* d, void* scratch, cudaStream_t s) {
+                         const Rect* rects, float* d, void* scratch, cudaStream_t s, bool residual) {
     if (D.F != 64 || !D.wtc || !D.wtc_last || !D.h_first || !D.h_last) return cudaErrorInvalidValue;
     const int nxp = bf16_pad_width(nx);
     const size_t act = (size_t)nimg * ny * nxp * 64;
@@ -652,7 +653,7 @@ cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, i
         if (e != cudaSuccess) return e;
         __nv_bfloat16* t = A; A = B; B = t;
     }
-    return last_layer_bf16(D, A, x, ny, nx, nimg, d, err, s);
+    return last_layer_bf16(D, A, residual ? nullptr : x, ny, nx, nimg, d, err, s);
 }
 
 __global__ void k_to_e4m3(const float* __restrict__ src, uint8_t* __restrict__ dst, size_t n) {
@@ -673,7 +674,7 @@ size_t denoise_fp8_scratch(const DenoiserDev& D, int ny, int nx, int nimg) {
 // E4M3 denoiser: activations quantised with the per-layer static scales
 // D.a8_scale (input of layer k), weights with per-output-channel scales.
 cudaError_t denoise_fp8(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
-                        const Rect* rects, float* d, void* scratch, cudaStream_t s) {
+                        const Rect* rects, float* d, void* scratch, cudaStream_t s, bool residual) {
     if (D.F != 64 || !D.wtc8 || !D.wtc8_last || !D.fp8_calibrated) return cudaErrorInvalidValue;
     const int nxp = bf16_pad_width(nx);
     const size_t act = (size_t)nimg * ny * nxp * 64;
@@ -701,7 +702,7 @@ cudaError_t denoise_fp8(const DenoiserDev& D, const float* x, int ny, int nx, in
     TcJob J;
     e = tc_make_job(&J, A, nullptr, ny, nx, nimg, nullptr, 0, true);
     if (e != cudaSuccess) return e;
-    J.xin = x;
+    J.xin = residual ? nullptr : x;
     J.dout = d;
     const float sl = D.a8_scale[D.K - 1] * D.w8_scale[(D.K - 1) * 64];
     return tc_launch(J, nullptr, 1, J.rows, D.wtc8_last, &D.h_last->b[0], err, true, s, true, &sl, 1.f);

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(ST_THREADS) k_update(UpdateParams p) {
         const int64_t n = (int64_t)i * nx + j;
         const float xv = xc[n];
         float v = xv - p.gamma * (g[q] * p.inv_s2);
-        if (dc) v += p.c_prior * (__ldg(dc + n) - xv);
+        if (dc) v += p.d_residual ? -p.c_prior * __ldg(dc + n) : p.c_prior * (__ldg(dc + n) - xv);
         const float pr = fminf(fmaxf(xv, 0.f), 1.f);
         v += p.c_proj * (pr - xv);
         v += p.c_noise * z[q];

@@ -133,6 +133,7 @@ struct UpdateParams {
     float inv_n;        // 1 / n_kept (0: no accumulation)
     const int32_t* burn_dev;   // if non-null: sample number n = t + 1 - *burn_dev,
                                // accumulated when n > 0 (graph replay)
+    int d_residual;            // d holds G = x - D(x) instead of D(x)
 };
 cudaError_t launch_langevin_update(const UpdateParams& p, cudaStream_t s);
 cudaError_t launch_finalize_moments(const float* mean, const float* m2, int64_t npix,
@@ -177,11 +178,15 @@ cudaError_t last_layer_bf16(const DenoiserDev& D, const __nv_bfloat16* act, cons
                             int ny, int nx, int nimg, float* d, int* err, cudaStream_t s);
 
 // BF16 tcgen05 denoiser (F = 64). scratch must hold denoise_bf16_scratch() bytes.
+// residual = true: write G = x - D(x) instead of d = D(x) (the chain's update
+// takes either; the tensor-core last layer then reads no x).
 cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
-                         const Rect* rects, float* d, void* scratch, cudaStream_t s);
+                         const Rect* rects, float* d, void* scratch, cudaStream_t s,
+                         bool residual = false);
 size_t denoise_bf16_scratch(const DenoiserDev& D, int ny, int nx, int nimg);
 cudaError_t denoise_fp8(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
-                        const Rect* rects, float* d, void* scratch, cudaStream_t s);
+                        const Rect* rects, float* d, void* scratch, cudaStream_t s,
+                        bool residual = false);
 size_t denoise_fp8_scratch(const DenoiserDev& D, int ny, int nx, int nimg);
 // FP32 denoiser that also records the largest activation of every layer's
 // output (amax_dev[k], k < K-1; activations are >= 0 after ReLU).
