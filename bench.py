@@ -123,6 +123,42 @@ def dist_setup():
     return ws, rank, local
 
 
+# Replicas: every rank runs its own independent problems (no data-path
+# collective); timing is bracketed by barriers and the whole-job rate is all
+# ranks' pixel-iterations over the slowest rank's time.
+def rank_barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _rank_reduce(v, ws, op, device):
+    if ws == 1:
+        return float(v)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=op)
+    return t.item()
+
+
+def rank_max(v, ws, device="cuda"):
+    import torch.distributed as dist
+    return _rank_reduce(v, ws, dist.ReduceOp.MAX if ws > 1 else None, device)
+
+
+def rank_sum(v, ws, device="cuda"):
+    import torch.distributed as dist
+    return _rank_reduce(v, ws, dist.ReduceOp.SUM if ws > 1 else None, device)
+
+
+def replica_rate(pix_iters, seconds, ws, device="cuda"):
+    """(Mpixel-iters/s of the whole job, slowest rank's seconds)."""
+    tot = rank_sum(pix_iters, ws, device)
+    slow = rank_max(seconds, ws, device)
+    return tot / slow / 1e6, slow
+
+
 def _oracle_setup(cfg_id, crop):
     import oracle
     if cfg_id == 4:
@@ -233,6 +269,8 @@ def run_batch(args, P, torch, stream, ws, rank, local):
         b = P.Batch(jobs, den, precision=prec, stream=stream.cuda_stream)
         b.step(args.warmup)
         torch.cuda.synchronize()
+        rank_barrier(ws)
+        torch.cuda.synchronize()
         sampler = ClockSampler(local)
         sampler.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -240,9 +278,10 @@ def run_batch(args, P, torch, stream, ws, rank, local):
         b.step(steps)
         e1.record(stream)
         torch.cuda.synchronize()
+        rank_barrier(ws)
         ck = sampler.stop()
-        ms = e0.elapsed_time(e1)
-        out[prec] = dict(ms=ms, steps=steps, value=npix * steps / (ms * 1e3), clocks=ck)
+        rate, slow = replica_rate(npix * steps, e0.elapsed_time(e1) / 1e3, ws)
+        out[prec] = dict(ms=slow * 1e3, steps=steps, value=rate, clocks=ck)
         if prec == "bf16":
             P.pnp_kernel_timer(True)
             b.step(10)
@@ -256,7 +295,7 @@ def run_batch(args, P, torch, stream, ws, rank, local):
     achieved = 2.0 * 64 * 64 * 9 * npix / (out["bf16"]["conv_tc_avg_ms"] * 1e-3) / 1e12
     sizes = [p.y.shape[0] for p in probs]
     line = dict(
-        metric=METRIC, value=round(out["bf16"]["value"] * ws, 3), unit=UNIT, n_gpus=ws,
+        metric=METRIC, value=round(out["bf16"]["value"], 3), unit=UNIT, n_gpus=ws,
         steps=args.steps, warmup=args.warmup, ms_per_step=round(out["bf16"]["ms"] / args.steps, 4),
         higher_is_better=True, scaling="weak", vs_baseline=None, dtype="bf16", data="synthetic",
         config=dict(workload=f"batch48: 48 problems, sizes log-uniform 256..2048 (min {min(sizes)}, "
@@ -294,7 +333,7 @@ def run_serve(args, P, torch, stream, ws, rank, local):
     free, total = torch.cuda.mem_get_info()
     srv = P.Server(den, precision="bf16", hbm_budget_bytes=int(0.8 * free), round_iters=8)
     ids = [None] * n
-    t_start = time.perf_counter()
+    t_start = 0.0
 
     def submitter():
         for k in range(n):
@@ -304,6 +343,8 @@ def run_serve(args, P, torch, stream, ws, rank, local):
             p = probs[k]
             ids[k] = srv.submit(p.y, p.h, p.sigma, T, TB, seed=p.seed)
 
+    rank_barrier(ws)
+    t_start = time.perf_counter()
     sampler = ClockSampler(local)
     sampler.start()
     thr = th.Thread(target=submitter)
@@ -316,7 +357,7 @@ def run_serve(args, P, torch, stream, ws, rank, local):
     lat = [t["done"] - t["submit"] for t in times]
     span = max(t["done"] for t in times) - min(t["submit"] for t in times)
     pix_iters = sum(p.y.size for p in probs) * T
-    value = pix_iters / span / 1e6
+    value, _ = replica_rate(pix_iters, span, ws)
     # quality at equal PSNR on the first (smallest-index) job: BF16 served vs FP32 plain chain
     q = probs[0]
     _, mm16, _ = srv.poll(ids[0])
@@ -346,7 +387,7 @@ def run_serve(args, P, torch, stream, ws, rank, local):
     d2h = sum(2 * p.y.size * 8 for p in probs)
     iters = n * T
     line = dict(
-        metric=METRIC, value=round(value * ws, 3), unit=UNIT, n_gpus=ws, steps=T, warmup=0,
+        metric=METRIC, value=round(value, 3), unit=UNIT, n_gpus=ws, steps=T, warmup=0,
         ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="bf16",
         data="synthetic",
         config=dict(workload=f"serve: first {n} jobs of a Poisson stream at 20 jobs/s, sizes "
@@ -363,7 +404,7 @@ def run_serve(args, P, torch, stream, ws, rank, local):
         quality=dict(job=f"{q.y.shape[0]}x{q.y.shape[1]}", psnr_bf16_served_db=round(psnr(mm16), 4),
                      psnr_fp32_plain_db=round(psnr(mm32), 4),
                      delta_db=round(psnr(mm16) - psnr(mm32), 4)),
-        e2e=dict(value=round(value * ws, 3), unit=UNIT, h2d_bytes_per_step=h2d / iters,
+        e2e=dict(value=round(value, 3), unit=UNIT, h2d_bytes_per_step=h2d / iters,
                  d2h_bytes_per_step=d2h / iters,
                  note="the served path is end to end: host inputs in, host MMSE/std out"),
         clocks=ck,
@@ -426,15 +467,7 @@ def main():
         precs = ["fp32"]
 
     def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
-
-    def max_over_ranks(v):
-        if ws == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return t.item()
+        rank_barrier(ws)
 
     results = {}
     clocks = None
@@ -456,9 +489,8 @@ def main():
         torch.cuda.synchronize()
         barrier()
         ck = sampler.stop()
-        ms = e0.elapsed_time(e1)
-        ms_max = max_over_ranks(ms)
-        results[prec] = dict(ms=ms_max, steps=steps, value=ws * npix * steps / (ms_max * 1e3))
+        rate, slow = replica_rate(npix * steps, e0.elapsed_time(e1) / 1e3, ws)
+        results[prec] = dict(ms=slow * 1e3, steps=steps, value=rate)
         if prec == precs[0]:
             clocks = ck
         # dominant-kernel timing: same iterations launched eagerly with CUDA events
@@ -468,10 +500,11 @@ def main():
         name = "conv_fp32" if prec == "fp32" else "conv_tc"
         kms, kn = P.pnp_kernel_timer_read(name)
         tot = {k: P.pnp_kernel_timer_read(k) for k in ("blur", "update", "conv_fp32", "conv_tc",
-                                                        "conv_edge")}
+                                                        "conv_edge", "conv_last")}
         P.pnp_kernel_timer(False)
         results[prec]["kernel"] = dict(name=name, avg_ms=kms / max(kn, 1), launches=kn,
-                                       breakdown={k: v[0] for k, v in tot.items()})
+                                       breakdown={k: v[0] for k, v in tot.items()},
+                                       counts={k: v[1] for k, v in tot.items()})
         gp.close()
 
     # end-to-end through the public API with host buffers: create (H2D of y, h),
@@ -484,9 +517,9 @@ def main():
                    burn_in=0, precision=prec0, stream=stream.cuda_stream)
     gp.run_chain(args.steps, 0)
     mm, sd, _ = gp.moments()
-    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    e2e_rate, t_e2e = replica_rate(npix * args.steps, time.perf_counter() - t0, ws)
     gp.close()
-    e2e = dict(value=ws * npix * args.steps / t_e2e / 1e6, unit=UNIT,
+    e2e = dict(value=e2e_rate, unit=UNIT,
                h2d_bytes_per_step=(prob.y.size * 4 + prob.h.size * 4) / args.steps,
                d2h_bytes_per_step=2 * npix * 8 / args.steps)
 
@@ -534,7 +567,22 @@ def main():
         roof = dict(bound="alu", achieved=round(achieved, 2), peak=round(alu_peak, 2),
                     unit="TFLOP/s", frac=round(achieved / alu_peak, 4), traffic=None,
                     kernel="k_conv3x3<64,64>", peak_kind="FP32 FFMA: 148 SM x 128 lanes x 2 x max clock")
-    launches_per_step = (K + 3) if precs[0] == "bf16" else (K + 3)
+    # stencils against HBM: algorithmic bytes per pixel = r = Hx - y: read x, y,
+    # write r (12 B); update while sampling: read r, x, d, mean, m2, write x,
+    # mean, m2 (32 B)
+    stencils = {}
+    for kname, bpp in (("blur", 12), ("update", 32)):
+        n = kern["counts"].get(kname, 0)
+        if n:
+            avg = kern["breakdown"][kname] / n
+            gbs = bpp * npix / (avg * 1e-3) / 1e9
+            stencils[kname] = dict(avg_us=round(avg * 1e3, 2), bytes_per_pixel=bpp,
+                                   achieved_gbs=round(gbs, 1), frac=round(gbs / peaks["hbm"], 4))
+    if stencils:
+        stencils["peak_gbs"] = peaks["hbm"]
+        stencils["peak_kind"] = f"HBM copy ({peaks['src']})"
+    # blur, K conv layers, update (the update's last block advances the step counter)
+    launches_per_step = K + 2
     cpu = None
     if not args.no_cpu_baseline:
         try:
@@ -558,6 +606,7 @@ def main():
         gpu_launches=launches_per_step * args.steps,
         clocks=clocks,
         kernel_breakdown_ms={p: results[p]["kernel"]["breakdown"] for p in results},
+        stencil_roofline=stencils,
     )
     if "fp32" in results and precs[0] != "fp32":
         line["fp32_plain"] = dict(value=round(results["fp32"]["value"], 3), unit=UNIT,

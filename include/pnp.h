@@ -217,8 +217,33 @@ pnp_status pnp_get_state(pnp_problem* p, float* x, int64_t* t);
 pnp_status pnp_set_state(pnp_problem* p, const float* x, int64_t t);
 /* Device pointer of the chain state x [nchain][ny][nx] (valid until destroy). */
 float* pnp_problem_x_device(pnp_problem* p);
-/* Replay one captured CUDA graph per iteration (default on) or launch eagerly. */
+/* Replay captured CUDA graphs (one of 8 iterations, plus a one-iteration graph
+ * for remainders; default on) or launch every kernel eagerly. */
 pnp_status pnp_set_graph_mode(int enable);
+/* Programmatic dependent launch between the kernels of an iteration (default
+ * on): a kernel's prologue (barriers, TMEM, weights) overlaps its
+ * predecessor's tail. Changes timings only, never results. */
+pnp_status pnp_set_pdl(int enable);
+
+/* ------------------------------------------------------------------------
+ * Stencil tile shapes (library tuning; the paper has no counterpart). The
+ * H / H^T stencils and the fused update (Eq. 8) run with one of
+ * pnp_stencil_tile_count() tile shapes; pnp_create_problem times them all on
+ * the new problem's buffers and keeps the fastest for each kernel (cached per
+ * image size, kernel size and chain count). Every shape sums each output in
+ * the same order, so the choice changes timings, never results.
+ * pnp_set_stencil_tile(k) forces shape k for every later stencil launch
+ * (operators and problems, all threads); k = -1 restores the per-problem
+ * choice. PNP_EINVAL for k outside [-1, count). A blur kernel that is rank
+ * one up to FP32 rounding (h = u v^T, |h - u v^T|_F <= 1e-7 |h|_F: Gaussian,
+ * uniform) runs as two 1-D passes (kh + kw instead of kh kw FMAs per pixel).
+ * pnp_problem_stencil_tiles reports a problem's tile choices and whether it
+ * uses the separable form (any pointer may be NULL).
+ * ------------------------------------------------------------------------ */
+int pnp_stencil_tile_count(void);
+pnp_status pnp_set_stencil_tile(int tile);
+pnp_status pnp_problem_stencil_tiles(const pnp_problem* p, int* blur_tile, int* update_tile,
+                                     int* separable);
 
 /* ------------------------------------------------------------------------
  * Batch: independent problems of different sizes stepped together (all with
@@ -278,7 +303,8 @@ void pnp_server_destroy(pnp_server* s);
 
 /* ------------------------------------------------------------------------
  * Instrumentation: CUDA events around every launch of the hot kernels
- * ("blur", "update", "conv_fp32", "conv_tc", "conv_edge"). Enabling resets
+ * ("blur", "update", "conv_fp32", "conv_tc", "conv_edge" = first layer and the
+ * FP32 last layer, "conv_last" = tensor-core last layer). Enabling resets
  * the counters and forces eager launches (no graph replay). Reading
  * synchronizes the device and returns the summed device time and launches.
  * ------------------------------------------------------------------------ */

@@ -90,6 +90,20 @@ def pnp_set_graph_mode(enable: bool):
     check(load().pnp_set_graph_mode(int(bool(enable))))
 
 
+def pnp_set_pdl(enable: bool):
+    """Programmatic dependent launch between the kernels of an iteration (default on)."""
+    check(load().pnp_set_pdl(int(bool(enable))))
+
+
+def pnp_stencil_tile_count() -> int:
+    return int(load().pnp_stencil_tile_count())
+
+
+def pnp_set_stencil_tile(tile: int):
+    """Force stencil tile shape `tile` for every later launch (-1: per-problem choice)."""
+    check(load().pnp_set_stencil_tile(int(tile)))
+
+
 def pnp_kernel_timer(enable: bool):
     check(load().pnp_kernel_timer(int(bool(enable))))
 
@@ -212,6 +226,12 @@ class Problem:
         check(load().pnp_problem_params(self.handle, C.byref(lam), C.byref(gam), C.byref(al),
                                         C.byref(ep)))
         return dict(lam=lam.value, gamma=gam.value, alpha=al.value, eps=ep.value)
+
+    def stencil_tiles(self):
+        """(blur tile, update tile, separable) picked for this problem."""
+        b, u, s = C.c_int(), C.c_int(), C.c_int()
+        check(load().pnp_problem_stencil_tiles(self.handle, C.byref(b), C.byref(u), C.byref(s)))
+        return b.value, u.value, bool(s.value)
 
     def step(self, n=1):
         check(load().pnp_step(self.handle, int(n)))

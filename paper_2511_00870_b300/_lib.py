@@ -67,6 +67,10 @@ SIGNATURES = {
     "pnp_set_state": ([vp, fp, i64], i32),
     "pnp_problem_x_device": ([vp], vp),
     "pnp_set_graph_mode": ([i32], i32),
+    "pnp_set_pdl": ([i32], i32),
+    "pnp_stencil_tile_count": ([], i32),
+    "pnp_set_stencil_tile": ([i32], i32),
+    "pnp_problem_stencil_tiles": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], i32),
     "pnp_batch_create": ([C.POINTER(ProblemDesc), i32, vp, C.POINTER(vp)], i32),
     "pnp_batch_destroy": ([vp], None),
     "pnp_batch_step": ([vp, i32], i32),

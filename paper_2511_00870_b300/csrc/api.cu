@@ -45,7 +45,9 @@ struct TimerSlot {
 };
 static TimerSlot g_timers[T_COUNT];
 static bool g_timing = false;
-static const char* g_timer_names[T_COUNT] = {"blur", "update", "conv_fp32", "conv_tc", "conv_edge"};
+static bool g_pdl = true;
+bool pdl_enabled() { return g_pdl; }
+static const char* g_timer_names[T_COUNT] = {"blur", "update", "conv_fp32", "conv_tc", "conv_edge", "conv_last"};
 
 bool timer_enabled() { return g_timing; }
 void timer_begin(int id, cudaStream_t s) {
@@ -70,13 +72,6 @@ void timer_end(int id, cudaStream_t s) {
 cudaError_t conv_tc_layer(const __nv_bfloat16* in, const __nv_bfloat16* wblob, const float* bias_host,
                           int ny, int nx, int nimg, const Rect* rects, __nv_bfloat16* out,
                           int* err, cudaStream_t s);
-
-__global__ void k_advance(StepState* st) { st->t += 1; }
-
-cudaError_t launch_advance(StepState* st, cudaStream_t s) {
-    k_advance<<<1, 1, 0, s>>>(st);
-    return cudaGetLastError();
-}
 
 }  // namespace pnp
 
@@ -118,6 +113,13 @@ static uint16_t f32_to_bf16_rne(float f) {
     const uint32_t lsb = (u >> 16) & 1u;
     u += 0x7fffu + lsb;
     return (uint16_t)(u >> 16);
+}
+
+static float bf16_to_f32(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
 }
 
 // ------------------------------------------------------------------ misc API
@@ -217,6 +219,25 @@ extern "C" pnp_status pnp_create_denoiser(int K, int F, const float* weights, co
                     for (int c8 = 0; c8 < 8; ++c8)
                         blob_last[(((size_t)dx * 8 + cg) * 16 + dy) * 8 + c8] =
                             f32_to_bf16_rne(weights[src_off[K - 1] + (int64_t)(cg * 8 + c8) * 9 + dy * 3 + dx]);
+        // first layer: [kc][co][8], K = [w_hi(9) | w_hi(9) | w_lo(9) | b_hi | b_lo | 0 0 0]
+        std::vector<uint16_t> blob_first(4 * 64 * 8, 0);
+        for (int co = 0; co < 64; ++co) {
+            auto put = [&](int k, float v) { blob_first[((size_t)(k / 8) * 64 + co) * 8 + k % 8] = f32_to_bf16_rne(v); };
+            auto head = [](float v) { return bf16_to_f32(f32_to_bf16_rne(v)); };
+            for (int t = 0; t < 9; ++t) {
+                const float w = weights[src_off[0] + (int64_t)co * 9 + t];
+                put(t, w);
+                put(9 + t, w);
+                put(18 + t, w - head(w));
+            }
+            put(27, biases[co]);
+            put(28, biases[co] - head(biases[co]));
+        }
+        if ((st = dalloc(&D.wtc_first, blob_first.size())) != PNP_OK) {
+            pnp_destroy_denoiser(den);
+            return st;
+        }
+        cudaMemcpy(D.wtc_first, blob_first.data(), blob_first.size() * 2, cudaMemcpyHostToDevice);
         if ((st = dalloc(&D.wtc_last, blob_last.size())) != PNP_OK) {
             pnp_destroy_denoiser(den);
             return st;
@@ -266,33 +287,14 @@ extern "C" pnp_status pnp_create_denoiser(int K, int F, const float* weights, co
         convert_e4m3(stage, D.wtc8_last, st8l.size(), 0);
         cudaDeviceSynchronize();
         cudaFree(stage);
-        D.h_first = new EdgeW();
-        D.h_last = new EdgeW();
-        memset(D.h_first, 0, sizeof(EdgeW));
-        memset(D.h_last, 0, sizeof(EdgeW));
         int64_t b_last = 0;
         for (int k = 0; k < K - 1; ++k) b_last += cout[k];
-        for (int t = 0; t < 9; ++t)
-            for (int c = 0; c < 64; ++c) {
-                D.h_first->w[t][c] = weights[src_off[0] + (int64_t)c * 9 + t];
-                D.h_last->w[t][c] = weights[src_off[K - 1] + (int64_t)c * 9 + t];
-            }
-        for (int c = 0; c < 64; ++c) D.h_first->b[c] = biases[c];
-        D.h_last->b[0] = biases[b_last];
-        std::vector<float> wf(9 * 64), wl(9 * 64);
-        for (int t = 0; t < 9; ++t)
-            for (int c = 0; c < 64; ++c) {
-                wf[t * 64 + c] = weights[src_off[0] + (int64_t)c * 9 + t];
-                wl[t * 64 + c] = weights[src_off[K - 1] + (int64_t)c * 9 + t];
-            }
-        if ((st = dalloc(&D.wtc, blob.size())) != PNP_OK || (st = dalloc(&D.wfirst, 9 * 64)) != PNP_OK ||
-            (st = dalloc(&D.wlast, 9 * 64)) != PNP_OK) {
+        D.last_bias = biases[b_last];
+        if ((st = dalloc(&D.wtc, blob.size())) != PNP_OK) {
             pnp_destroy_denoiser(den);
             return st;
         }
         cudaMemcpy(D.wtc, blob.data(), blob.size() * 2, cudaMemcpyHostToDevice);
-        cudaMemcpy(D.wfirst, wf.data(), wf.size() * 4, cudaMemcpyHostToDevice);
-        cudaMemcpy(D.wlast, wl.data(), wl.size() * 4, cudaMemcpyHostToDevice);
     }
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -310,18 +312,15 @@ extern "C" void pnp_destroy_denoiser(pnp_denoiser* den) {
     dfree(D.b32);
     dfree(D.wtc);
     dfree(D.wtc_last);
+    dfree(D.wtc_first);
     dfree(D.wtc8);
     dfree(D.wtc8_last);
     delete[] D.w8_scale;
-    dfree(D.wfirst);
-    dfree(D.wlast);
     dfree(den->scratch);
     delete[] D.w32_off;
     delete[] D.b_off;
     delete[] D.hw;
     delete[] D.hb;
-    delete D.h_first;
-    delete D.h_last;
     delete den;
 }
 
@@ -524,6 +523,9 @@ static pnp_status fill_update_params(UpdateParams& u, float* x, const float* r, 
     u.inv_n = 0.f;
     u.burn_dev = nullptr;
     u.d_residual = 0;
+    u.arrive = nullptr;
+    u.tile = -1;
+    u.hsep = nullptr;
     return PNP_OK;
 }
 
@@ -561,9 +563,11 @@ extern "C" void pnp_destroy_problem(pnp_problem* p) {
     if (!p) return;
     if (p->stream) cudaStreamSynchronize(p->stream);
     if (p->graph) cudaGraphExecDestroy(p->graph);
+    if (p->graph_batch) cudaGraphExecDestroy(p->graph_batch);
     for (void* q : {(void*)p->y, (void*)p->h, (void*)p->x, (void*)p->r, (void*)p->d,
                     (void*)p->mean, (void*)p->m2, (void*)p->blocks, (void*)p->tiles,
-                    (void*)p->dtiles, (void*)p->rects, p->scratch, (void*)p->st})
+                    (void*)p->dtiles, (void*)p->rects, p->scratch, (void*)p->st,
+                    (void*)p->hsep})
         dfree(q);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
     delete p;
@@ -572,23 +576,33 @@ extern "C" void pnp_destroy_problem(pnp_problem* p) {
 namespace pnp {
 
 pnp_status problem_pre(pnp_problem* p, cudaStream_t s) {
-    PNP_CUDA_TRY(launch_blur(p->x, p->y, p->h, p->kh, p->kw, p->ny, p->nx, p->nchain, p->r, s));
+    PNP_CUDA_TRY(launch_blur(p->x, p->y, p->h, p->kh, p->kw, p->ny, p->nx, p->nchain, p->r, s,
+                             p->blur_tile, p->hsep));
     return PNP_OK;
 }
 
-pnp_status problem_post(pnp_problem* p, cudaStream_t s) {
+// The update of one iteration on the problem's buffers; the kernel reads the
+// step counter from the device and its last block advances it.
+static pnp_status problem_update_params(const pnp_problem* p, UpdateParams& u) {
     const bool prior = p->D && p->alpha != 0.0;
-    UpdateParams u;
     PNP_TRY(fill_update_params(u, p->x, p->r, prior ? p->d : nullptr, p->h, p->kh, p->kw, p->ny,
                                p->nx, p->nchain, p->sigma, p->alpha, p->eps, p->lambda, p->gamma,
                                p->seed, 1));
     u.t_dev = &p->st->t;
     u.burn_dev = &p->st->burn_in;
+    u.arrive = &p->st->arrive;
     u.mean = p->mean;
     u.m2 = p->m2;
     u.d_residual = p->prec != PNP_FP32;   // the tensor-core denoisers hand over G = x - D(x)
+    u.tile = p->update_tile;
+    u.hsep = p->hsep;
+    return PNP_OK;
+}
+
+pnp_status problem_post(pnp_problem* p, cudaStream_t s) {
+    UpdateParams u;
+    PNP_TRY(problem_update_params(p, u));
     PNP_CUDA_TRY(launch_langevin_update(u, s));
-    PNP_CUDA_TRY(launch_advance(p->st, s));
     return PNP_OK;
 }
 
@@ -613,6 +627,60 @@ static pnp_status enqueue_iteration(pnp_problem* p) {
         }
     }
     return problem_post(p, s);
+}
+
+// Rank-one split of the blur kernel: h = u v^T up to FP32 rounding
+// (|h - u v^T|_F <= 1e-7 |h|_F; Gaussian and uniform kernels are rank one, a
+// motion kernel is not). The top singular pair comes from power iteration in
+// FP64. out = [u (kh) | v (kw) | u reversed | v reversed], the reversed pair
+// being the taps of the flipped kernel used by the forward operator.
+static bool separable_taps(const float* h, int kh, int kw, std::vector<float>& out) {
+    if (kh < 2 || kw < 2) return false;
+    std::vector<double> u(kh, 0.0), v(kw, 1.0 / std::sqrt((double)kw));
+    double sig = 0.0, hn = 0.0;
+    for (int i = 0; i < kh * kw; ++i) hn += (double)h[i] * h[i];
+    if (!(hn > 0)) return false;
+    for (int it = 0; it < 200; ++it) {
+        double nu = 0.0;
+        for (int a = 0; a < kh; ++a) {
+            double s = 0.0;
+            for (int b = 0; b < kw; ++b) s += (double)h[a * kw + b] * v[b];
+            u[a] = s;
+            nu += s * s;
+        }
+        nu = std::sqrt(nu);
+        if (!(nu > 0)) return false;
+        for (double& x : u) x /= nu;
+        double nv = 0.0;
+        for (int b = 0; b < kw; ++b) {
+            double s = 0.0;
+            for (int a = 0; a < kh; ++a) s += (double)h[a * kw + b] * u[a];
+            v[b] = s;
+            nv += s * s;
+        }
+        sig = std::sqrt(nv);
+        if (!(sig > 0)) return false;
+        for (double& x : v) x /= sig;
+    }
+    double res = 0.0, su = 0.0;
+    for (int a = 0; a < kh; ++a)
+        for (int b = 0; b < kw; ++b) {
+            const double d = (double)h[a * kw + b] - sig * u[a] * v[b];
+            res += d * d;
+        }
+    if (res > 1e-14 * hn) return false;
+    for (double x : u) su += x;
+    const double sgn = su < 0 ? -1.0 : 1.0, rs = std::sqrt(sig);
+    out.assign(2 * (kh + kw), 0.f);
+    for (int a = 0; a < kh; ++a) {
+        out[a] = (float)(sgn * rs * u[a]);
+        out[kh + kw + a] = (float)(sgn * rs * u[kh - 1 - a]);
+    }
+    for (int b = 0; b < kw; ++b) {
+        out[kh + b] = (float)(sgn * rs * v[b]);
+        out[2 * kh + kw + b] = (float)(sgn * rs * v[kw - 1 - b]);
+    }
+    return true;
 }
 
 extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_problem** out) {
@@ -735,13 +803,47 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
 #undef ALLOC
     cudaMemcpy(p->y, q.y, N * 4, cudaMemcpyHostToDevice);
     cudaMemcpy(p->h, q.h, (size_t)q.kh * q.kw * 4, cudaMemcpyHostToDevice);
+    {
+        std::vector<float> sep;
+        if (separable_taps(q.h, q.kh, q.kw, sep)) {
+            if ((st = dalloc(&p->hsep, sep.size())) != PNP_OK) {
+                pnp_destroy_problem(p);
+                return st;
+            }
+            cudaMemcpy(p->hsep, sep.data(), sep.size() * 4, cudaMemcpyHostToDevice);
+        }
+    }
+    {
+        // stencil tile shapes, timed on this problem's buffers before they are initialised
+        cudaMemset(p->x, 0, NC * 4);
+        cudaMemset(p->r, 0, NC * 4);
+        cudaMemset(p->d, 0, NC * 4);
+        cudaMemset(p->mean, 0, NC * 4);
+        cudaMemset(p->m2, 0, NC * 4);
+        UpdateParams u;
+        pnp_status us = problem_update_params(p, u);
+        if (us == PNP_OK) {
+            u.t_dev = nullptr;
+            u.burn_dev = nullptr;
+            u.arrive = nullptr;
+            u.inv_n = 1.0f;   // time the sampling form (Welford traffic included)
+            cudaError_t e = stencil_autotune(p->x, p->y, p->h, p->hsep, p->kh, p->kw, p->ny,
+                                             p->nx, p->nchain, p->r, u, p->stream,
+                                             &p->blur_tile, &p->update_tile);
+            if (e != cudaSuccess) us = cuda_fail(e, "stencil autotune");
+        }
+        if (us != PNP_OK) {
+            pnp_destroy_problem(p);
+            return us;
+        }
+    }
     if (q.x0) cudaMemcpy(p->x, q.x0, NC * 4, cudaMemcpyHostToDevice);
     else cudaMemset(p->x, 0, NC * 4);
     cudaMemset(p->mean, 0, NC * 4);
     cudaMemset(p->m2, 0, NC * 4);
     cudaMemset(p->r, 0, NC * 4);
     cudaMemset(p->d, 0, NC * 4);
-    StepState s0{0u, (int32_t)q.burn_in};
+    StepState s0{0u, (int32_t)q.burn_in, 0u};
     cudaMemcpy(p->st, &s0, sizeof(s0), cudaMemcpyHostToDevice);
     if (q.D && q.precision == PNP_FP8 && !q.D->dev.fp8_calibrated) {
         // static activation scales from the observation y (x = y)
@@ -771,22 +873,22 @@ extern "C" pnp_status pnp_problem_params(const pnp_problem* p, double* lambda, d
     return PNP_OK;
 }
 
-static pnp_status ensure_graph(pnp_problem* p) {
-    if (p->graph) return PNP_OK;
-    // first, make sure every launcher did its one-time setup outside capture
+// Captures `iters` iterations of the problem into one executable graph.
+static pnp_status capture_graph(pnp_problem* p, int iters, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
     PNP_CUDA_TRY(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
-    pnp_status st = enqueue_iteration(p);
+    pnp_status st = PNP_OK;
+    for (int i = 0; i < iters && st == PNP_OK; ++i) st = enqueue_iteration(p);
     cudaError_t e = cudaStreamEndCapture(p->stream, &g);
     if (st != PNP_OK) {
         if (g) cudaGraphDestroy(g);
         return st;
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&p->graph, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        p->graph = nullptr;
+        *out = nullptr;
         return cuda_fail(e, "cudaGraphInstantiate");
     }
     return PNP_OK;
@@ -824,6 +926,28 @@ extern "C" pnp_status pnp_set_graph_mode(int enable) {
     return PNP_OK;
 }
 
+extern "C" pnp_status pnp_set_pdl(int enable) {
+    g_pdl = enable != 0;
+    return PNP_OK;
+}
+
+extern "C" int pnp_stencil_tile_count(void) { return stencil_tile_count(); }
+
+extern "C" pnp_status pnp_set_stencil_tile(int tile) {
+    if (!set_forced_stencil_tile(tile))
+        return fail(PNP_EINVAL, "pnp_set_stencil_tile: tile must be -1 or in [0, count)");
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_problem_stencil_tiles(const pnp_problem* p, int* blur_tile,
+                                                int* update_tile, int* separable) {
+    if (!p) return fail(PNP_EINVAL, "problem is NULL");
+    if (blur_tile) *blur_tile = p->blur_tile;
+    if (update_tile) *update_tile = p->update_tile;
+    if (separable) *separable = p->hsep != nullptr;
+    return PNP_OK;
+}
+
 extern "C" pnp_status pnp_step(pnp_problem* p, int n_iters) {
     if (!p || n_iters < 0) return fail(PNP_EINVAL, "pnp_step: bad arguments");
     if (n_iters == 0) return PNP_OK;
@@ -834,9 +958,14 @@ extern "C" pnp_status pnp_step(pnp_problem* p, int n_iters) {
             p->t += 1;
             --n_iters;
             if (n_iters == 0) return PNP_OK;
-            PNP_TRY(ensure_graph(p));
+            PNP_TRY(capture_graph(p, 1, &p->graph));
         }
-        for (int i = 0; i < n_iters; ++i) PNP_CUDA_TRY(cudaGraphLaunch(p->graph, p->stream));
+        if (n_iters >= kGraphBatch && !p->graph_batch)
+            PNP_TRY(capture_graph(p, kGraphBatch, &p->graph_batch));
+        int left = n_iters;
+        for (; left >= kGraphBatch; left -= kGraphBatch)
+            PNP_CUDA_TRY(cudaGraphLaunch(p->graph_batch, p->stream));
+        for (; left > 0; --left) PNP_CUDA_TRY(cudaGraphLaunch(p->graph, p->stream));
     } else {
         for (int i = 0; i < n_iters; ++i) PNP_TRY(enqueue_iteration(p));
     }
@@ -894,7 +1023,7 @@ extern "C" pnp_status pnp_set_state(pnp_problem* p, const float* x, int64_t t) {
     if (x) {
         PNP_CUDA_TRY(cudaMemcpyAsync(p->x, x, (size_t)p->N * p->nchain * 4, cudaMemcpyHostToDevice, p->stream));
     }
-    StepState s0{(uint32_t)t, (int32_t)p->burn_in};
+    StepState s0{(uint32_t)t, (int32_t)p->burn_in, 0u};
     PNP_CUDA_TRY(cudaMemcpyAsync(p->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, p->stream));
     PNP_CUDA_TRY(cudaStreamSynchronize(p->stream));
     p->t = t;

@@ -85,7 +85,7 @@ pnp_status plan_enqueue_step(const BatchPlan& plan, const std::vector<pnp_proble
                 __nv_bfloat16 *A, *B;
                 int* err;
                 bf16_planes(p, &A, &B, &err);
-                PNP_CUDA_TRY(first_layer_bf16(D, p->x, p->ny, p->nx, p->nchain, nullptr, A, s));
+                PNP_CUDA_TRY(first_layer_bf16(D, p->x, p->ny, p->nx, p->nchain, nullptr, A, err, s));
             }
             TcJob dummy;
             memset(&dummy, 0, sizeof(dummy));
@@ -96,7 +96,7 @@ pnp_status plan_enqueue_step(const BatchPlan& plan, const std::vector<pnp_proble
                                        plan.err, false, s, false, nullptr, 1.f));
             }
             PNP_CUDA_TRY(tc_launch(dummy, plan.tables + 2 * (size_t)plan.n, plan.n, plan.total_rows,
-                                   D.wtc_last, &D.h_last->b[0], plan.err, true, s, false, nullptr, 1.f));
+                                   D.wtc_last, &D.last_bias, plan.err, true, s, false, nullptr, 1.f));
         } else {
             for (pnp_problem* p : jobs)
                 PNP_CUDA_TRY(denoise_fp32(D, p->x, p->ny, p->nx, p->nchain, nullptr, p->d,

@@ -38,6 +38,7 @@
 
 #include <cuda_fp8.h>
 
+#include "pdl.cuh"
 #include "pnp_internal.h"
 #include "tc_ptx.cuh"
 
@@ -50,20 +51,11 @@ constexpr int HALO_PX = 8;                  // smem row starts 8 px left of the 
 constexpr int ROW_PX = SEG + 2 * HALO_PX;   // 144
 constexpr int CG_BYTES = ROW_PX * 16;       // 2304: one channel-group plane of a row
 constexpr int ROW_BYTES = 8 * CG_BYTES;     // 18432
-constexpr int NS = 8;                       // input-row ring slots
-constexpr int NACC = 2;                     // TMEM regions of 192 columns (double buffer)
 constexpr int TMEM_COLS = 512;              // allocation (power of two >= 2 x 192)
 constexpr int NB = 3 * F;                   // stacked rows of one column shift (dy, co)
 constexpr int DX_W_BYTES = 8 * NB * 16;     // 24576: [cg][dy*64+co][8 ci] of one dx
 constexpr int W_BYTES = 3 * DX_W_BYTES;     // 73728
 constexpr int THREADS = 192;
-constexpr int OFF_RING = 0;
-constexpr int OFF_W = OFF_RING + NS * ROW_BYTES;
-constexpr int OFF_BIAS = OFF_W + W_BYTES;
-constexpr int OFF_BAR = OFF_BIAS + F * 4;
-constexpr int NBAR = 2 * NS + 1 + 2 * NACC + 1;   // full, empty, weights, tfull, tempty, drain
-constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
-constexpr int SMEM = OFF_MISC + 16 + 1024;        // + alignment slack
 constexpr uint32_t IDESC192 = ptx::idesc_bf16_f32(SEG, 192);
 constexpr long long BUDGET = 4000000000LL;        // ~2 s of SM clock per wait
 // descriptor words (no swizzle, K-major): low = start>>4 | (LBO>>4)<<16,
@@ -94,8 +86,21 @@ struct TcMode {
     static constexpr uint32_t IDESC = FP8 ? ptx::idesc_e4m3_f32(tc::SEG, NB)
                                           : ptx::idesc_bf16_f32(tc::SEG, NB);
     static constexpr uint32_t B_LBO = (uint32_t)((NB * 16) >> 4) << 16;
+    // pipeline depth: input-row ring slots and TMEM accumulator regions. The
+    // F -> F layers hold 72 KB of weights and 2 x 192 TMEM columns; the last
+    // layer's 6 KB of weights and 16-column regions leave room for a deeper
+    // ring and 8 regions, so its MMAs run further ahead of its epilogue.
+    static constexpr int NS = LAST ? 11 : 8;
+    static constexpr int NACC = LAST ? 8 : 2;
+    static constexpr int RSTRIDE = LAST ? 32 : NB;   // TMEM columns between regions
+    static constexpr int OFF_W = NS * tc::ROW_BYTES;
+    static constexpr int OFF_BAR = OFF_W + WB;
+    static constexpr int NBAR = 2 * NS + 1 + 2 * NACC + 1;   // full, empty, weights, tfull, tempty, drain
+    static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
+    static constexpr int SMEM = OFF_MISC + 16 + 1024;        // + alignment slack
+    static_assert(SMEM <= 232448, "shared memory budget");
+    static_assert(NACC * RSTRIDE <= tc::TMEM_COLS, "TMEM regions");
 };
-static_assert(tc::SMEM <= 232448, "shared memory budget");
 
 __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 
@@ -188,17 +193,18 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     using Mode = TcMode<LAST, FP8>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* ring = smem + OFF_RING;
-    uint8_t* wsm = smem + OFF_W;
-    uint64_t* bars = (uint64_t*)(smem + OFF_BAR);
+    constexpr int NS = Mode::NS, NACC = Mode::NACC;
+    uint8_t* ring = smem;
+    uint8_t* wsm = smem + Mode::OFF_W;
+    uint64_t* bars = (uint64_t*)(smem + Mode::OFF_BAR);
     uint64_t* full = bars;
     uint64_t* empty = bars + NS;
     uint64_t* wbar = bars + 2 * NS;
     uint64_t* tfull = bars + 2 * NS + 1;
     uint64_t* tempty = tfull + NACC;
     uint64_t* drain = tempty + NACC;
-    uint32_t* tmem_slot = (uint32_t*)(smem + OFF_MISC);
-    volatile int* abort_flag = (volatile int*)(smem + OFF_MISC + 4);
+    uint32_t* tmem_slot = (uint32_t*)(smem + Mode::OFF_MISC);
+    volatile int* abort_flag = (volatile int*)(smem + Mode::OFF_MISC + 4);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) {
@@ -214,6 +220,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         ptx::mbar_init(drain, 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
+        // the layer's weights are constant: fetched before the predecessor finishes
+        ptx::mbar_arrive_expect_tx(wbar, Mode::WB);
+        for (int t = 0; t < 3; ++t)
+            ptx::bulk_load(wsm + t * Mode::DX_W, (const uint8_t*)c.wblob + t * Mode::DX_W,
+                           Mode::DX_W, wbar);
     }
     if (warp == 0 && lane == 0 && !c.jobs) ptx::prefetch_tensormap(&job0.tin);
     if (warp == 2) {
@@ -224,6 +235,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    pdl_launch_dependents();   // after this CTA's TMEM allocation
+    pdl_wait();                // the predecessor's output is this layer's input
 
     // this CTA's share of the concatenated row stream
     const int64_t g_begin = c.total_rows * blockIdx.x / gridDim.x;
@@ -232,10 +245,6 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer
-            ptx::mbar_arrive_expect_tx(wbar, Mode::WB);
-            for (int t = 0; t < 3; ++t)
-                ptx::bulk_load(wsm + t * Mode::DX_W, (const uint8_t*)c.wblob + t * Mode::DX_W,
-                               Mode::DX_W, wbar);
             uint32_t L = 0;
             bool ok = true;
             int j = 0;
@@ -268,13 +277,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             for (int64_t g = g_begin; g < g_end && ok;) {
                 const RowPos p = locate(job0, c, j, g, g_end);
                 for (int ri = -1; ri <= p.len && ok; ++ri, ++L) {
-                    const uint32_t reg = L & 1, u = L >> 1;
+                    const uint32_t reg = L % NACC, u = L / NACC;
                     ok = ptx::mbar_wait(&full[L % NS], (L / NS) & 1, abort_flag, BUDGET);
                     if (ok) ok = ptx::mbar_wait(&tempty[reg], (u & 1) ^ 1, abort_flag, BUDGET);
                     if (!ok) break;
                     ptx::tc_fence_after();
                     const uint32_t a_row = ring_lo + (L % NS) * (ROW_BYTES >> 4);
-                    const uint32_t d = tmem_base + reg * NB;
+                    const uint32_t d = tmem_base + reg * Mode::RSTRIDE;
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
@@ -326,12 +335,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                     if (ri + 1 < p.len) Xprev = pr[0];
                 };
                 for (int ri = -1; ri <= p.len; ++ri, ++L) {
-                    const uint32_t reg = L & 1, u = L >> 1;
+                    const uint32_t reg = L % NACC, u = L / NACC;
                     // x of the output row this step completes, loaded before the wait
                     const float xv = (xin && ri >= 1 && in_img) ? __ldg(xin + (int64_t)(p.y + ri - 1) * J->nx + x) : 0.f;
-                    if (!ptx::mbar_wait(&tfull[reg], u & 1, abort_flag, BUDGET)) { ok = false; break; }
+                    if (!__all_sync(0xffffffffu, ptx::mbar_wait(&tfull[reg], u & 1, abort_flag, BUDGET))) { ok = false; break; }
                     ptx::tc_fence_after();
-                    const uint32_t taddr = lane_base + reg * NB;
+                    const uint32_t taddr = lane_base + reg * Mode::RSTRIDE;
                     if ((ri + 1) & 1) step(X1, X0, ri, taddr, xv);
                     else step(X0, X1, ri, taddr, xv);
                     ptx::tc_fence_before();
@@ -411,10 +420,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 if (ri + 1 < p.len) tm_load64(taddr, Xprev);
             };
             for (int ri = -1; ri <= p.len; ++ri, ++L) {
-                const uint32_t reg = L & 1, u = L >> 1;
-                if (!ptx::mbar_wait(&tfull[reg], u & 1, abort_flag, BUDGET)) { ok = false; break; }
+                const uint32_t reg = L % NACC, u = L / NACC;
+                if (!__all_sync(0xffffffffu, ptx::mbar_wait(&tfull[reg], u & 1, abort_flag, BUDGET))) { ok = false; break; }
                 ptx::tc_fence_after();
-                const uint32_t taddr = lane_base + reg * NB;
+                const uint32_t taddr = lane_base + reg * Mode::RSTRIDE;
                 // output row k lives in X[k & 1]: prev = X[(ri-1) & 1], cur = X[ri & 1]
                 if ((ri + 1) & 1) step(X1, X0, ri, taddr);
                 else step(X0, X1, ri, taddr);
@@ -438,74 +447,165 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
-// First layer 1 -> 64 (+bias, ReLU) from the FP32 image into the BF16
-// channel-group-planar layout; padding columns are written as zeros. One
-// pixel per thread; the weights are a by-value kernel parameter, so every FMA
-// reads its weight as a constant-bank operand (no load instruction). A warp's
-// store to one channel-group plane is 512 contiguous bytes.
+// First layer 1 -> 64 on the tensor cores. Each CTA takes one 128-pixel row
+// segment: every thread gathers its pixel's 3 x 3 taps of the FP32 image (zero
+// outside it) into one row of A (M = 128 pixels, K = 32), one thread issues
+// two 128 x 64 x 16 MMAs into 64 TMEM columns, and the four warps read their
+// 32 lanes back, apply ReLU and the valid-rect mask and store 64 channels per
+// pixel (BF16 planes, or E4M3 scaled by inv_out). BF16 operands would round
+// the FP32 image and weights to 8 bits; instead each is split into a BF16 head
+// and a BF16 tail (v = hi + lo, |lo| <= 2^-9 |v|) and K carries
+// x_hi w_hi + x_lo w_hi + x_hi w_lo + b_hi + b_lo (the dropped x_lo w_lo is
+// below 2^-17 of each product), accumulated in FP32:
+//   A row (pixel)  : [x_hi(9) | x_lo(9) | x_hi(9) | 1 | 1 | 0 0 0]
+//   B row (channel): [w_hi(9) | w_hi(9) | w_lo(9) | b_hi | b_lo | 0 0 0]
+// Operands in the no-swizzle K-major layout: A [kc 4][pixel 128][8] (LBO
+// 2048 B, SBO 128 B), B [kc 4][channel 64][8] (LBO 1024 B, SBO 128 B).
 // ---------------------------------------------------------------------------
+namespace ftc {
+constexpr int A_BYTES = 4 * 128 * 16;          // 8192
+constexpr int B_BYTES = 4 * 64 * 16;           // 4096
+constexpr int OFF_A = 0;
+constexpr int OFF_B = OFF_A + A_BYTES;
+constexpr int OFF_BAR = OFF_B + B_BYTES;
+constexpr int OFF_MISC = OFF_BAR + 8;
+// requested dynamic shared memory: caps residency at 8 CTAs per SM, so the
+// CTAs of an SM never ask for more than its 512 TMEM columns (8 x 64)
+constexpr int SMEM = 27 * 1024;
+constexpr uint32_t IDESC = ptx::idesc_bf16_f32(128, 64);
+constexpr long long BUDGET = 2000000000LL;
+}  // namespace ftc
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
 template <bool FP8>
-__global__ void __launch_bounds__(128) k_first(const float* __restrict__ x,
-                                               const __grid_constant__ EdgeW W, int ny, int nx,
-                                               int nxp, const Rect* __restrict__ rects,
-                                               void* __restrict__ out_, float inv_out) {
-    const int xx = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(128) k_first_tc(const float* __restrict__ x,
+                                                  const uint4* __restrict__ wb, int ny, int nx,
+                                                  int nxp, const Rect* __restrict__ rects,
+                                                  void* __restrict__ out_, float inv_out,
+                                                  int* __restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* As = smem + ftc::OFF_A;
+    uint8_t* Bs = smem + ftc::OFF_B;
+    uint64_t* bar = (uint64_t*)(smem + ftc::OFF_BAR);
+    uint32_t* tmem_slot = (uint32_t*)(smem + ftc::OFF_MISC);
+    volatile int* abort_flag = (volatile int*)(smem + ftc::OFF_MISC + 4);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int p = threadIdx.x;
+    const int xx = blockIdx.x * 128 + p;
     const int yy = blockIdx.y, img = blockIdx.z;
-    if (xx >= nxp) return;
+
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(bar, 1);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    // the .sync.aligned TMEM calls are issued by warp 1, whose lanes never diverge before them
+    if (warp == 1) {
+        ptx::tmem_alloc(tmem_slot, 64);
+        ptx::tmem_relinquish();
+    }
+    // B: 4 KB of weights, 32 B per thread (constant: read before the predecessor finishes)
+    reinterpret_cast<uint4*>(Bs)[2 * p] = __ldg(wb + 2 * p);
+    reinterpret_cast<uint4*>(Bs)[2 * p + 1] = __ldg(wb + 2 * p + 1);
+    __syncthreads();   // TMEM allocated (warp 1) before dependents may launch
+    pdl_launch_dependents();
+    pdl_wait();
+    // A: this pixel's taps, split into BF16 head and tail
     const int64_t plane = (int64_t)ny * nx;
-    const Rect rc = rects ? rects[img] : Rect{0, ny, 0, nx};
-    const bool valid = xx < nx && yy >= rc.y0 && yy < rc.y1 && xx >= rc.x0 && xx < rc.x1;
-    float v[9];
+    float hi[9], lo[9];
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
         const int sy = yy + t / 3 - 1, sx = xx + t % 3 - 1;
-        v[t] = (sy >= 0 && sy < ny && sx >= 0 && sx < nx) ? __ldg(x + img * plane + (int64_t)sy * nx + sx)
-                                                          : 0.f;
+        const float v = (sy >= 0 && sy < ny && sx >= 0 && sx < nx)
+                            ? __ldg(x + img * plane + (int64_t)sy * nx + sx)
+                            : 0.f;
+        hi[t] = __bfloat162float(__float2bfloat16_rn(v));
+        lo[t] = v - hi[t];
     }
-    if constexpr (FP8) {
-        uint8_t* o = reinterpret_cast<uint8_t*>(out_) + (((int64_t)img * ny + yy) * 4 * nxp + xx) * 16;
+    uint4 ch[4];
+    ch[0] = make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), pack_bf16(hi[4], hi[5]),
+                       pack_bf16(hi[6], hi[7]));
+    ch[1] = make_uint4(pack_bf16(hi[8], lo[0]), pack_bf16(lo[1], lo[2]), pack_bf16(lo[3], lo[4]),
+                       pack_bf16(lo[5], lo[6]));
+    ch[2] = make_uint4(pack_bf16(lo[7], lo[8]), pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]),
+                       pack_bf16(hi[4], hi[5]));
+    ch[3] = make_uint4(pack_bf16(hi[6], hi[7]), pack_bf16(hi[8], 1.f), pack_bf16(1.f, 0.f), 0u);
 #pragma unroll
-        for (int cg = 0; cg < 4; ++cg) {
-            uint32_t pk[4];
+    for (int kc = 0; kc < 4; ++kc)
+        *reinterpret_cast<uint4*>(As + kc * 2048 + (p / 8) * 128 + (p % 8) * 16) = ch[kc];
+    ptx::fence_proxy_async_shared();   // generic-proxy smem writes -> tensor core
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    if (threadIdx.x == 0) {
+        const uint32_t a0 = ptx::smem_u32(As), b0 = ptx::smem_u32(Bs);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                float r4[4];
+        for (int k = 0; k < 2; ++k)
+            ptx::mma_bf16(tmem_base, ptx::smem_desc_noswizzle(a0 + k * 2 * 2048, 2048, 128),
+                          ptx::smem_desc_noswizzle(b0 + k * 2 * 1024, 1024, 128), ftc::IDESC,
+                          k);
+        ptx::mma_commit(bar);
+    }
+    __syncwarp();
+    // warp-uniform: the TMEM load below is .sync.aligned (all 32 lanes, converged)
+    const bool ok = __all_sync(0xffffffffu, ptx::mbar_wait(bar, 0, abort_flag, ftc::BUDGET));
+    ptx::tc_fence_after();
+    if (ok) {
+        uint32_t acc[64];
+        ptx::tmem_ld_32x32b_x64(tmem_base + ((uint32_t)(warp * 32) << 16), acc);
+        ptx::tmem_ld_wait();
+        const Rect rc = rects ? rects[img] : Rect{0, ny, 0, nx};
+        const bool valid = xx < nx && yy >= rc.y0 && yy < rc.y1 && xx >= rc.x0 && xx < rc.x1;
+        if (xx >= nxp) {
+            // past the padded width: nothing to store
+        } else if constexpr (FP8) {
+            uint8_t* o = reinterpret_cast<uint8_t*>(out_) + (((int64_t)img * ny + yy) * 4 * nxp + xx) * 16;
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int co = cg * 16 + 4 * e + h;
-                    float s = W.b[co];
+            for (int cg = 0; cg < 4; ++cg) {
+                uint32_t pk[4];
 #pragma unroll
-                    for (int t = 0; t < 9; ++t) s = fmaf(W.w[t][co], v[t], s);
-                    r4[h] = valid ? fmaxf(s, 0.f) * inv_out : 0.f;
+                for (int e = 0; e < 4; ++e) {
+                    float r4[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const float v = __uint_as_float(acc[cg * 16 + 4 * e + h]);
+                        r4[h] = valid ? fmaxf(v, 0.f) * inv_out : 0.f;
+                    }
+                    const uint32_t l2 = __nv_cvt_float2_to_fp8x2(make_float2(r4[0], r4[1]), __NV_SATFINITE, __NV_E4M3);
+                    const uint32_t h2 = __nv_cvt_float2_to_fp8x2(make_float2(r4[2], r4[3]), __NV_SATFINITE, __NV_E4M3);
+                    pk[e] = l2 | (h2 << 16);
                 }
-                const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(r4[0], r4[1]), __NV_SATFINITE, __NV_E4M3);
-                const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(r4[2], r4[3]), __NV_SATFINITE, __NV_E4M3);
-                pk[e] = lo | (hi << 16);
+                *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
-            *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        }
-    } else {
-        __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out_) + ((((int64_t)img * ny + yy) * 8) * nxp + xx) * 8;
+        } else {
+            __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out_) + ((((int64_t)img * ny + yy) * 8) * nxp + xx) * 8;
 #pragma unroll
-        for (int cg = 0; cg < 8; ++cg) {
-            uint32_t pk[4];
+            for (int cg = 0; cg < 8; ++cg) {
+                uint32_t pk[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                float r2[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int co = cg * 8 + 2 * e + h;
-                    float s = W.b[co];
-#pragma unroll
-                    for (int t = 0; t < 9; ++t) s = fmaf(W.w[t][co], v[t], s);
-                    r2[h] = valid ? fmaxf(s, 0.f) : 0.f;
+                for (int e = 0; e < 4; ++e) {
+                    float v0 = fmaxf(__uint_as_float(acc[cg * 8 + 2 * e]), 0.f);
+                    float v1 = fmaxf(__uint_as_float(acc[cg * 8 + 2 * e + 1]), 0.f);
+                    if (!valid) v0 = v1 = 0.f;
+                    pk[e] = pack_bf16(v0, v1);
                 }
-                __nv_bfloat162 h2 = __floats2bfloat162_rn(r2[0], r2[1]);
-                pk[e] = *reinterpret_cast<uint32_t*>(&h2);
+                *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
-            *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
     }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem_base, 64);
+    }
+    if (threadIdx.x == 0 && !ok && err) atomicExch(err, (int)PNP_ETIMEOUT);
 }
 
 // ---------------------------------------------------------------------------
@@ -574,10 +674,15 @@ cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaSuccess;
-        for (auto f : {k_conv_tc<false, false>, k_conv_tc<true, false>, k_conv_tc<false, true>,
-                       k_conv_tc<true, true>})
+        using KFn = void (*)(TcJob, TcCommon);
+        const std::pair<KFn, int> fns[] = {
+            {k_conv_tc<false, false>, TcMode<false, false>::SMEM},
+            {k_conv_tc<true, false>, TcMode<true, false>::SMEM},
+            {k_conv_tc<false, true>, TcMode<false, true>::SMEM},
+            {k_conv_tc<true, true>, TcMode<true, true>::SMEM}};
+        for (const auto& f : fns)
             if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM);
+                e = cudaFuncSetAttribute(f.first, cudaFuncAttributeMaxDynamicSharedMemorySize, f.second);
         if (e != cudaSuccess) return e;
         configured = true;
     }
@@ -594,16 +699,17 @@ cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64
     c.njobs = jobs_dev ? njobs : 1;
     c.total_rows = total_rows;
     const int grid = (int)std::min<int64_t>(num_sms(), total_rows);
-    timer_begin(last ? T_CONV_EDGE : T_CONV_TC, s);
+    timer_begin(last ? T_CONV_LAST : T_CONV_TC, s);
+    cudaError_t e;
     if (fp8) {
-        if (last) k_conv_tc<true, true><<<grid, tc::THREADS, tc::SMEM, s>>>(job0, c);
-        else k_conv_tc<false, true><<<grid, tc::THREADS, tc::SMEM, s>>>(job0, c);
+        if (last) e = launch_pdl(k_conv_tc<true, true>, dim3(grid), dim3(tc::THREADS), TcMode<true, true>::SMEM, s, job0, c);
+        else e = launch_pdl(k_conv_tc<false, true>, dim3(grid), dim3(tc::THREADS), TcMode<false, true>::SMEM, s, job0, c);
     } else {
-        if (last) k_conv_tc<true, false><<<grid, tc::THREADS, tc::SMEM, s>>>(job0, c);
-        else k_conv_tc<false, false><<<grid, tc::THREADS, tc::SMEM, s>>>(job0, c);
+        if (last) e = launch_pdl(k_conv_tc<true, false>, dim3(grid), dim3(tc::THREADS), TcMode<true, false>::SMEM, s, job0, c);
+        else e = launch_pdl(k_conv_tc<false, false>, dim3(grid), dim3(tc::THREADS), TcMode<false, false>::SMEM, s, job0, c);
     }
-    timer_end(last ? T_CONV_EDGE : T_CONV_TC, s);
-    return cudaGetLastError();
+    timer_end(last ? T_CONV_LAST : T_CONV_TC, s);
+    return e;
 }
 
 cudaError_t conv_tc_layer(const __nv_bfloat16* in, const __nv_bfloat16* wblob, const float* bias_host,
@@ -615,14 +721,31 @@ cudaError_t conv_tc_layer(const __nv_bfloat16* in, const __nv_bfloat16* wblob, c
     return tc_launch(J, nullptr, 1, J.rows, wblob, bias_host, err, false, s, false, nullptr, 1.f);
 }
 
-cudaError_t first_layer_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
-                             const Rect* rects, __nv_bfloat16* out, cudaStream_t s) {
+template <bool FP8>
+static cudaError_t launch_first_tc(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
+                                   const Rect* rects, void* out, float inv_out, int* err,
+                                   cudaStream_t s) {
+    static bool attr_done[2] = {false, false};
+    if (!attr_done[FP8]) {
+        cudaError_t e = cudaFuncSetAttribute(k_first_tc<FP8>,
+                                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             (int)cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        attr_done[FP8] = true;
+    }
     const int nxp = bf16_pad_width(nx);
     dim3 g1(ceil_div(nxp, 128), ny, nimg);
     timer_begin(T_CONV_EDGE, s);
-    k_first<false><<<g1, 128, 0, s>>>(x, *D.h_first, ny, nx, nxp, rects, out, 1.f);
+    cudaError_t e = launch_pdl(k_first_tc<FP8>, g1, dim3(128), ftc::SMEM, s, x,
+                               reinterpret_cast<const uint4*>(D.wtc_first), ny, nx, nxp, rects,
+                               out, inv_out, err);
     timer_end(T_CONV_EDGE, s);
-    return cudaGetLastError();
+    return e;
+}
+
+cudaError_t first_layer_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
+                             const Rect* rects, __nv_bfloat16* out, int* err, cudaStream_t s) {
+    return launch_first_tc<false>(D, x, ny, nx, nimg, rects, out, 1.f, err, s);
 }
 
 cudaError_t last_layer_bf16(const DenoiserDev& D, const __nv_bfloat16* act, const float* x,
@@ -632,19 +755,19 @@ cudaError_t last_layer_bf16(const DenoiserDev& D, const __nv_bfloat16* act, cons
     if (e != cudaSuccess) return e;
     J.xin = x;   // nullptr: write the residual G instead of d = x - G
     J.dout = d;
-    return tc_launch(J, nullptr, 1, J.rows, D.wtc_last, &D.h_last->b[0], err, true, s, false,
+    return tc_launch(J, nullptr, 1, J.rows, D.wtc_last, &D.last_bias, err, true, s, false,
                      nullptr, 1.f);
 }
 
 cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
                          const Rect* rects, float* d, void* scratch, cudaStream_t s, bool residual) {
-    if (D.F != 64 || !D.wtc || !D.wtc_last || !D.h_first || !D.h_last) return cudaErrorInvalidValue;
+    if (D.F != 64 || !D.wtc || !D.wtc_last || !D.wtc_first || D.K < 2) return cudaErrorInvalidValue;
     const int nxp = bf16_pad_width(nx);
     const size_t act = (size_t)nimg * ny * nxp * 64;
     __nv_bfloat16* A = (__nv_bfloat16*)scratch;
     __nv_bfloat16* B = A + act;
     int* err = (int*)(B + act);
-    cudaError_t e = first_layer_bf16(D, x, ny, nx, nimg, rects, A, s);
+    cudaError_t e = first_layer_bf16(D, x, ny, nx, nimg, rects, A, err, s);
     if (e != cudaSuccess) return e;
     for (int k = 1; k < D.K - 1; ++k) {
         // host copy of the layer's biases (layers before k all have 64 outputs)
@@ -675,17 +798,14 @@ size_t denoise_fp8_scratch(const DenoiserDev& D, int ny, int nx, int nimg) {
 // D.a8_scale (input of layer k), weights with per-output-channel scales.
 cudaError_t denoise_fp8(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
                         const Rect* rects, float* d, void* scratch, cudaStream_t s, bool residual) {
-    if (D.F != 64 || !D.wtc8 || !D.wtc8_last || !D.fp8_calibrated) return cudaErrorInvalidValue;
+    if (D.F != 64 || !D.wtc8 || !D.wtc8_last || !D.wtc_first || !D.fp8_calibrated)
+        return cudaErrorInvalidValue;
     const int nxp = bf16_pad_width(nx);
     const size_t act = (size_t)nimg * ny * nxp * 64;
     uint8_t* A = (uint8_t*)scratch;
     uint8_t* B = A + act;
     int* err = (int*)(B + act);
-    dim3 g1(ceil_div(nxp, 128), ny, nimg);
-    timer_begin(T_CONV_EDGE, s);
-    k_first<true><<<g1, 128, 0, s>>>(x, *D.h_first, ny, nx, nxp, rects, A, 1.f / D.a8_scale[1]);
-    timer_end(T_CONV_EDGE, s);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_first_tc<true>(D, x, ny, nx, nimg, rects, A, 1.f / D.a8_scale[1], err, s);
     if (e != cudaSuccess) return e;
     const size_t blob = 3 * 4 * 192 * 16;   // bytes of one F -> F layer
     for (int k = 1; k < D.K - 1; ++k) {
@@ -705,7 +825,7 @@ cudaError_t denoise_fp8(const DenoiserDev& D, const float* x, int ny, int nx, in
     J.xin = residual ? nullptr : x;
     J.dout = d;
     const float sl = D.a8_scale[D.K - 1] * D.w8_scale[(D.K - 1) * 64];
-    return tc_launch(J, nullptr, 1, J.rows, D.wtc8_last, &D.h_last->b[0], err, true, s, true, &sl, 1.f);
+    return tc_launch(J, nullptr, 1, J.rows, D.wtc8_last, &D.last_bias, err, true, s, true, &sl, 1.f);
 }
 
 }  // namespace pnp

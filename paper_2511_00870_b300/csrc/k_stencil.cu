@@ -3,114 +3,313 @@
 // H is the circular 2-D convolution of the Gaussian-deconvolution likelihood
 // (Sec. III-A2): (h * x)[i,j] = sum_{a,b} h[a,b] x[i-a+ry, j-b+rx] (indices mod
 // the image size). H^T is the correlation sum_{a,b} h[a,b] r[i+a-ry, j+b-rx].
-// Both are evaluated as a correlation over a shared-memory tile that holds the
+// Both are evaluated as a correlation over a shared-memory window that holds the
 // output tile plus a (kh-1) x (kw-1) circular halo; the forward operator just
-// uses the flipped kernel. Every output is a fixed-order sum over (a, b), so
-// results do not depend on the tile shape or the launch.
+// uses the flipped kernel.
+//
+// A tile is 64 outputs wide and R * BY rows high: a block of 16 x BY threads,
+// each thread owning R rows of 4 consecutive outputs. The kernel width kw is a
+// template parameter (the tap loop is unrolled; taps and window rows come out of
+// shared memory as 128-bit loads, the window row slides through registers), the
+// kernel height is a run-time loop. Every output is the fixed-order sum
+// acc = fma(h[a][b], w, acc) over a = 0..kh-1, then b = 0..kw-1, starting from 0,
+// so results are bitwise the same for every tile shape, which is what lets the
+// tile be picked by timing (stencil_autotune) without changing any result.
+//
+// Rank-one kernels h = u v^T (Gaussian, uniform; detected on the host) take a
+// separable path: a horizontal pass over the window rows into a shared-memory
+// strip T = window * v, then a vertical pass out = sum_a u[a] T[i + a] -
+// kh + kw instead of kh kw FMAs per output, again in a fixed order.
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "pdl.cuh"
 #include "philox.cuh"
 #include "pnp_internal.h"
 
 namespace pnp {
 
-constexpr int ST_TX = 64;    // tile width  (outputs)
-constexpr int ST_TY = 16;    // tile height (outputs)
-constexpr int ST_THREADS = 256;   // 16 x 16, 4 consecutive outputs per thread
+constexpr int ST_TX = 64;     // tile width (outputs): 16 threads x 4 columns
 constexpr int ST_MAXK = 31;
 
-struct StencilSmem {
-    int pitch;
+// Candidate tile shapes: R output rows per thread, BY thread rows per block.
+struct TileShape {
+    int R, BY;
+};
+constexpr TileShape kTiles[] = {{1, 16}, {2, 8}, {2, 16}, {4, 8}, {1, 8}, {4, 16}};
+constexpr int kNumTiles = (int)(sizeof(kTiles) / sizeof(kTiles[0]));
+static std::atomic<int> g_forced_tile{-1};
+
+template <int KW>
+struct Geom {
+    static constexpr int WX = ST_TX + KW - 1;        // window width
+    static constexpr int WP = (WX + 3) & ~3;          // window pitch (floats, 16-B rows)
+    static constexpr int KWP = (KW + 3) & ~3;         // tap row pitch
+    static constexpr int NW4 = (KW + 3 + 3) / 4;      // float4 per thread window row
+    static_assert(60 + 4 * NW4 <= WP, "window row read past the pitch");
 };
 
-// Load the (ST_TY + kh - 1) x (ST_TX + kw - 1) circular window whose top-left
-// image coordinate is (i0 - ry, j0 - rx), and the kernel (flipped if `flip`).
-__device__ __forceinline__ void load_window(const float* __restrict__ img, int ny, int nx, int i0,
-                                            int j0, int kh, int kw, float* win, int pitch,
-                                            const float* __restrict__ h, float* hs, bool flip) {
-    const int ry = kh / 2, rx = kw / 2;
-    const int wy = ST_TY + kh - 1, wx = ST_TX + kw - 1;
-    for (int e = threadIdx.x; e < wy * wx; e += blockDim.x) {
-        const int u = e / wx, v = e - u * wx;
-        int gi = i0 - ry + u, gj = j0 - rx + v;
-        gi %= ny; if (gi < 0) gi += ny;
-        gj %= nx; if (gj < 0) gj += nx;
-        win[u * pitch + v] = __ldg(img + (int64_t)gi * nx + gj);
-    }
-    const int kk = kh * kw;
-    for (int e = threadIdx.x; e < kk; e += blockDim.x) hs[e] = __ldg(h + (flip ? kk - 1 - e : e));
+
+// c mod n for c in [-n, 2n); anything else (rows of a ragged tile past the
+// image, never used) is clamped into the image.
+__device__ __forceinline__ int wrap(int c, int n) {
+    c += c < 0 ? n : 0;
+    c -= c >= n ? n : 0;
+    return min(max(c, 0), n - 1);
 }
 
-// acc[q] = sum_{a,b} hs[a,b] win[di + a][dj + q + b], q = 0..3
-__device__ __forceinline__ void correlate4(const float* win, int pitch, const float* hs, int kh,
-                                           int kw, int di, int dj, float acc[4]) {
-    acc[0] = acc[1] = acc[2] = acc[3] = 0.f;
-    for (int a = 0; a < kh; ++a) {
-        const float* row = win + (di + a) * pitch + dj;
-        const float* hr = hs + a * kw;
-        float w0 = row[0], w1 = row[1], w2 = row[2];
-        for (int b = 0; b < kw; ++b) {
-            const float w3 = row[b + 3];
-            const float hv = hr[b];
-            acc[0] = fmaf(hv, w0, acc[0]);
-            acc[1] = fmaf(hv, w1, acc[1]);
-            acc[2] = fmaf(hv, w2, acc[2]);
-            acc[3] = fmaf(hv, w3, acc[3]);
-            w0 = w1; w1 = w2; w2 = w3;
+// Window rows [0, rows + kh - 1) x cols [0, WX) of image `img` starting at
+// image coordinate (i0 - ry, j0 - rx), wrapped circularly.
+template <int KW>
+__device__ __forceinline__ void fill_window(const float* __restrict__ img, int ny, int nx, int i0,
+                                            int j0, int kh, int rows, float* win) {
+    using G = Geom<KW>;
+    const int ry = kh / 2, rx = KW / 2;
+    const int wy = rows + kh - 1;
+    const int nt = blockDim.x * blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const bool interior = i0 - ry >= 0 && i0 + rows - 1 + ry < ny && j0 - rx >= 0 &&
+                          j0 + ST_TX - 1 + rx < nx;
+    if (interior) {
+        const float* base = img + (int64_t)(i0 - ry) * nx + (j0 - rx);
+        for (int e = tid; e < wy * G::WX; e += nt) {
+            const int u = e / G::WX, v = e - u * G::WX;
+            win[u * G::WP + v] = __ldg(base + (int64_t)u * nx + v);
+        }
+    } else {
+        for (int e = tid; e < wy * G::WX; e += nt) {
+            const int u = e / G::WX, v = e - u * G::WX;
+            const int gi = wrap(i0 - ry + u, ny), gj = wrap(j0 - rx + v, nx);
+            win[u * G::WP + v] = __ldg(img + (int64_t)gi * nx + gj);
         }
     }
 }
 
-__global__ void __launch_bounds__(ST_THREADS) k_blur(const float* __restrict__ x,
-                                                     const float* __restrict__ y,
-                                                     const float* __restrict__ h, int kh, int kw,
-                                                     int ny, int nx, float scale, bool adjoint,
-                                                     float* __restrict__ out) {
-    extern __shared__ float sm[];
-    const int pitch = ST_TX + kw - 1 + 1;
+// 2-D taps (flipped if `flip`), zero-padded to KWP per row.
+template <int KW>
+__device__ __forceinline__ void load_taps2d(const float* __restrict__ h, int kh, bool flip,
+                                            float* hs) {
+    using G = Geom<KW>;
+    const int nt = blockDim.x * blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int kk = kh * KW;
+    for (int e = tid; e < kh * G::KWP; e += nt) {
+        const int a = e / G::KWP, b = e - a * G::KWP;
+        float v = 0.f;
+        if (b < KW) {
+            const int k = a * KW + b;
+            v = __ldg(h + (flip ? kk - 1 - k : k));
+        }
+        hs[e] = v;
+    }
+}
+
+// Separable taps from hsep = [u (kh) | v (KW) | u flipped | v flipped]: v
+// zero-padded to KWP, then u.
+template <int KW>
+__device__ __forceinline__ void load_taps_sep(const float* __restrict__ hsep, int kh, bool flip,
+                                              float* vs, float* us) {
+    using G = Geom<KW>;
+    const int nt = blockDim.x * blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const float* src = hsep + (flip ? kh + KW : 0);
+    for (int e = tid; e < G::KWP + kh; e += nt) {
+        if (e < G::KWP) vs[e] = e < KW ? __ldg(src + kh + e) : 0.f;
+        else us[e - G::KWP] = __ldg(src + (e - G::KWP));
+    }
+}
+
+// acc[o][q] = sum_{a,b} hs[a][b] win[ty R + o + a][4 tx + q + b]
+template <int KW, int R>
+__device__ __forceinline__ void correlate(const float* win, const float* hs, int kh, int ty, int tx,
+                                          float acc[R][4]) {
+    using G = Geom<KW>;
+#pragma unroll
+    for (int o = 0; o < R; ++o)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[o][q] = 0.f;
+#pragma unroll 1
+    for (int u = 0; u < R + kh - 1; ++u) {
+        float w[4 * G::NW4];
+        const float4* src = reinterpret_cast<const float4*>(win + (ty * R + u) * G::WP + 4 * tx);
+#pragma unroll
+        for (int k = 0; k < G::NW4; ++k) {
+            const float4 v = src[k];
+            w[4 * k] = v.x;
+            w[4 * k + 1] = v.y;
+            w[4 * k + 2] = v.z;
+            w[4 * k + 3] = v.w;
+        }
+#pragma unroll
+        for (int o = 0; o < R; ++o) {
+            const int a = u - o;
+            if (a < 0 || a >= kh) continue;
+            const float4* hp = reinterpret_cast<const float4*>(hs + a * G::KWP);
+#pragma unroll
+            for (int b4 = 0; b4 < G::KWP / 4; ++b4) {
+                const float4 hv = hp[b4];
+                const float hh[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb) {
+                    const int b = 4 * b4 + bb;
+                    if (b < KW) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[o][q] = fmaf(hh[bb], w[q + b], acc[o][q]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Separable pass 1: T[r][c] = sum_b vs[b] win[r][c + b] for every window row r
+// and the 64 tile columns (4 per work item).
+template <int KW>
+__device__ __forceinline__ void sep_rows(const float* win, const float* vs, int wy, float* T) {
+    using G = Geom<KW>;
+    const int nt = blockDim.x * blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int it = tid; it < wy * (ST_TX / 4); it += nt) {
+        const int r = it / (ST_TX / 4), c4 = it - r * (ST_TX / 4);
+        float w[4 * G::NW4];
+        const float4* src = reinterpret_cast<const float4*>(win + r * G::WP + 4 * c4);
+#pragma unroll
+        for (int k = 0; k < G::NW4; ++k) {
+            const float4 v = src[k];
+            w[4 * k] = v.x;
+            w[4 * k + 1] = v.y;
+            w[4 * k + 2] = v.z;
+            w[4 * k + 3] = v.w;
+        }
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const float4* vp = reinterpret_cast<const float4*>(vs);
+#pragma unroll
+        for (int b4 = 0; b4 < G::KWP / 4; ++b4) {
+            const float4 hv = vp[b4];
+            const float hh[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb) {
+                const int b = 4 * b4 + bb;
+                if (b < KW) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[q] = fmaf(hh[bb], w[q + b], acc[q]);
+                }
+            }
+        }
+        *reinterpret_cast<float4*>(T + r * ST_TX + 4 * c4) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    }
+}
+
+// Separable pass 2: acc[o][q] = sum_a us[a] T[ty R + o + a][4 tx + q]
+template <int R>
+__device__ __forceinline__ void sep_cols(const float* T, const float* us, int kh, int ty, int tx,
+                                         float acc[R][4]) {
+#pragma unroll
+    for (int o = 0; o < R; ++o)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[o][q] = 0.f;
+#pragma unroll 1
+    for (int u = 0; u < R + kh - 1; ++u) {
+        const float4 tv = *reinterpret_cast<const float4*>(T + (ty * R + u) * ST_TX + 4 * tx);
+#pragma unroll
+        for (int o = 0; o < R; ++o) {
+            const int a = u - o;
+            if (a < 0 || a >= kh) continue;
+            const float hu = us[a];
+            acc[o][0] = fmaf(hu, tv.x, acc[o][0]);
+            acc[o][1] = fmaf(hu, tv.y, acc[o][1]);
+            acc[o][2] = fmaf(hu, tv.z, acc[o][2]);
+            acc[o][3] = fmaf(hu, tv.w, acc[o][3]);
+        }
+    }
+}
+
+// Shared-memory floats of one tile: window, then the 2-D taps or the strip T
+// and the separable taps.
+static size_t tile_smem(int kw, int kh, int rows, bool sep) {
+    const int wp = (ST_TX + kw - 1 + 3) & ~3, kwp = (kw + 3) & ~3;
+    const size_t wy = (size_t)rows + kh - 1;
+    if (!sep) return sizeof(float) * (wy * wp + (size_t)kh * kwp);
+    return sizeof(float) * (wy * wp + wy * ST_TX + kwp + ((kh + 3) & ~3));
+}
+
+// The R x 4 outputs of thread (threadIdx.x, threadIdx.y) of the tile at
+// (i0, j0): the correlation of `img` with the taps (flipped if `flip`). Every
+// thread of the block must call it (it synchronises); `active` threads get acc.
+template <int KW, int R, bool SEP>
+__device__ __forceinline__ void stencil_tile(const float* img, int ny, int nx, int i0, int j0,
+                                             int kh, int rows, const float* h, bool flip,
+                                             float* sm, bool active, float acc[R][4]) {
+    using G = Geom<KW>;
+    const int wy = rows + kh - 1;
     float* win = sm;
-    float* hs = sm + (ST_TY + kh - 1) * pitch;
+    fill_window<KW>(img, ny, nx, i0, j0, kh, rows, win);
+    if constexpr (SEP) {
+        float* T = win + wy * G::WP;
+        float* vs = T + wy * ST_TX;
+        float* us = vs + G::KWP;
+        load_taps_sep<KW>(h, kh, flip, vs, us);
+        __syncthreads();
+        sep_rows<KW>(win, vs, wy, T);
+        __syncthreads();
+        if (active) sep_cols<R>(T, us, kh, threadIdx.y, threadIdx.x, acc);
+    } else {
+        float* hs = win + wy * G::WP;
+        load_taps2d<KW>(h, kh, flip, hs);
+        __syncthreads();
+        if (active) correlate<KW, R>(win, hs, kh, threadIdx.y, threadIdx.x, acc);
+    }
+}
+
+template <int KW, int R, bool SEP>
+__global__ void __launch_bounds__(256) k_blur(const float* __restrict__ x,
+                                              const float* __restrict__ y,
+                                              const float* __restrict__ h, int kh, int ny, int nx,
+                                              float scale, int adjoint, float* __restrict__ out) {
+    extern __shared__ float4 sm4[];
+    const int rows = R * blockDim.y;
     const int64_t plane = (int64_t)ny * nx;
     const int img = blockIdx.z;
-    const int i0 = blockIdx.y * ST_TY, j0 = blockIdx.x * ST_TX;
+    const int i0 = blockIdx.y * rows, j0 = blockIdx.x * ST_TX;
+    pdl_wait();
+    pdl_launch_dependents();
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int j = j0 + 4 * tx;
+    const bool active = j < nx && i0 + ty * R < ny;
+    float acc[R][4];
     // forward H: correlation with the flipped kernel; adjoint: with h itself
-    load_window(x + img * plane, ny, nx, i0, j0, kh, kw, win, pitch, h, hs, !adjoint);
-    __syncthreads();
-    const int di = threadIdx.x / (ST_TX / 4), dj = (threadIdx.x % (ST_TX / 4)) * 4;
-    const int i = i0 + di;
-    if (i >= ny) return;
-    float acc[4];
-    correlate4(win, pitch, hs, kh, kw, di, dj, acc);
+    stencil_tile<KW, R, SEP>(x + img * plane, ny, nx, i0, j0, kh, rows, h, !adjoint,
+                             reinterpret_cast<float*>(sm4), active, acc);
+    if (!active) return;
+    // 128-bit accesses when rows are whole float4s (then j + 3 < nx) and aligned
+    const bool vec = (nx & 3) == 0 && ((reinterpret_cast<uintptr_t>(out) |
+                                        reinterpret_cast<uintptr_t>(y)) & 15) == 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int j = j0 + dj + q;
-        if (j < nx) {
-            const int64_t n = (int64_t)i * nx + j;
-            float v = acc[q];
-            if (y) v -= __ldg(y + n);
-            out[img * plane + n] = v * scale;
+    for (int o = 0; o < R; ++o) {
+        const int i = i0 + ty * R + o;
+        if (i >= ny) break;
+        const int64_t n = (int64_t)i * nx + j;
+        if (vec) {
+            float4 v = make_float4(acc[o][0], acc[o][1], acc[o][2], acc[o][3]);
+            if (y) {
+                const float4 yv = __ldg(reinterpret_cast<const float4*>(y + n));
+                v.x -= yv.x; v.y -= yv.y; v.z -= yv.z; v.w -= yv.w;
+            }
+            v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
+            *reinterpret_cast<float4*>(out + img * plane + n) = v;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (j + q < nx) {
+                    float v = acc[o][q];
+                    if (y) v -= __ldg(y + n + q);
+                    out[img * plane + n + q] = v * scale;
+                }
+            }
         }
     }
-}
-
-static size_t stencil_smem(int kh, int kw) {
-    const int pitch = ST_TX + kw - 1 + 1;
-    return sizeof(float) * ((size_t)(ST_TY + kh - 1) * pitch + kh * kw);
-}
-
-cudaError_t launch_blur(const float* x, const float* y, const float* h, int kh, int kw, int ny,
-                        int nx, int nimg, float* r, cudaStream_t s) {
-    dim3 grid(ceil_div(nx, ST_TX), ceil_div(ny, ST_TY), nimg);
-    timer_begin(T_BLUR, s);
-    k_blur<<<grid, ST_THREADS, stencil_smem(kh, kw), s>>>(x, y, h, kh, kw, ny, nx, 1.0f, false, r);
-    timer_end(T_BLUR, s);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_blur_adjoint(const float* r, const float* h, int kh, int kw, int ny, int nx,
-                                int nimg, float scale, float* g, cudaStream_t s) {
-    dim3 grid(ceil_div(nx, ST_TX), ceil_div(ny, ST_TY), nimg);
-    k_blur<<<grid, ST_THREADS, stencil_smem(kh, kw), s>>>(r, nullptr, h, kh, kw, ny, nx, scale,
-                                                          true, g);
-    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -118,85 +317,311 @@ cudaError_t launch_blur_adjoint(const float* r, const float* h, int kh, int kw, 
 // of r, then x+ = x - gamma g + c_prior (d - x) + c_proj (clamp(x) - x)
 // + c_noise xi and, when sampling, the FP32 Welford step
 // delta = x+ - mean; mean += delta / n; m2 += delta (x+ - mean).
+// With `arrive` set, the last block to finish advances the device step counter
+// (every block has read t by then).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(ST_THREADS) k_update(UpdateParams p) {
-    extern __shared__ float sm[];
-    const int kh = p.kh, kw = p.kw, ny = p.ny, nx = p.nx;
-    const int pitch = ST_TX + kw - 1 + 1;
-    float* win = sm;
-    float* hs = sm + (ST_TY + kh - 1) * pitch;
+__device__ __forceinline__ void normals4(const UpdateParams& p, int64_t n0, uint32_t t,
+                                         uint32_t chain, float z[4]) {
+    // normals of the 4 pixels n0..n0+3 (flat row-major index): 1 or 2 Philox groups
+    const uint32_t m0 = (uint32_t)(n0 >> 2);
+    float za[4];
+    normals_group(m0, t, chain, p.key0, p.key1, za);
+    const int off = (int)(n0 & 3);
+    if (off == 0) {
+        z[0] = za[0]; z[1] = za[1]; z[2] = za[2]; z[3] = za[3];
+    } else {
+        float zb[4];
+        normals_group(m0 + 1, t, chain, p.key0, p.key1, zb);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = off + q;
+            const float a = k == 0 ? za[0] : k == 1 ? za[1] : k == 2 ? za[2] : za[3];
+            const float b = k == 4 ? zb[0] : k == 5 ? zb[1] : zb[2];
+            z[q] = k < 4 ? a : b;
+        }
+    }
+}
+
+__device__ __forceinline__ float update1(const UpdateParams& p, float xv, float gq, float dv,
+                                         float zq) {
+    float v = xv - p.gamma * (gq * p.inv_s2);
+    if (p.d) v += p.d_residual ? -p.c_prior * dv : p.c_prior * (dv - xv);
+    const float pr = fminf(fmaxf(xv, 0.f), 1.f);
+    v += p.c_proj * (pr - xv);
+    v += p.c_noise * zq;
+    return v;
+}
+
+__device__ __forceinline__ void welford1(float v, float inv_n, float& mo, float& q) {
+    const float delta = v - mo;
+    const float mn = mo + delta * inv_n;
+    q = q + delta * (v - mn);
+    mo = mn;
+}
+
+template <int KW, int R, bool SEP>
+__global__ void __launch_bounds__(256) k_update(UpdateParams p) {
+    extern __shared__ float4 sm4[];
+    const int kh = p.kh, ny = p.ny, nx = p.nx;
+    const int rows = R * blockDim.y;
     const int64_t plane = (int64_t)ny * nx;
     const int chain = blockIdx.z;
-    const int i0 = blockIdx.y * ST_TY, j0 = blockIdx.x * ST_TX;
-    load_window(p.r + chain * plane, ny, nx, i0, j0, kh, kw, win, pitch, p.h, hs, false);
-    __syncthreads();
-    const int di = threadIdx.x / (ST_TX / 4), dj = (threadIdx.x % (ST_TX / 4)) * 4;
-    const int i = i0 + di;
-    if (i >= ny || j0 + dj >= nx) return;
-    float g[4];
-    correlate4(win, pitch, hs, kh, kw, di, dj, g);
-
+    const int i0 = blockIdx.y * rows, j0 = blockIdx.x * ST_TX;
+    pdl_wait();
+    pdl_launch_dependents();
     const uint32_t t = p.t_dev ? *p.t_dev : p.t;
-    float inv_n = p.inv_n;
-    if (p.burn_dev) {
-        const int64_t n = (int64_t)t + 1 - *p.burn_dev;
-        inv_n = n > 0 ? 1.0f / (float)n : 0.0f;
-    }
-    // Normals for the 4 pixels n0..n0+3 (flat row-major index); they span
-    // at most two Philox groups.
-    const int64_t n0 = (int64_t)i * nx + j0 + dj;
-    float z[4] = {0.f, 0.f, 0.f, 0.f};
-    if (p.c_noise != 0.f) {
-        const uint32_t m0 = (uint32_t)(n0 >> 2);
-        float za[4], zb[4];
-        normals_group(m0, t, (uint32_t)chain, p.key0, p.key1, za);
-        const int off = (int)(n0 & 3);
-        if (off == 0) {
-            z[0] = za[0]; z[1] = za[1]; z[2] = za[2]; z[3] = za[3];
-        } else {
-            normals_group(m0 + 1, t, (uint32_t)chain, p.key0, p.key1, zb);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int j = j0 + 4 * tx;
+    const bool active = j < nx && i0 + ty * R < ny;
+    float g[R][4];
+    stencil_tile<KW, R, SEP>(p.r + chain * plane, ny, nx, i0, j0, kh, rows,
+                             SEP ? p.hsep : p.h, false, reinterpret_cast<float*>(sm4), active, g);
+    if (active) {
+        float inv_n = p.inv_n;
+        if (p.burn_dev) {
+            const int64_t n = (int64_t)t + 1 - *p.burn_dev;
+            inv_n = n > 0 ? 1.0f / (float)n : 0.0f;
+        }
+        float* xc = p.x + chain * plane;
+        const float* dc = p.d ? p.d + chain * plane : nullptr;
+        float* mc = p.mean ? p.mean + chain * plane : nullptr;
+        float* qc = p.m2 ? p.m2 + chain * plane : nullptr;
+        const bool vec = (nx & 3) == 0 &&
+                         ((reinterpret_cast<uintptr_t>(p.x) | reinterpret_cast<uintptr_t>(p.d) |
+                           reinterpret_cast<uintptr_t>(p.mean) | reinterpret_cast<uintptr_t>(p.m2)) &
+                          15) == 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int k = off + q;
-                const float a = k == 0 ? za[0] : k == 1 ? za[1] : k == 2 ? za[2] : za[3];
-                const float b = k == 4 ? zb[0] : k == 5 ? zb[1] : zb[2];
-                z[q] = k < 4 ? a : b;
+        for (int o = 0; o < R; ++o) {
+            const int i = i0 + ty * R + o;
+            if (i >= ny) break;
+            const int64_t n0 = (int64_t)i * nx + j;
+            float z[4] = {0.f, 0.f, 0.f, 0.f};
+            if (p.c_noise != 0.f) normals4(p, n0, t, (uint32_t)chain, z);
+            if (vec) {
+                float4 xv = *reinterpret_cast<const float4*>(xc + n0);
+                float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (dc) dv = __ldg(reinterpret_cast<const float4*>(dc + n0));
+                float4 v;
+                v.x = update1(p, xv.x, g[o][0], dv.x, z[0]);
+                v.y = update1(p, xv.y, g[o][1], dv.y, z[1]);
+                v.z = update1(p, xv.z, g[o][2], dv.z, z[2]);
+                v.w = update1(p, xv.w, g[o][3], dv.w, z[3]);
+                *reinterpret_cast<float4*>(xc + n0) = v;
+                if (inv_n > 0.f) {
+                    float4 mo = *reinterpret_cast<const float4*>(mc + n0);
+                    float4 qo = *reinterpret_cast<const float4*>(qc + n0);
+                    welford1(v.x, inv_n, mo.x, qo.x);
+                    welford1(v.y, inv_n, mo.y, qo.y);
+                    welford1(v.z, inv_n, mo.z, qo.z);
+                    welford1(v.w, inv_n, mo.w, qo.w);
+                    *reinterpret_cast<float4*>(mc + n0) = mo;
+                    *reinterpret_cast<float4*>(qc + n0) = qo;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (j + q >= nx) break;
+                    const int64_t n = n0 + q;
+                    const float v = update1(p, xc[n], g[o][q], dc ? __ldg(dc + n) : 0.f, z[q]);
+                    xc[n] = v;
+                    if (inv_n > 0.f) {
+                        float mo = mc[n], qo = qc[n];
+                        welford1(v, inv_n, mo, qo);
+                        mc[n] = mo;
+                        qc[n] = qo;
+                    }
+                }
             }
         }
     }
-    float* xc = p.x + chain * plane;
-    const float* dc = p.d ? p.d + chain * plane : nullptr;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int j = j0 + dj + q;
-        if (j >= nx) break;
-        const int64_t n = (int64_t)i * nx + j;
-        const float xv = xc[n];
-        float v = xv - p.gamma * (g[q] * p.inv_s2);
-        if (dc) v += p.d_residual ? -p.c_prior * __ldg(dc + n) : p.c_prior * (__ldg(dc + n) - xv);
-        const float pr = fminf(fmaxf(xv, 0.f), 1.f);
-        v += p.c_proj * (pr - xv);
-        v += p.c_noise * z[q];
-        xc[n] = v;
-        if (inv_n > 0.f) {
-            float* mc = p.mean + chain * plane;
-            float* qc = p.m2 + chain * plane;
-            const float mo = mc[n];
-            const float delta = v - mo;
-            const float mn = mo + delta * inv_n;
-            mc[n] = mn;
-            qc[n] = qc[n] + delta * (v - mn);
+    if (p.arrive) {
+        __syncthreads();
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+            if (atomicAdd(p.arrive, 1u) == nblk - 1) {
+                *p.arrive = 0u;
+                *const_cast<uint32_t*>(p.t_dev) = t + 1u;
+            }
         }
     }
 }
 
-cudaError_t launch_langevin_update(const UpdateParams& p, cudaStream_t s) {
-    dim3 grid(ceil_div(p.nx, ST_TX), ceil_div(p.ny, ST_TY), p.nchain);
-    timer_begin(T_UPDATE, s);
-    k_update<<<grid, ST_THREADS, stencil_smem(p.kh, p.kw), s>>>(p);
-    timer_end(T_UPDATE, s);
-    return cudaGetLastError();
+// ------------------------------------------------------------ dispatch
+
+using BlurFn = void (*)(const float*, const float*, const float*, int, int, int, float, int,
+                        float*);
+using UpdFn = void (*)(UpdateParams);
+
+template <int KW>
+static BlurFn blur_fn_r(int R, bool sep) {
+    if (sep) return R == 1 ? k_blur<KW, 1, true> : R == 2 ? k_blur<KW, 2, true> : k_blur<KW, 4, true>;
+    return R == 1 ? k_blur<KW, 1, false> : R == 2 ? k_blur<KW, 2, false> : k_blur<KW, 4, false>;
 }
+template <int KW>
+static UpdFn upd_fn_r(int R, bool sep) {
+    if (sep) return R == 1 ? k_update<KW, 1, true> : R == 2 ? k_update<KW, 2, true> : k_update<KW, 4, true>;
+    return R == 1 ? k_update<KW, 1, false> : R == 2 ? k_update<KW, 2, false> : k_update<KW, 4, false>;
+}
+
+#define PNP_KW_CASES(F)                                                                        \
+    switch (kw) {                                                                              \
+    case 1: return F<1>(R, sep);   case 3: return F<3>(R, sep);   case 5: return F<5>(R, sep); \
+    case 7: return F<7>(R, sep);   case 9: return F<9>(R, sep);   case 11: return F<11>(R, sep); \
+    case 13: return F<13>(R, sep); case 15: return F<15>(R, sep); case 17: return F<17>(R, sep); \
+    case 19: return F<19>(R, sep); case 21: return F<21>(R, sep); case 23: return F<23>(R, sep); \
+    case 25: return F<25>(R, sep); case 27: return F<27>(R, sep); case 29: return F<29>(R, sep); \
+    case 31: return F<31>(R, sep);                                                             \
+    default: return nullptr;                                                                   \
+    }
+
+static BlurFn blur_fn(int kw, int R, bool sep) { PNP_KW_CASES(blur_fn_r) }
+static UpdFn upd_fn(int kw, int R, bool sep) { PNP_KW_CASES(upd_fn_r) }
+#undef PNP_KW_CASES
+
+// Tiles whose shared memory exceeds the 48 KB default need the opt-in, once
+// per kernel.
+template <typename Fn>
+static cudaError_t allow_smem(Fn fn, size_t smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    static std::mutex mu;
+    static std::map<const void*, size_t> done;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& have = done[reinterpret_cast<const void*>(fn)];
+    if (smem <= have) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) have = smem;
+    return e;
+}
+
+// the tile a launch uses: the forced one if set, else the caller's choice
+static int resolve_tile(int tile) {
+    const int f = g_forced_tile.load();
+    if (f >= 0) return f;
+    return (tile >= 0 && tile < kNumTiles) ? tile : 0;
+}
+
+static cudaError_t blur_raw(const float* x, const float* y, const float* h, const float* hsep,
+                            int kh, int kw, int ny, int nx, int nimg, float scale, bool adjoint,
+                            float* out, int tile, cudaStream_t s) {
+    const TileShape ts = kTiles[tile];
+    const int rows = ts.R * ts.BY;
+    const bool sep = hsep != nullptr;
+    BlurFn fn = blur_fn(kw, ts.R, sep);
+    if (!fn || kh > ST_MAXK) return cudaErrorInvalidValue;
+    const size_t smem = tile_smem(kw, kh, rows, sep);
+    cudaError_t e = allow_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(ceil_div(nx, ST_TX), ceil_div(ny, rows), nimg);
+    return launch_pdl(fn, grid, dim3(16, ts.BY), smem, s, x, y, sep ? hsep : h, kh, ny, nx, scale,
+                      adjoint ? 1 : 0, out);
+}
+
+static cudaError_t update_raw(const UpdateParams& p, int tile, cudaStream_t s) {
+    const TileShape ts = kTiles[tile];
+    const int rows = ts.R * ts.BY;
+    const bool sep = p.hsep != nullptr;
+    UpdFn fn = upd_fn(p.kw, ts.R, sep);
+    if (!fn || p.kh > ST_MAXK) return cudaErrorInvalidValue;
+    const size_t smem = tile_smem(p.kw, p.kh, rows, sep);
+    cudaError_t e = allow_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(ceil_div(p.nx, ST_TX), ceil_div(p.ny, rows), p.nchain);
+    return launch_pdl(fn, grid, dim3(16, ts.BY), smem, s, p);
+}
+
+cudaError_t launch_blur(const float* x, const float* y, const float* h, int kh, int kw, int ny,
+                        int nx, int nimg, float* r, cudaStream_t s, int tile, const float* hsep) {
+    timer_begin(T_BLUR, s);
+    cudaError_t e = blur_raw(x, y, h, hsep, kh, kw, ny, nx, nimg, 1.0f, false, r,
+                             resolve_tile(tile), s);
+    timer_end(T_BLUR, s);
+    return e;
+}
+
+cudaError_t launch_blur_adjoint(const float* r, const float* h, int kh, int kw, int ny, int nx,
+                                int nimg, float scale, float* g, cudaStream_t s, int tile) {
+    return blur_raw(r, nullptr, h, nullptr, kh, kw, ny, nx, nimg, scale, true, g,
+                    resolve_tile(tile), s);
+}
+
+cudaError_t launch_langevin_update(const UpdateParams& p, cudaStream_t s) {
+    timer_begin(T_UPDATE, s);
+    cudaError_t e = update_raw(p, resolve_tile(p.tile), s);
+    timer_end(T_UPDATE, s);
+    return e;
+}
+
+int stencil_tile_count() { return kNumTiles; }
+
+bool set_forced_stencil_tile(int tile) {
+    if (tile < -1 || tile >= kNumTiles) return false;
+    g_forced_tile = tile;
+    return true;
+}
+
+// ------------------------------------------------------------ autotuner
+
+// Times every tile shape for r = Hx - y and for the update on the problem's own
+// buffers and returns the fastest of each. The update candidates overwrite x,
+// mean and m2 (callers initialise them afterwards). Choices are cached per
+// (ny, nx, kh, kw, nimg, separable): every shape gives bitwise the same
+// results, so the cache only saves the timing.
+cudaError_t stencil_autotune(const float* x, const float* y, const float* h, const float* hsep,
+                             int kh, int kw, int ny, int nx, int nimg, float* r,
+                             const UpdateParams& u, cudaStream_t s, int* blur_tile,
+                             int* update_tile) {
+    using Key = std::tuple<int, int, int, int, int, bool>;
+    static std::mutex mu;
+    static std::map<Key, std::pair<int, int>> cache;
+    const Key key{ny, nx, kh, kw, nimg, hsep != nullptr};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *blur_tile = it->second.first;
+            *update_tile = it->second.second;
+            return cudaSuccess;
+        }
+    }
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    constexpr int reps = 3;
+    float best_b = 1e30f, best_u = 1e30f;
+    int bt = 0, ut = 0;
+    for (int c = 0; c < kNumTiles && e == cudaSuccess; ++c) {
+        for (int kind = 0; kind < 2 && e == cudaSuccess; ++kind) {
+            for (int it = 0; it <= reps && e == cudaSuccess; ++it) {
+                if (it == 1) e = cudaEventRecord(e0, s);
+                if (e != cudaSuccess) break;
+                e = kind == 0 ? blur_raw(x, y, h, hsep, kh, kw, ny, nx, nimg, 1.0f, false, r, c, s)
+                              : update_raw(u, c, s);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) break;
+            if (kind == 0 && ms < best_b) best_b = ms, bt = c;
+            if (kind == 1 && ms < best_u) best_u = ms, ut = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = {bt, ut};
+    *blur_tile = bt;
+    *update_tile = ut;
+    return cudaSuccess;
+}
+
+// ------------------------------------------------------------ final moments
 
 __global__ void k_finalize(const float* __restrict__ mean, const float* __restrict__ m2,
                            int64_t npix, int64_t n_kept, int want_var, double* __restrict__ mmse,

@@ -40,7 +40,31 @@ int num_sms();
 bool timer_enabled();
 void timer_begin(int id, cudaStream_t s);
 void timer_end(int id, cudaStream_t s);
-enum TimerId { T_BLUR = 0, T_UPDATE = 1, T_CONV_FP32 = 2, T_CONV_TC = 3, T_CONV_EDGE = 4, T_COUNT = 5 };
+enum TimerId { T_BLUR = 0, T_UPDATE = 1, T_CONV_FP32 = 2, T_CONV_TC = 3, T_CONV_EDGE = 4, T_CONV_LAST = 5, T_COUNT = 6 };
+
+// Programmatic dependent launch for the kernels of one iteration (stencils,
+// tensor-core conv layers): a kernel launched this way may start while its
+// predecessor in the stream drains; it runs its prologue (barriers, TMEM,
+// constant weights), then waits in griddepcontrol.wait for the predecessor to
+// complete before touching any buffer the predecessor reads or writes. Every
+// such kernel signals griddepcontrol.launch_dependents only after its own TMEM
+// allocation, so a dependent that holds TMEM can never block a predecessor.
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 // --------------------------------------------------------------------------
 // Valid rectangle of an activation image: positions outside [y0,y1) x [x0,x1)
@@ -48,13 +72,6 @@ enum TimerId { T_BLUR = 0, T_UPDATE = 1, T_CONV_FP32 = 2, T_CONV_TC = 3, T_CONV_
 // --------------------------------------------------------------------------
 struct Rect {
     int y0, y1, x0, x1;
-};
-
-// First / last layer weights of the BF16 path, passed by value as kernel
-// parameters so that the FMAs read them as constant-bank operands.
-struct EdgeW {
-    float w[9][64];   // [tap][channel]: first layer = output channel, last = input channel
-    float b[64];      // first layer: per output channel; last layer: b[0]
 };
 
 // --------------------------------------------------------------------------
@@ -72,6 +89,9 @@ struct DenoiserDev {
     __nv_bfloat16* wtc = nullptr;
     // last layer (F -> 1): [dx 3][cg 8][16 rows: kernel row dy in row dy][8 ci]
     __nv_bfloat16* wtc_last = nullptr;
+    // first layer (1 -> F) on tensor cores: [kc 4][co 64][8], K = 32 holding
+    // w_hi (taps 0-8), w_hi, w_lo, b_hi, b_lo (BF16 head/tail split of FP32)
+    __nv_bfloat16* wtc_first = nullptr;
     // E4M3 variant: same blobs with 16-channel groups ([dx][4 cg][rows][16 ci]),
     // per-output-channel weight scales (host, [K][64]) and per-layer static
     // activation scales (host; a8_scale[k] = scale of layer k's input)
@@ -80,20 +100,18 @@ struct DenoiserDev {
     float* w8_scale = nullptr;
     float a8_scale[32] = {0};
     bool fp8_calibrated = false;
-    EdgeW* h_first = nullptr;   // host copies for the BF16 edge layers
-    EdgeW* h_last = nullptr;
-    // FP32 first/last layer weights in tap-major order for the BF16 path
-    float* wfirst = nullptr;  // [9][F]
-    float* wlast = nullptr;   // [9][F]
+    float last_bias = 0.f;      // bias of the single output channel of the last layer
     // host copies (FP32, OIHW) for reference / re-packing
     float* hw = nullptr;
     float* hb = nullptr;
 };
 
-// Step counter read by the update kernel during graph replay.
+// Step counter read by the update kernel during graph replay; the update's
+// last block to finish advances t (arrive counts the blocks done).
 struct StepState {
     uint32_t t;
     int32_t burn_in;
+    uint32_t arrive;
 };
 
 }  // namespace pnp
@@ -109,10 +127,16 @@ struct pnp_denoiser {
 namespace pnp {
 
 // ---------------------------------------------------------------- kernels
+// Stencils take a tile-shape index (stencil_autotune's choice; -1 = default);
+// every shape gives bitwise the same results.
+// hsep (optional): separable taps [u | v | u flipped | v flipped] of a rank-one h.
 cudaError_t launch_blur(const float* x, const float* y, const float* h, int kh, int kw, int ny,
-                        int nx, int nimg, float* r, cudaStream_t s);
+                        int nx, int nimg, float* r, cudaStream_t s, int tile = -1,
+                        const float* hsep = nullptr);
 cudaError_t launch_blur_adjoint(const float* r, const float* h, int kh, int kw, int ny, int nx,
-                                int nimg, float scale, float* g, cudaStream_t s);
+                                int nimg, float scale, float* g, cudaStream_t s, int tile = -1);
+int stencil_tile_count();
+bool set_forced_stencil_tile(int tile);   // -1 = use each launch's own choice
 
 struct UpdateParams {
     float* x;
@@ -134,8 +158,17 @@ struct UpdateParams {
     const int32_t* burn_dev;   // if non-null: sample number n = t + 1 - *burn_dev,
                                // accumulated when n > 0 (graph replay)
     int d_residual;            // d holds G = x - D(x) instead of D(x)
+    uint32_t* arrive;          // if non-null: the last block advances *t_dev (graph replay)
+    int tile;                  // stencil tile shape (-1 = default)
+    const float* hsep;         // separable taps of a rank-one h (nullptr: 2-D taps)
 };
 cudaError_t launch_langevin_update(const UpdateParams& p, cudaStream_t s);
+// Times the stencil tile shapes for r = H x - y and for the update `u` (which it
+// runs, overwriting u.x / u.mean / u.m2) and returns the fastest of each.
+cudaError_t stencil_autotune(const float* x, const float* y, const float* h, const float* hsep,
+                             int kh, int kw, int ny, int nx, int nimg, float* r,
+                             const UpdateParams& u, cudaStream_t s, int* blur_tile,
+                             int* update_tile);
 cudaError_t launch_finalize_moments(const float* mean, const float* m2, int64_t npix,
                                     int64_t n_kept, int want_var, double* mmse, double* out2,
                                     cudaStream_t s);
@@ -173,7 +206,7 @@ cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64
                       cudaStream_t s, bool fp8 = false, const float* scale_host = nullptr,
                       float inv_out = 1.f);
 cudaError_t first_layer_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
-                             const Rect* rects, __nv_bfloat16* out, cudaStream_t s);
+                             const Rect* rects, __nv_bfloat16* out, int* err, cudaStream_t s);
 cudaError_t last_layer_bf16(const DenoiserDev& D, const __nv_bfloat16* act, const float* x,
                             int ny, int nx, int nimg, float* d, int* err, cudaStream_t s);
 
@@ -240,11 +273,14 @@ struct pnp_problem {
     size_t scratch_bytes = 0;
     pnp::StepState* st = nullptr;
     int64_t t = 0;
-    cudaGraphExec_t graph = nullptr;
+    int blur_tile = -1, update_tile = -1;   // autotuned stencil tile shapes
+    float* hsep = nullptr;                  // separable taps when h is rank one
+    cudaGraphExec_t graph = nullptr;         // one iteration
+    cudaGraphExec_t graph_batch = nullptr;   // kGraphBatch iterations
 };
 
 namespace pnp {
-cudaError_t launch_advance(StepState* st, cudaStream_t s);
+constexpr int kGraphBatch = 8;   // iterations per replayed graph
 // The two halves of one iteration around the denoiser: r = H x - y, and the
 // fused update (+ step counter advance).
 pnp_status problem_pre(pnp_problem* p, cudaStream_t s);

@@ -82,3 +82,15 @@ def test_problem_rejects_bad_descriptors_without_gpu(lib):
         Problem(y, h, 0.1, blocks=(17, 1))              # more blocks than rows
     with pytest.raises(PnpError):
         Problem(y, h, 0.1, gamma=10.0)                  # violates Eq. 10
+
+
+def test_stencil_tile_override_is_validated_on_the_host(lib):
+    from paper_2511_00870_b300 import PnpError, pnp_set_stencil_tile, pnp_stencil_tile_count
+    n = pnp_stencil_tile_count()
+    assert n >= 2
+    for bad in (-2, n):
+        with pytest.raises(PnpError) as e:
+            pnp_set_stencil_tile(bad)
+        assert e.value.status == 1
+    pnp_set_stencil_tile(n - 1)
+    pnp_set_stencil_tile(-1)
