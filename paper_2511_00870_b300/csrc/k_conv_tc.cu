@@ -24,8 +24,12 @@
 // slower). The epilogue sums output row r = P_{r-1}^0 + P_r^1 + P_{r+1}^2 in
 // registers, two partial rows at a time. Warp roles: warp 0 = TMA producer,
 // warp 1 = MMA issuer, warps 2-5 = epilogue (TMEM -> registers, sum, bias,
-// ReLU, zero outside the valid rect, BF16, global store). Input rows
-// circulate through an 8-slot shared-memory ring.
+// ReLU, zero outside the valid rect, BF16, global store); the epilogue makes
+// two TMEM round trips per input row with 64-column loads (a load and wait
+// per 16 columns left the epilogue, not the tensor core, setting the pace).
+// Input rows circulate through an 8-slot shared-memory ring. The last layer
+// (one output channel) drains four input rows per wait, with an 11-slot ring
+// and eight 32-column TMEM regions.
 //
 // One launch covers a table of jobs (images of possibly different sizes,
 // each with its own tensor map): every CTA walks a contiguous range of the
@@ -55,7 +59,6 @@ constexpr int TMEM_COLS = 512;              // allocation (power of two >= 2 x 1
 constexpr int NB = 3 * F;                   // stacked rows of one column shift (dy, co)
 constexpr int DX_W_BYTES = 8 * NB * 16;     // 24576: [cg][dy*64+co][8 ci] of one dx
 constexpr int W_BYTES = 3 * DX_W_BYTES;     // 73728
-constexpr int THREADS = 192;
 constexpr uint32_t IDESC192 = ptx::idesc_bf16_f32(SEG, 192);
 constexpr long long BUDGET = 4000000000LL;        // ~2 s of SM clock per wait
 // descriptor words (no swizzle, K-major): low = start>>4 | (LBO>>4)<<16,
@@ -93,6 +96,9 @@ struct TcMode {
     static constexpr int NS = LAST ? 11 : 8;
     static constexpr int NACC = LAST ? 8 : 2;
     static constexpr int RSTRIDE = LAST ? 32 : NB;   // TMEM columns between regions
+    // epilogue warps, one per TMEM lane quadrant
+    static constexpr int EPI_WARPS = 4;
+    static constexpr int THREADS = 64 + 32 * EPI_WARPS;
     static constexpr int OFF_W = NS * tc::ROW_BYTES;
     static constexpr int OFF_BAR = OFF_W + WB;
     static constexpr int NBAR = 2 * NS + 1 + 2 * NACC + 1;   // full, empty, weights, tfull, tempty, drain
@@ -187,7 +193,7 @@ __device__ __forceinline__ void tm_load64(uint32_t taddr, float* acc) {
 }
 
 template <bool LAST, bool FP8>
-__global__ void __launch_bounds__(tc::THREADS, 1)
+__global__ void __launch_bounds__(TcMode<LAST, FP8>::THREADS, 1)
     k_conv_tc(const __grid_constant__ TcJob job0, const __grid_constant__ TcCommon c) {
     using namespace tc;
     using Mode = TcMode<LAST, FP8>;
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         ptx::mbar_init(wbar, 1);
         for (int i = 0; i < NACC; ++i) {
             ptx::mbar_init(&tfull[i], 1);
-            ptx::mbar_init(&tempty[i], 4);
+            ptx::mbar_init(&tempty[i], Mode::EPI_WARPS);
         }
         ptx::mbar_init(drain, 1);
         *abort_flag = 0;
@@ -302,61 +308,90 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 ptx::mbar_wait(drain, 0, abort_flag, BUDGET);
             }
         }
-    } else {
-        // ---------------- epilogue: warps 2..5 own TMEM lane quadrants 2,3,0,1
-        if constexpr (LAST) {
-            // last layer: output row r = P_{r-1}[col 0] + P_r[col 1] + P_{r+1}[col 2];
-            // d = x - (G + b) in FP32
-            const int quad = warp & 3;
-            const int jx = quad * 32 + lane;
-            const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
-            uint32_t L = 0;
-            bool ok = true;
-            int j = 0;
-            float X0 = 0.f, X1 = 0.f;
-            for (int64_t g = g_begin; g < g_end && ok;) {
-                const RowPos p = locate(job0, c, j, g, g_end);
-                const TcJob* J = p.J;
-                const int x = p.strip * SEG + jx;
-                const bool in_img = x < J->nx;
-                const int64_t plane = (int64_t)J->ny * J->nx;
-                const float* xin = J->xin ? J->xin + p.img * plane : nullptr;
-                float* dout = J->dout + p.img * plane;
-                auto step = [&](float& Xprev, float& Xcur, int ri, uint32_t taddr, float xv) {
-                    float pr[4];
-                    ptx::tmem_ld4(taddr, pr);
-                    if (ri >= 1) {
-                        Xprev += pr[2];
-                        const float G = FP8 ? fmaf(Xprev, c.scale[0], c.bias[0]) : Xprev + c.bias[0];
-                        // d = x - G, or the residual G itself when no x is given
-                        if (in_img) dout[(int64_t)(p.y + ri - 1) * J->nx + x] = xin ? xv - G : G;
-                    }
-                    if (ri >= 0 && ri < p.len) Xcur += pr[1];
-                    if (ri + 1 < p.len) Xprev = pr[0];
-                };
-                for (int ri = -1; ri <= p.len; ++ri, ++L) {
-                    const uint32_t reg = L % NACC, u = L / NACC;
-                    // x of the output row this step completes, loaded before the wait
-                    const float xv = (xin && ri >= 1 && in_img) ? __ldg(xin + (int64_t)(p.y + ri - 1) * J->nx + x) : 0.f;
-                    if (!__all_sync(0xffffffffu, ptx::mbar_wait(&tfull[reg], u & 1, abort_flag, BUDGET))) { ok = false; break; }
-                    ptx::tc_fence_after();
-                    const uint32_t taddr = lane_base + reg * Mode::RSTRIDE;
-                    if ((ri + 1) & 1) step(X1, X0, ri, taddr, xv);
-                    else step(X0, X1, ri, taddr, xv);
-                    ptx::tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) ptx::mbar_arrive(&tempty[reg]);
-                }
-                g += p.len;
-            }
-        } else {
+    } else if constexpr (LAST) {
+        // ---------------- epilogue of the last layer: warps 2..5 own TMEM lane
+        // quadrants 2,3,0,1. Output row r = P_{r-1}[col 0] + P_r[col 1] +
+        // P_{r+1}[col 2] (+ bias): G, or d = x - G when x is given. Input rows
+        // are drained four at a time: four TMEM loads, one wait.
         const int quad = warp & 3;
         const int jx = quad * 32 + lane;
         const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
         uint32_t L = 0;
         bool ok = true;
         int j = 0;
-        float X0[64], X1[64];   // partial sums of the output rows of even / odd index
+        float X0 = 0.f, X1 = 0.f;
+        for (int64_t g = g_begin; g < g_end && ok;) {
+            const RowPos p = locate(job0, c, j, g, g_end);
+            const TcJob* J = p.J;
+            const int x = p.strip * SEG + jx;
+            const bool in_img = x < J->nx;
+            const int64_t plane = (int64_t)J->ny * J->nx;
+            const float* xin = J->xin ? J->xin + p.img * plane : nullptr;
+            float* dout = J->dout + p.img * plane;
+            auto step = [&](float& Xprev, float& Xcur, int ri, const uint32_t* pr, float xv) {
+                if (ri >= 1) {
+                    Xprev += __uint_as_float(pr[2]);
+                    const float G = FP8 ? fmaf(Xprev, c.scale[0], c.bias[0]) : Xprev + c.bias[0];
+                    // d = x - G, or the residual G itself when no x is given
+                    if (in_img) dout[(int64_t)(p.y + ri - 1) * J->nx + x] = xin ? xv - G : G;
+                }
+                if (ri >= 0 && ri < p.len) Xcur += __uint_as_float(pr[1]);
+                if (ri + 1 < p.len) Xprev = __uint_as_float(pr[0]);
+            };
+            // chunks of 4 input rows starting at ri0 = -1, 3, 7, ...: the row
+            // parity of chunk member k is that of k
+            for (int ri0 = -1; ri0 <= p.len && ok; ri0 += 4) {
+                const int nb = min(4, p.len + 1 - ri0);
+                float xv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int ri = ri0 + k;
+                    xv[k] = (k < nb && xin && ri >= 1 && in_img)
+                                ? __ldg(xin + (int64_t)(p.y + ri - 1) * J->nx + x) : 0.f;
+                }
+                bool w = true;
+                for (int k = 0; k < nb && w; ++k) {
+                    const uint32_t Lk = L + k;
+                    w = ptx::mbar_wait(&tfull[Lk % NACC], (Lk / NACC) & 1, abort_flag, BUDGET);
+                }
+                if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+                ptx::tc_fence_after();
+                uint32_t pr[4][4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < nb) ptx::tmem_ld_32x32b_x4(lane_base + ((L + k) % NACC) * Mode::RSTRIDE, pr[k]);
+                ptx::tmem_ld_wait();
+#pragma unroll
+                for (int k = 0; k < 4; ++k) ptx::tie_regs4(pr[k]);
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    for (int k = 0; k < nb; ++k) ptx::mbar_arrive(&tempty[(L + k) % NACC]);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (k >= nb) break;
+                    // output row q lives in X[q & 1]: prev = X[(ri-1) & 1], cur = X[ri & 1]
+                    if (k & 1) step(X1, X0, ri0 + k, pr[k], xv[k]);
+                    else step(X0, X1, ri0 + k, pr[k], xv[k]);
+                }
+                L += nb;
+            }
+            g += p.len;
+        }
+    } else {
+        // ---------------- epilogue of an F -> F layer: warps 2..5 own TMEM lane
+        // quadrants 2,3,0,1. Per input row two TMEM round trips: P^2 (completes
+        // output row ri - 1, stored), then P^1 and P^0 together (P^0 straight
+        // into the registers the stored row freed).
+        const int quad = warp & 3;
+        const int jx = quad * 32 + lane;
+        const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
+        uint32_t L = 0;
+        bool ok = true;
+        int j = 0;
+        // partial sums of the output rows of even / odd index, FP32 bit patterns
+        // (TMEM loads write them directly)
+        uint32_t X0[64], X1[64];
         for (int64_t g = g_begin; g < g_end && ok;) {
             const RowPos p = locate(job0, c, j, g, g_end);
             const TcJob* J = p.J;
@@ -365,8 +400,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             const int nxp = J->nxp;
             const bool col_ok = x < nxp;
             const bool x_valid = x < J->nx && x >= rc.x0 && x < rc.x1;
-            __nv_bfloat16* obase = J->out + ((((int64_t)p.img * J->ny) * 8) * nxp + x) * 8;
-            auto store_row = [&](const float* acc, int yy) {
+            auto store_row = [&](const uint32_t* accb, int yy) {
+                auto acc = [&](int k) { return __uint_as_float(accb[k]); };
                 if (!col_ok) return;
                 const bool valid = x_valid && yy >= rc.y0 && yy < rc.y1;
                 if constexpr (FP8) {
@@ -382,7 +417,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 #pragma unroll
                             for (int h = 0; h < 4; ++h) {
                                 const int ch = cg * 16 + 4 * e + h;
-                                const float t = fmaxf(fmaf(acc[ch], c.scale[ch], c.bias[ch]), 0.f);
+                                const float t = fmaxf(fmaf(acc(ch), c.scale[ch], c.bias[ch]), 0.f);
                                 v[h] = valid ? t * c.inv_out : 0.f;
                             }
                             const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[0], v[1]), __NV_SATFINITE, __NV_E4M3);
@@ -392,15 +427,16 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                         *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     }
                 } else {
-                    __nv_bfloat16* o = obase + (int64_t)yy * 8 * nxp * 8;
+                    // BF16 activations: [img][y][8 cg][xp][8]
+                    __nv_bfloat16* o = J->out + ((((int64_t)p.img * J->ny + yy) * 8) * nxp + x) * 8;
 #pragma unroll
                     for (int cg = 0; cg < 8; ++cg) {
                         uint32_t pk[4];
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int c0 = cg * 8 + 2 * e;
-                            float v0 = fmaxf(acc[c0] + c.bias[c0], 0.f);
-                            float v1 = fmaxf(acc[c0 + 1] + c.bias[c0 + 1], 0.f);
+                            float v0 = fmaxf(acc(c0) + c.bias[c0], 0.f);
+                            float v1 = fmaxf(acc(c0 + 1) + c.bias[c0 + 1], 0.f);
                             if (!valid) v0 = v1 = 0.f;
                             __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
                             pk[e] = *reinterpret_cast<uint32_t*>(&h2);
@@ -411,20 +447,42 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             };
             // input row ri adds P^2 to output row ri-1 (then complete), P^1 to
             // output row ri, and starts output row ri+1 with P^0
-            auto step = [&](float* Xprev, float* Xcur, int ri, uint32_t taddr) {
+            auto step = [&](uint32_t* Xprev, uint32_t* Xcur, int ri, uint32_t taddr) {
+                uint32_t t[64];
                 if (ri >= 1) {
-                    tm_add64(taddr + 2 * F, Xprev);
+                    ptx::tmem_ld_32x32b_x64(taddr + 2 * F, t);
+                    ptx::tmem_ld_wait();
+                    ptx::tie_regs32(t);
+                    ptx::tie_regs32(t + 32);
+#pragma unroll
+                    for (int e = 0; e < 64; ++e)
+                        Xprev[e] = __float_as_uint(__uint_as_float(Xprev[e]) + __uint_as_float(t[e]));
                     store_row(Xprev, p.y + ri - 1);
                 }
-                if (ri >= 0 && ri < p.len) tm_add64(taddr + F, Xcur);
-                if (ri + 1 < p.len) tm_load64(taddr, Xprev);
+                // both loads unconditional (conditional asm outputs into the
+                // register arrays would force them to memory): P^1 is added only
+                // when row ri exists, and Xprev holds no live data any more -
+                // it was stored above, or belongs to a row before the image
+                const bool s1 = ri >= 0 && ri < p.len;
+                ptx::tmem_ld_32x32b_x64(taddr + F, t);
+                ptx::tmem_ld_32x32b_x64(taddr, Xprev);
+                ptx::tmem_ld_wait();
+                ptx::tie_regs32(t);
+                ptx::tie_regs32(t + 32);
+                ptx::tie_regs32(Xprev);
+                ptx::tie_regs32(Xprev + 32);
+                if (s1) {
+#pragma unroll
+                    for (int e = 0; e < 64; ++e)
+                        Xcur[e] = __float_as_uint(__uint_as_float(Xcur[e]) + __uint_as_float(t[e]));
+                }
             };
             for (int ri = -1; ri <= p.len; ++ri, ++L) {
                 const uint32_t reg = L % NACC, u = L / NACC;
                 if (!__all_sync(0xffffffffu, ptx::mbar_wait(&tfull[reg], u & 1, abort_flag, BUDGET))) { ok = false; break; }
                 ptx::tc_fence_after();
                 const uint32_t taddr = lane_base + reg * Mode::RSTRIDE;
-                // output row k lives in X[k & 1]: prev = X[(ri-1) & 1], cur = X[ri & 1]
+                // output row q lives in X[q & 1]: prev = X[(ri-1) & 1], cur = X[ri & 1]
                 if ((ri + 1) & 1) step(X1, X0, ri, taddr);
                 else step(X0, X1, ri, taddr);
                 ptx::tc_fence_before();
@@ -432,8 +490,6 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
                 if (lane == 0) ptx::mbar_arrive(&tempty[reg]);
             }
             g += p.len;
-        }
-    
         }
     }
 
@@ -447,31 +503,37 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
-// First layer 1 -> 64 on the tensor cores. Each CTA takes one 128-pixel row
-// segment: every thread gathers its pixel's 3 x 3 taps of the FP32 image (zero
-// outside it) into one row of A (M = 128 pixels, K = 32), one thread issues
-// two 128 x 64 x 16 MMAs into 64 TMEM columns, and the four warps read their
-// 32 lanes back, apply ReLU and the valid-rect mask and store 64 channels per
-// pixel (BF16 planes, or E4M3 scaled by inv_out). BF16 operands would round
-// the FP32 image and weights to 8 bits; instead each is split into a BF16 head
-// and a BF16 tail (v = hi + lo, |lo| <= 2^-9 |v|) and K carries
-// x_hi w_hi + x_lo w_hi + x_hi w_lo + b_hi + b_lo (the dropped x_lo w_lo is
-// below 2^-17 of each product), accumulated in FP32:
+// First layer 1 -> 64 on the tensor cores. Persistent CTAs of 128 threads walk
+// the image's 128-pixel row segments; for each, every thread gathers its
+// pixel's 3 x 3 taps of the FP32 image (zero outside it) into one row of A
+// (M = 128 pixels, K = 32), one thread issues two 128 x 64 x 16 MMAs into one
+// of two 64-column TMEM buffers, and the four warps read their 32 lanes back,
+// apply ReLU and the valid-rect mask and store 64 channels per pixel (BF16
+// planes, or E4M3 scaled by inv_out). The loop is software-pipelined: the
+// taps of segment k + 1 are loaded while the epilogue of segment k - 1 runs
+// and the MMAs of segment k are in flight.
+//
+// BF16 operands would round the FP32 image and weights to 8 bits; instead each
+// is split into a BF16 head and a BF16 tail (v = hi + lo, |lo| <= 2^-9 |v|)
+// and K carries x_hi w_hi + x_lo w_hi + x_hi w_lo + b_hi + b_lo (the dropped
+// x_lo w_lo is below 2^-17 of each product), accumulated in FP32:
 //   A row (pixel)  : [x_hi(9) | x_lo(9) | x_hi(9) | 1 | 1 | 0 0 0]
 //   B row (channel): [w_hi(9) | w_hi(9) | w_lo(9) | b_hi | b_lo | 0 0 0]
 // Operands in the no-swizzle K-major layout: A [kc 4][pixel 128][8] (LBO
 // 2048 B, SBO 128 B), B [kc 4][channel 64][8] (LBO 1024 B, SBO 128 B).
 // ---------------------------------------------------------------------------
 namespace ftc {
-constexpr int A_BYTES = 4 * 128 * 16;          // 8192
+constexpr int A_BYTES = 4 * 128 * 16;          // 8192 per buffer
 constexpr int B_BYTES = 4 * 64 * 16;           // 4096
-constexpr int OFF_A = 0;
-constexpr int OFF_B = OFF_A + A_BYTES;
-constexpr int OFF_BAR = OFF_B + B_BYTES;
-constexpr int OFF_MISC = OFF_BAR + 8;
-// requested dynamic shared memory: caps residency at 8 CTAs per SM, so the
-// CTAs of an SM never ask for more than its 512 TMEM columns (8 x 64)
-constexpr int SMEM = 27 * 1024;
+constexpr int OFF_A = 0;                       // two A buffers
+constexpr int OFF_B = OFF_A + 2 * A_BYTES;
+constexpr int OFF_BAR = OFF_B + B_BYTES;       // two mbarriers
+constexpr int OFF_MISC = OFF_BAR + 16;
+constexpr int CTAS_PER_SM = 4;
+constexpr int TMEM_COLS = 128;                 // 2 x 64; 4 CTAs x 128 = 512 per SM
+// requested dynamic shared memory: also caps residency at 4 CTAs per SM, so the
+// CTAs of an SM never ask for more than its 512 TMEM columns
+constexpr int SMEM = 52 * 1024;
 constexpr uint32_t IDESC = ptx::idesc_bf16_f32(128, 64);
 constexpr long long BUDGET = 2000000000LL;
 }  // namespace ftc
@@ -484,87 +546,89 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 template <bool FP8>
 __global__ void __launch_bounds__(128) k_first_tc(const float* __restrict__ x,
                                                   const uint4* __restrict__ wb, int ny, int nx,
-                                                  int nxp, const Rect* __restrict__ rects,
+                                                  int nxp, int nimg, const Rect* __restrict__ rects,
                                                   void* __restrict__ out_, float inv_out,
                                                   int* __restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* As = smem + ftc::OFF_A;
     uint8_t* Bs = smem + ftc::OFF_B;
     uint64_t* bar = (uint64_t*)(smem + ftc::OFF_BAR);
     uint32_t* tmem_slot = (uint32_t*)(smem + ftc::OFF_MISC);
     volatile int* abort_flag = (volatile int*)(smem + ftc::OFF_MISC + 4);
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int warp = threadIdx.x / 32;
     const int p = threadIdx.x;
-    const int xx = blockIdx.x * 128 + p;
-    const int yy = blockIdx.y, img = blockIdx.z;
+    const int nsx = (nxp + 127) / 128;
+    const int64_t nseg = (int64_t)nimg * ny * nsx;
+    const int64_t plane = (int64_t)ny * nx;
 
     if (threadIdx.x == 0) {
-        ptx::mbar_init(bar, 1);
+        ptx::mbar_init(&bar[0], 1);
+        ptx::mbar_init(&bar[1], 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
     // the .sync.aligned TMEM calls are issued by warp 1, whose lanes never diverge before them
     if (warp == 1) {
-        ptx::tmem_alloc(tmem_slot, 64);
+        ptx::tmem_alloc(tmem_slot, ftc::TMEM_COLS);
         ptx::tmem_relinquish();
     }
     // B: 4 KB of weights, 32 B per thread (constant: read before the predecessor finishes)
     reinterpret_cast<uint4*>(Bs)[2 * p] = __ldg(wb + 2 * p);
     reinterpret_cast<uint4*>(Bs)[2 * p + 1] = __ldg(wb + 2 * p + 1);
-    __syncthreads();   // TMEM allocated (warp 1) before dependents may launch
-    pdl_launch_dependents();
-    pdl_wait();
-    // A: this pixel's taps, split into BF16 head and tail
-    const int64_t plane = (int64_t)ny * nx;
-    float hi[9], lo[9];
-#pragma unroll
-    for (int t = 0; t < 9; ++t) {
-        const int sy = yy + t / 3 - 1, sx = xx + t % 3 - 1;
-        const float v = (sy >= 0 && sy < ny && sx >= 0 && sx < nx)
-                            ? __ldg(x + img * plane + (int64_t)sy * nx + sx)
-                            : 0.f;
-        hi[t] = __bfloat162float(__float2bfloat16_rn(v));
-        lo[t] = v - hi[t];
-    }
-    uint4 ch[4];
-    ch[0] = make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), pack_bf16(hi[4], hi[5]),
-                       pack_bf16(hi[6], hi[7]));
-    ch[1] = make_uint4(pack_bf16(hi[8], lo[0]), pack_bf16(lo[1], lo[2]), pack_bf16(lo[3], lo[4]),
-                       pack_bf16(lo[5], lo[6]));
-    ch[2] = make_uint4(pack_bf16(lo[7], lo[8]), pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]),
-                       pack_bf16(hi[4], hi[5]));
-    ch[3] = make_uint4(pack_bf16(hi[6], hi[7]), pack_bf16(hi[8], 1.f), pack_bf16(1.f, 0.f), 0u);
-#pragma unroll
-    for (int kc = 0; kc < 4; ++kc)
-        *reinterpret_cast<uint4*>(As + kc * 2048 + (p / 8) * 128 + (p % 8) * 16) = ch[kc];
-    ptx::fence_proxy_async_shared();   // generic-proxy smem writes -> tensor core
     ptx::tc_fence_before();
-    __syncthreads();
+    __syncthreads();   // TMEM allocated before dependents may launch
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    if (threadIdx.x == 0) {
-        const uint32_t a0 = ptx::smem_u32(As), b0 = ptx::smem_u32(Bs);
+    pdl_launch_dependents();
+    pdl_wait();
+
+    // taps of one pixel of segment `seg` (zero outside the image)
+    auto load_taps = [&](int64_t seg, float v[9]) {
+        const int bx = (int)(seg % nsx);
+        const int64_t r = seg / nsx;
+        const int yy = (int)(r % ny), img = (int)(r / ny);
+        const int xx = bx * 128 + p;
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
-            ptx::mma_bf16(tmem_base, ptx::smem_desc_noswizzle(a0 + k * 2 * 2048, 2048, 128),
-                          ptx::smem_desc_noswizzle(b0 + k * 2 * 1024, 1024, 128), ftc::IDESC,
-                          k);
-        ptx::mma_commit(bar);
-    }
-    __syncwarp();
-    // warp-uniform: the TMEM load below is .sync.aligned (all 32 lanes, converged)
-    const bool ok = __all_sync(0xffffffffu, ptx::mbar_wait(bar, 0, abort_flag, ftc::BUDGET));
-    ptx::tc_fence_after();
-    if (ok) {
+        for (int t = 0; t < 9; ++t) {
+            const int sy = yy + t / 3 - 1, sx = xx + t % 3 - 1;
+            v[t] = (sy >= 0 && sy < ny && sx >= 0 && sx < nx)
+                       ? __ldg(x + img * plane + (int64_t)sy * nx + sx)
+                       : 0.f;
+        }
+    };
+    auto write_a = [&](int buf, const float v[9]) {
+        float hi[9], lo[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            hi[t] = __bfloat162float(__float2bfloat16_rn(v[t]));
+            lo[t] = v[t] - hi[t];
+        }
+        uint4 ch[4];
+        ch[0] = make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]), pack_bf16(hi[4], hi[5]),
+                           pack_bf16(hi[6], hi[7]));
+        ch[1] = make_uint4(pack_bf16(hi[8], lo[0]), pack_bf16(lo[1], lo[2]), pack_bf16(lo[3], lo[4]),
+                           pack_bf16(lo[5], lo[6]));
+        ch[2] = make_uint4(pack_bf16(lo[7], lo[8]), pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]),
+                           pack_bf16(hi[4], hi[5]));
+        ch[3] = make_uint4(pack_bf16(hi[6], hi[7]), pack_bf16(hi[8], 1.f), pack_bf16(1.f, 0.f), 0u);
+        uint8_t* As = smem + ftc::OFF_A + buf * ftc::A_BYTES;
+#pragma unroll
+        for (int kc = 0; kc < 4; ++kc)
+            *reinterpret_cast<uint4*>(As + kc * 2048 + (p / 8) * 128 + (p % 8) * 16) = ch[kc];
+    };
+    // TMEM buffer `buf` -> ReLU, mask, 64 channels of this thread's pixel of segment `seg`
+    auto epilogue = [&](int64_t seg, int buf) {
         uint32_t acc[64];
-        ptx::tmem_ld_32x32b_x64(tmem_base + ((uint32_t)(warp * 32) << 16), acc);
+        ptx::tmem_ld_32x32b_x64(tmem_base + ((uint32_t)(warp * 32) << 16) + buf * 64, acc);
         ptx::tmem_ld_wait();
+        const int bx = (int)(seg % nsx);
+        const int64_t r = seg / nsx;
+        const int yy = (int)(r % ny), img = (int)(r / ny);
+        const int xx = bx * 128 + p;
+        if (xx >= nxp) return;   // past the padded width: nothing to store
         const Rect rc = rects ? rects[img] : Rect{0, ny, 0, nx};
         const bool valid = xx < nx && yy >= rc.y0 && yy < rc.y1 && xx >= rc.x0 && xx < rc.x1;
-        if (xx >= nxp) {
-            // past the padded width: nothing to store
-        } else if constexpr (FP8) {
+        if constexpr (FP8) {
             uint8_t* o = reinterpret_cast<uint8_t*>(out_) + (((int64_t)img * ny + yy) * 4 * nxp + xx) * 16;
 #pragma unroll
             for (int cg = 0; cg < 4; ++cg) {
@@ -598,14 +662,58 @@ __global__ void __launch_bounds__(128) k_first_tc(const float* __restrict__ x,
                 *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
         }
+    };
+
+    bool ok = true;
+    int64_t seg = blockIdx.x;
+    float v[9];
+    if (seg < nseg) load_taps(seg, v);
+    uint32_t k = 0;
+    for (; seg < nseg && ok; seg += gridDim.x, ++k) {
+        const int buf = k & 1;
+        // A[buf] and TMEM[buf] were last used by segment k - 2, whose MMAs the
+        // epilogue of iteration k - 1 waited for
+        write_a(buf, v);
+        ptx::fence_proxy_async_shared();   // generic-proxy smem writes -> tensor core
+        ptx::tc_fence_before();
+        __syncthreads();
+        ptx::tc_fence_after();
+        if (threadIdx.x == 0) {
+            const uint32_t a0 = ptx::smem_u32(smem + ftc::OFF_A + buf * ftc::A_BYTES);
+            const uint32_t b0 = ptx::smem_u32(Bs);
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk)
+                ptx::mma_bf16(tmem_base + buf * 64,
+                              ptx::smem_desc_noswizzle(a0 + kk * 2 * 2048, 2048, 128),
+                              ptx::smem_desc_noswizzle(b0 + kk * 2 * 1024, 1024, 128), ftc::IDESC,
+                              kk);
+            ptx::mma_commit(&bar[buf]);
+        }
+        __syncwarp();
+        // taps of the next segment in flight during the previous segment's epilogue
+        if (seg + gridDim.x < nseg) load_taps(seg + gridDim.x, v);
+        if (k > 0) {
+            const int pb = buf ^ 1;
+            // block-uniform: every thread leaves the loop in the same iteration
+            ok = __syncthreads_and(ptx::mbar_wait(&bar[pb], ((k - 1) >> 1) & 1, abort_flag, ftc::BUDGET));
+            ptx::tc_fence_after();
+            if (ok) epilogue(seg - gridDim.x, pb);
+            ptx::tc_fence_before();
+        }
+    }
+    if (ok && k > 0) {
+        const int pb = (k - 1) & 1;
+        ok = __syncthreads_and(ptx::mbar_wait(&bar[pb], ((k - 1) >> 1) & 1, abort_flag, ftc::BUDGET));
+        ptx::tc_fence_after();
+        if (ok) epilogue(seg - gridDim.x, pb);
     }
     ptx::tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         ptx::tc_fence_after();
-        ptx::tmem_dealloc(tmem_base, 64);
+        ptx::tmem_dealloc(tmem_base, ftc::TMEM_COLS);
     }
-    if (threadIdx.x == 0 && !ok && err) atomicExch(err, (int)PNP_ETIMEOUT);
+    if (threadIdx.x == 0 && *abort_flag && err) atomicExch(err, (int)PNP_ETIMEOUT);
 }
 
 // ---------------------------------------------------------------------------
@@ -702,11 +810,11 @@ cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64
     timer_begin(last ? T_CONV_LAST : T_CONV_TC, s);
     cudaError_t e;
     if (fp8) {
-        if (last) e = launch_pdl(k_conv_tc<true, true>, dim3(grid), dim3(tc::THREADS), TcMode<true, true>::SMEM, s, job0, c);
-        else e = launch_pdl(k_conv_tc<false, true>, dim3(grid), dim3(tc::THREADS), TcMode<false, true>::SMEM, s, job0, c);
+        if (last) e = launch_pdl(k_conv_tc<true, true>, dim3(grid), dim3(TcMode<true, true>::THREADS), TcMode<true, true>::SMEM, s, job0, c);
+        else e = launch_pdl(k_conv_tc<false, true>, dim3(grid), dim3(TcMode<false, true>::THREADS), TcMode<false, true>::SMEM, s, job0, c);
     } else {
-        if (last) e = launch_pdl(k_conv_tc<true, false>, dim3(grid), dim3(tc::THREADS), TcMode<true, false>::SMEM, s, job0, c);
-        else e = launch_pdl(k_conv_tc<false, false>, dim3(grid), dim3(tc::THREADS), TcMode<false, false>::SMEM, s, job0, c);
+        if (last) e = launch_pdl(k_conv_tc<true, false>, dim3(grid), dim3(TcMode<true, false>::THREADS), TcMode<true, false>::SMEM, s, job0, c);
+        else e = launch_pdl(k_conv_tc<false, false>, dim3(grid), dim3(TcMode<false, false>::THREADS), TcMode<false, false>::SMEM, s, job0, c);
     }
     timer_end(last ? T_CONV_LAST : T_CONV_TC, s);
     return e;
@@ -727,18 +835,21 @@ static cudaError_t launch_first_tc(const DenoiserDev& D, const float* x, int ny,
                                    cudaStream_t s) {
     static bool attr_done[2] = {false, false};
     if (!attr_done[FP8]) {
-        cudaError_t e = cudaFuncSetAttribute(k_first_tc<FP8>,
-                                             cudaFuncAttributePreferredSharedMemoryCarveout,
-                                             (int)cudaSharedmemCarveoutMaxShared);
+        cudaError_t e = cudaFuncSetAttribute(k_first_tc<FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             ftc::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_first_tc<FP8>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         attr_done[FP8] = true;
     }
     const int nxp = bf16_pad_width(nx);
-    dim3 g1(ceil_div(nxp, 128), ny, nimg);
+    const int64_t nseg = (int64_t)nimg * ny * ceil_div(nxp, 128);
+    const int grid = (int)std::min<int64_t>(nseg, (int64_t)num_sms() * ftc::CTAS_PER_SM);
     timer_begin(T_CONV_EDGE, s);
-    cudaError_t e = launch_pdl(k_first_tc<FP8>, g1, dim3(128), ftc::SMEM, s, x,
-                               reinterpret_cast<const uint4*>(D.wtc_first), ny, nx, nxp, rects,
-                               out, inv_out, err);
+    cudaError_t e = launch_pdl(k_first_tc<FP8>, dim3(grid), dim3(128), ftc::SMEM, s, x,
+                               reinterpret_cast<const uint4*>(D.wtc_first), ny, nx, nxp, nimg,
+                               rects, out, inv_out, err);
     timer_end(T_CONV_EDGE, s);
     return e;
 }
