@@ -28,7 +28,7 @@
 // two TMEM round trips per input row with 64-column loads (a load and wait
 // per 16 columns left the epilogue, not the tensor core, setting the pace).
 // Input rows circulate through an 8-slot shared-memory ring. The last layer
-// (one output channel) drains four input rows per wait, with an 11-slot ring
+// (one output channel) drains four input rows per wait, with a 12-slot ring
 // and eight 32-column TMEM regions.
 //
 // One launch covers a table of jobs (images of possibly different sizes,
@@ -93,7 +93,7 @@ struct TcMode {
     // F -> F layers hold 72 KB of weights and 2 x 192 TMEM columns; the last
     // layer's 6 KB of weights and 16-column regions leave room for a deeper
     // ring and 8 regions, so its MMAs run further ahead of its epilogue.
-    static constexpr int NS = LAST ? 11 : 8;
+    static constexpr int NS = LAST ? 12 : 8;
     static constexpr int NACC = LAST ? 8 : 2;
     static constexpr int RSTRIDE = LAST ? 32 : NB;   // TMEM columns between regions
     // epilogue warps, one per TMEM lane quadrant
@@ -557,8 +557,8 @@ __global__ void __launch_bounds__(128) k_first_tc(const float* __restrict__ x,
     volatile int* abort_flag = (volatile int*)(smem + ftc::OFF_MISC + 4);
     const int warp = threadIdx.x / 32;
     const int p = threadIdx.x;
-    const int nsx = (nxp + 127) / 128;
-    const int64_t nseg = (int64_t)nimg * ny * nsx;
+    const uint32_t nsx = (uint32_t)(nxp + 127) / 128;
+    const uint32_t nseg = (uint32_t)nimg * (uint32_t)ny * nsx;   // < 2^31 (checked by the host)
     const int64_t plane = (int64_t)ny * nx;
 
     if (threadIdx.x == 0) {
@@ -582,12 +582,22 @@ __global__ void __launch_bounds__(128) k_first_tc(const float* __restrict__ x,
     pdl_launch_dependents();
     pdl_wait();
 
-    // taps of one pixel of segment `seg` (zero outside the image)
-    auto load_taps = [&](int64_t seg, float v[9]) {
-        const int bx = (int)(seg % nsx);
-        const int64_t r = seg / nsx;
-        const int yy = (int)(r % ny), img = (int)(r / ny);
-        const int xx = bx * 128 + p;
+    // segment -> (image, row, 128-pixel column block)
+    struct Seg {
+        int img, yy, bx;
+    };
+    auto decompose = [&](uint32_t seg) {
+        const uint32_t r = seg / nsx;
+        Seg q;
+        q.bx = (int)(seg - r * nsx);
+        q.img = (int)(r / (uint32_t)ny);
+        q.yy = (int)(r - (uint32_t)q.img * (uint32_t)ny);
+        return q;
+    };
+    // taps of one pixel of segment q (zero outside the image)
+    auto load_taps = [&](const Seg& q, float v[9]) {
+        const int yy = q.yy, img = q.img;
+        const int xx = q.bx * 128 + p;
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
             const int sy = yy + t / 3 - 1, sx = xx + t % 3 - 1;
@@ -616,15 +626,13 @@ __global__ void __launch_bounds__(128) k_first_tc(const float* __restrict__ x,
         for (int kc = 0; kc < 4; ++kc)
             *reinterpret_cast<uint4*>(As + kc * 2048 + (p / 8) * 128 + (p % 8) * 16) = ch[kc];
     };
-    // TMEM buffer `buf` -> ReLU, mask, 64 channels of this thread's pixel of segment `seg`
-    auto epilogue = [&](int64_t seg, int buf) {
+    // TMEM buffer `buf` -> ReLU, mask, 64 channels of this thread's pixel of segment q
+    auto epilogue = [&](const Seg& q, int buf) {
         uint32_t acc[64];
         ptx::tmem_ld_32x32b_x64(tmem_base + ((uint32_t)(warp * 32) << 16) + buf * 64, acc);
         ptx::tmem_ld_wait();
-        const int bx = (int)(seg % nsx);
-        const int64_t r = seg / nsx;
-        const int yy = (int)(r % ny), img = (int)(r / ny);
-        const int xx = bx * 128 + p;
+        const int yy = q.yy, img = q.img;
+        const int xx = q.bx * 128 + p;
         if (xx >= nxp) return;   // past the padded width: nothing to store
         const Rect rc = rects ? rects[img] : Rect{0, ny, 0, nx};
         const bool valid = xx < nx && yy >= rc.y0 && yy < rc.y1 && xx >= rc.x0 && xx < rc.x1;
@@ -665,9 +673,10 @@ __global__ void __launch_bounds__(128) k_first_tc(const float* __restrict__ x,
     };
 
     bool ok = true;
-    int64_t seg = blockIdx.x;
+    uint32_t seg = blockIdx.x;
     float v[9];
-    if (seg < nseg) load_taps(seg, v);
+    Seg cur = decompose(seg), prev = cur;
+    if (seg < nseg) load_taps(cur, v);
     uint32_t k = 0;
     for (; seg < nseg && ok; seg += gridDim.x, ++k) {
         const int buf = k & 1;
@@ -691,21 +700,24 @@ __global__ void __launch_bounds__(128) k_first_tc(const float* __restrict__ x,
         }
         __syncwarp();
         // taps of the next segment in flight during the previous segment's epilogue
-        if (seg + gridDim.x < nseg) load_taps(seg + gridDim.x, v);
+        const Seg next = decompose(seg + gridDim.x);
+        if (seg + gridDim.x < nseg) load_taps(next, v);
         if (k > 0) {
             const int pb = buf ^ 1;
             // block-uniform: every thread leaves the loop in the same iteration
             ok = __syncthreads_and(ptx::mbar_wait(&bar[pb], ((k - 1) >> 1) & 1, abort_flag, ftc::BUDGET));
             ptx::tc_fence_after();
-            if (ok) epilogue(seg - gridDim.x, pb);
+            if (ok) epilogue(prev, pb);
             ptx::tc_fence_before();
         }
+        prev = cur;
+        cur = next;
     }
     if (ok && k > 0) {
         const int pb = (k - 1) & 1;
         ok = __syncthreads_and(ptx::mbar_wait(&bar[pb], ((k - 1) >> 1) & 1, abort_flag, ftc::BUDGET));
         ptx::tc_fence_after();
-        if (ok) epilogue(seg - gridDim.x, pb);
+        if (ok) epilogue(prev, pb);
     }
     ptx::tc_fence_before();
     __syncthreads();
@@ -845,6 +857,7 @@ static cudaError_t launch_first_tc(const DenoiserDev& D, const float* x, int ny,
     }
     const int nxp = bf16_pad_width(nx);
     const int64_t nseg = (int64_t)nimg * ny * ceil_div(nxp, 128);
+    if (nseg + (int64_t)num_sms() * ftc::CTAS_PER_SM >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
     const int grid = (int)std::min<int64_t>(nseg, (int64_t)num_sms() * ftc::CTAS_PER_SM);
     timer_begin(T_CONV_EDGE, s);
     cudaError_t e = launch_pdl(k_first_tc<FP8>, dim3(grid), dim3(128), ftc::SMEM, s, x,

@@ -236,3 +236,28 @@ def test_bf16_mmse_psnr_matches_fp32(P):
         ps[prec] = 10 * np.log10(1.0 / np.mean((mm - prob.xbar) ** 2))
     print("MMSE PSNR fp32 %.3f dB  bf16 %.3f dB" % (ps["fp32"], ps["bf16"]))
     assert abs(ps["fp32"] - ps["bf16"]) <= 0.1
+
+
+@pytest.mark.parametrize("blocks,halo", [((1, 1), 0), ((2, 2), 8)])
+def test_bf16_one_step_against_oracle(P, orc, blocks, halo):
+    """One BF16 step from an injected state against the FP64 oracle, in the
+    direct and the block + halo layouts: the difference is the prior term's
+    BF16 error, c_prior |G_bf16 - G|, bounded like the denoiser tests (3 % of
+    max |G|), on a ragged 72 x 136 image."""
+    prob = synth.make_problem(72, 136, synth.uniform_kernel(5), 25.0, 909)
+    dw = synth.workload_denoiser(2)
+    den = P.Denoiser.from_weights(dw)
+    net = orc.Net.from_weights(dw)
+    gp = P.Problem(prob.y, prob.h, prob.sigma, den, blocks=blocks, halo=halo, seed=prob.seed,
+                   burn_in=0, precision="bf16")
+    prm = gp.params()
+    x0 = np.clip(prob.y + 0.03, 0, 1).astype(np.float64)
+    gp.set_state(x0, 3)
+    gp.step(1)
+    x1, _ = gp.state()
+    op = oracle_problem(orc, prob, prm, net)
+    ref = orc.langevin_step(op, x0, 3)
+    G = x0 - orc.denoise(x0, net)
+    c_prior = prm["alpha"] * prm["gamma"] / prm["eps"] ** 2
+    bound = c_prior * 3e-2 * np.abs(G).max() + 1e-5 * np.abs(ref).max()
+    assert np.abs(x1[0] - ref).max() <= bound, (np.abs(x1[0] - ref).max(), bound)
