@@ -47,6 +47,16 @@ class _Problem(C.Structure):
                 ("net", C.POINTER(_Net)), ("noise", C.c_int)]
 
 
+class _Poisson(C.Structure):
+    _fields_ = [("ny", C.c_int), ("nx", C.c_int), ("y", C.POINTER(C.c_double)),
+                ("h", C.POINTER(C.c_double)), ("kh", C.c_int), ("kw", C.c_int),
+                ("eta", C.c_double), ("rho1", C.c_double), ("rho2", C.c_double),
+                ("kappa1", C.c_double), ("kappa2", C.c_double),
+                ("alpha", C.c_double), ("eps", C.c_double),
+                ("lam", C.c_double), ("gamma", C.c_double), ("seed", C.c_uint64),
+                ("net", C.POINTER(_Net)), ("noise", C.c_int)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -66,6 +76,11 @@ def lib():
         _lib.ora_run_chain.argtypes = [C.POINTER(_Problem), d, i, i, i, u32, d, d,
                                        C.POINTER(C.c_int64), d]
         _lib.ora_moments_two_pass.argtypes = [d, i64, i64, d, d]
+        _lib.ora_normals_stream.argtypes = [C.c_uint64, u32, u32, u32, i64, d]
+        _lib.ora_kl_prox.argtypes = [C.c_double] * 3
+        _lib.ora_kl_prox.restype = C.c_double
+        _lib.ora_poisson_stepsizes.argtypes = [C.c_double] * 8 + [d] * 4
+        _lib.ora_poisson_step.argtypes = [C.POINTER(_Poisson), d, d, d, u32, u32, d, d, d]
     return _lib
 
 
@@ -211,6 +226,55 @@ def run_chain(p: Problem, x0, T: int, burn_in: int, chain: int = 0, t0: int = 0,
                         C.byref(n), _dp(samples) if samples is not None
                         else C.POINTER(C.c_double)())
     return dict(x=x, mean=mean, m2=m2, n=n.value, samples=samples)
+
+
+# ---------------------------------------------------------------- Poisson (AXDA + PSGLA)
+
+def normals_stream(seed: int, t: int, chain: int, stream: int, n: int):
+    xi = np.zeros(n)
+    lib().ora_normals_stream(C.c_uint64(seed), t, chain, stream, n, _dp(xi))
+    return xi
+
+
+def kl_prox(v, y, kappa):
+    return lib().ora_kl_prox(float(v), float(y), float(kappa))
+
+
+def poisson_stepsizes(hnorm, eta, rho1, rho2, alpha, eps, lip_eps, c=0.99):
+    """-> (lambda, gamma, kappa1, kappa2)."""
+    o = [C.c_double() for _ in range(4)]
+    lib().ora_poisson_stepsizes(hnorm, eta, rho1, rho2, alpha, eps, lip_eps, c,
+                                *[C.byref(v) for v in o])
+    return tuple(v.value for v in o)
+
+
+class PoissonProblem:
+    """Poisson-noise deconvolution sampled with AXDA + PnP-ULA / PSGLA."""
+
+    def __init__(self, y, h, eta, rho1, rho2, kappa1, kappa2, alpha, eps, lam, gamma, seed,
+                 net: Net | None = None, noise=True):
+        self.y = _f64(y)
+        self.h = _f64(h)
+        self.net = net
+        self.s = _Poisson(self.y.shape[0], self.y.shape[1], _dp(self.y), _dp(self.h),
+                          self.h.shape[0], self.h.shape[1], float(eta), float(rho1), float(rho2),
+                          float(kappa1), float(kappa2), float(alpha), float(eps), float(lam),
+                          float(gamma), C.c_uint64(seed),
+                          C.pointer(net.s) if net is not None else C.POINTER(_Net)(),
+                          int(bool(noise)))
+
+    @property
+    def shape(self):
+        return self.y.shape
+
+
+def poisson_step(p: PoissonProblem, x, z1, z2, t: int, chain: int = 0):
+    """-> (x+, z1+, z2+)."""
+    x, z1, z2 = _f64(x), _f64(z1), _f64(z2)
+    xn, z1n, z2n = np.empty_like(x), np.empty_like(x), np.empty_like(x)
+    lib().ora_poisson_step(C.byref(p.s), _dp(x), _dp(z1), _dp(z2), t, chain, _dp(xn), _dp(z1n),
+                           _dp(z2n))
+    return xn, z1n, z2n
 
 
 def moments_two_pass(samples):

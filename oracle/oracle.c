@@ -301,6 +301,104 @@ void ora_run_chain(const ora_problem* p, double* x, int t0, int T, int burn_in,
     free(xn);
 }
 
+void ora_normals_stream(uint64_t seed, uint32_t t, uint32_t chain, uint32_t stream, int64_t n,
+                        double* xi) {
+    const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    const double two_pi = 6.283185307179586476925286766559;
+    int64_t groups = (n + 3) / 4;
+#pragma omp parallel for schedule(static)
+    for (int64_t m = 0; m < groups; ++m) {
+        uint32_t ctr[4] = {(uint32_t)m, t, chain, stream};
+        uint32_t w[4];
+        ora_philox4x32_10(ctr, key, w);
+        double u[4];
+        for (int k = 0; k < 4; ++k) u[k] = ((double)(w[k] >> 8) + 0.5) * 5.9604644775390625e-08;
+        double r0 = sqrt(-2.0 * log(u[0])), r1 = sqrt(-2.0 * log(u[2]));
+        double z[4] = {r0 * cos(two_pi * u[1]), r0 * sin(two_pi * u[1]),
+                       r1 * cos(two_pi * u[3]), r1 * sin(two_pi * u[3])};
+        for (int k = 0; k < 4; ++k)
+            if (4 * m + k < n) xi[4 * m + k] = z[k];
+    }
+}
+
+double ora_kl_prox(double v, double y, double kappa) {
+    /* minimiser of kappa (u - y log u) + (u - v)^2 / 2 over u > 0 (u >= 0 when y = 0) */
+    double a = v - kappa;
+    return 0.5 * (a + sqrt(a * a + 4.0 * kappa * y));
+}
+
+void ora_poisson_stepsizes(double hnorm, double eta, double rho1, double rho2, double alpha,
+                           double eps, double lip_eps, double c, double* lambda, double* gamma,
+                           double* kappa1, double* kappa2) {
+    double c1 = eta * hnorm * eta * hnorm / rho1; /* ||eta H||^2 / rho1 */
+    double c2 = 1.0 / rho2;
+    double prior = alpha * lip_eps / (eps * eps);
+    double lam = 0.99 / (4.0 * c1 + 4.0 * c2 + 2.0 * prior);
+    *lambda = lam;
+    *gamma = c / (3.0 * (prior + c1 + c2 + 1.0 / lam));
+    *kappa1 = 0.99 * rho1;
+    *kappa2 = 0.99 * rho2;
+}
+
+/* ---------------------------------------------------------------------------
+ * One transition of the Poisson sampler (Eqs. 13-14 with f1 = 0 and the two
+ * AXDA blocks):
+ *   x+  = x - gamma [ (eta/rho1) H^T (eta H x - z1) + (x - z2)/rho2 ]
+ *           + (alpha gamma / eps^2)(D(x) - x) + (gamma / lambda)(proj_[0,1](x) - x)
+ *           + sqrt(2 gamma) xi                                   (xi: stream 0)
+ *   z1+ = prox_{kappa1 KL(y||.)}( z1 - (kappa1/rho1)(z1 - eta H x+) + sqrt(2 kappa1) zeta1 )
+ *   z2+ = max( z2 - (kappa2/rho2)(z2 - x+) + sqrt(2 kappa2) zeta2, 0 )
+ * ------------------------------------------------------------------------- */
+void ora_poisson_step(const ora_poisson* p, const double* x, const double* z1, const double* z2,
+                      uint32_t t, uint32_t chain, double* xnew, double* z1new, double* z2new) {
+    const int64_t N = (int64_t)p->ny * p->nx;
+    double* r = (double*)malloc(sizeof(double) * N);
+    double* g = (double*)malloc(sizeof(double) * N);
+    double* d = p->net ? (double*)malloc(sizeof(double) * N) : NULL;
+    double* xi = (double*)calloc(N, sizeof(double));
+    double* ze1 = (double*)calloc(N, sizeof(double));
+    double* ze2 = (double*)calloc(N, sizeof(double));
+    /* x-update */
+    ora_blur(x, p->ny, p->nx, p->h, p->kh, p->kw, r);
+    for (int64_t n = 0; n < N; ++n) r[n] = p->eta * r[n] - z1[n];
+    ora_blur_adj(r, p->ny, p->nx, p->h, p->kh, p->kw, g);
+    if (d) ora_denoise(x, p->ny, p->nx, p->net, d);
+    if (p->noise) {
+        ora_normals_stream(p->seed, t, chain, 0, N, xi);
+        ora_normals_stream(p->seed, t, chain, 1, N, ze1);
+        ora_normals_stream(p->seed, t, chain, 2, N, ze2);
+    }
+    const double gam = p->gamma;
+    const double cprior = p->alpha * gam / (p->eps * p->eps);
+    const double cproj = p->lambda > 0.0 ? gam / p->lambda : 0.0;
+    for (int64_t n = 0; n < N; ++n) {
+        double xv = x[n];
+        double grad = (p->eta / p->rho1) * g[n] + (xv - z2[n]) / p->rho2;
+        double v = xv - gam * grad;
+        if (d) v += cprior * (d[n] - xv);
+        double pr = xv < 0.0 ? 0.0 : (xv > 1.0 ? 1.0 : xv);
+        v += cproj * (pr - xv);
+        v += sqrt(2.0 * gam) * xi[n];
+        xnew[n] = v;
+    }
+    /* z-update from the new x */
+    ora_blur(xnew, p->ny, p->nx, p->h, p->kh, p->kw, r);
+    for (int64_t n = 0; n < N; ++n) {
+        double w1 = z1[n] - (p->kappa1 / p->rho1) * (z1[n] - p->eta * r[n]) +
+                    sqrt(2.0 * p->kappa1) * ze1[n];
+        z1new[n] = ora_kl_prox(w1, p->y[n], p->kappa1);
+        double w2 = z2[n] - (p->kappa2 / p->rho2) * (z2[n] - xnew[n]) +
+                    sqrt(2.0 * p->kappa2) * ze2[n];
+        z2new[n] = w2 > 0.0 ? w2 : 0.0;
+    }
+    free(r);
+    free(g);
+    free(d);
+    free(xi);
+    free(ze1);
+    free(ze2);
+}
+
 /* Two-pass moments of stored samples: mean, then unbiased variance. */
 void ora_moments_two_pass(const double* samples, int64_t n, int64_t npix,
                           double* mean, double* var) {

@@ -89,6 +89,48 @@ void ora_run_chain(const ora_problem* p, double* x, int t0, int T, int burn_in,
 void ora_moments_two_pass(const double* samples, int64_t n, int64_t npix,
                           double* mean, double* var);
 
+/* ---------------------------------------------------------------------------
+ * Deconvolution under Poisson noise (Sec. IV-A, Poisson case), sampled with
+ * the AXDA-split PnP-ULA / PSGLA scheme (Eqs. 13-14, Algorithm 1):
+ *   y ~ Poisson(eta H xbar),  f1 = 0,
+ *   f2(H2 x) = KL(y || eta H x) + iota_{R+}(x),  H2 x = (eta H x, x),
+ *   z = (z1, z2) coupled to (eta H x, x) with rho1, rho2,
+ *   KL(y || u) = sum_n u_n - y_n + y_n log(y_n / u_n).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int ny, nx;
+    const double* y;         /* photon counts [ny*nx]                         */
+    const double* h;         /* blur kernel [kh*kw], anchored at (kh/2, kw/2) */
+    int kh, kw;
+    double eta;              /* y ~ Poisson(eta H x)                          */
+    double rho1, rho2;       /* AXDA coupling of z1 ~ eta H x and z2 ~ x      */
+    double kappa1, kappa2;   /* PSGLA step sizes of z1, z2                    */
+    double alpha, eps;       /* prior weight and denoiser noise level         */
+    double lambda;           /* Moreau-Yosida parameter of iota_[0,1]; <= 0: off */
+    double gamma;            /* x step size                                   */
+    uint64_t seed;           /* Philox key                                    */
+    const ora_net* net;      /* NULL: no denoiser term                        */
+    int noise;               /* 0: xi, zeta := 0                              */
+} ora_poisson;
+
+/* Normals of Philox stream `stream` (counter word 3): stream 0 drives xi,
+ * streams 1 and 2 drive zeta_1 and zeta_2; ora_normals is stream 0. */
+void ora_normals_stream(uint64_t seed, uint32_t t, uint32_t chain, uint32_t stream, int64_t n,
+                        double* xi);
+/* prox of kappa KL(y || .) at v, one pixel: the positive root of
+ * u^2 + (kappa - v) u - kappa y = 0. */
+double ora_kl_prox(double v, double y, double kappa);
+/* Step sizes of the Poisson setting (Sec. IV-B (ii)), c = 0.99 in the paper:
+ *   lambda = 0.99 / (4 ||eta H||^2 / rho1 + 4 / rho2 + 2 alpha L_eps / eps^2)
+ *   gamma  = c / (3 (alpha L_eps / eps^2 + ||eta H||^2 / rho1 + 1 / rho2 + 1 / lambda))
+ *   kappa_i = 0.99 rho_i */
+void ora_poisson_stepsizes(double hnorm, double eta, double rho1, double rho2, double alpha,
+                           double eps, double lip_eps, double c, double* lambda, double* gamma,
+                           double* kappa1, double* kappa2);
+/* One transition t -> t + 1: x by Eq. 13, then z by Eq. 14 from the new x. */
+void ora_poisson_step(const ora_poisson* p, const double* x, const double* z1, const double* z2,
+                      uint32_t t, uint32_t chain, double* xnew, double* z1new, double* z2new);
+
 #ifdef __cplusplus
 }
 #endif

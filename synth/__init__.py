@@ -227,6 +227,32 @@ def make_problem(ny, nx, h, bsnr_db, gt_seed, name="", blocks=(1, 1), halo=0, T=
                    blocks=blocks, halo=halo, T=T, burn_in=burn_in, name=name)
 
 
+@dataclass
+class PoissonProblem:
+    """One Poisson-noise deconvolution problem (inputs only): y ~ Poisson(eta H xbar)."""
+    xbar: np.ndarray           # ground truth [ny, nx] float64
+    y: np.ndarray              # photon counts [ny, nx] float64 (integers)
+    h: np.ndarray              # blur kernel  [kh, kw] float64 (float32-exact)
+    eta: float
+    seed: int                  # chain seed (Philox key)
+
+    @property
+    def shape(self):
+        return self.y.shape
+
+
+def make_poisson_problem(ny, nx, h, eta, gt_seed):
+    """Counts y ~ Poisson(eta H xbar) (seeded numpy PCG64) for the synthetic
+    ground truth; the paper uses eta = 250 with the Gaussian-case blur."""
+    xbar = ground_truth(ny, nx, gt_seed)
+    h = _f32(h)
+    h = _f32(h / h.sum())
+    hx = np.maximum(fft_circular_blur(xbar, h), 0.0)
+    rng = np.random.Generator(np.random.PCG64(gt_seed + 104729))
+    y = rng.poisson(eta * hx).astype(np.float64)
+    return PoissonProblem(xbar=xbar, y=y, h=h, eta=float(eta), seed=gt_seed)
+
+
 def gt_seed(config: int, job: int = 0) -> int:
     return 1000 + config * 100 + job
 
