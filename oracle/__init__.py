@@ -44,7 +44,7 @@ class _Problem(C.Structure):
                 ("h", C.POINTER(C.c_double)), ("kh", C.c_int), ("kw", C.c_int),
                 ("sigma", C.c_double), ("alpha", C.c_double), ("eps", C.c_double),
                 ("lam", C.c_double), ("gamma", C.c_double), ("seed", C.c_uint64),
-                ("net", C.POINTER(_Net)), ("noise", C.c_int)]
+                ("net", C.POINTER(_Net)), ("noise", C.c_int), ("mask", C.POINTER(C.c_double))]
 
 
 class _Poisson(C.Structure):
@@ -191,15 +191,18 @@ class Problem:
     """Holds the FP64 arrays alive for the C struct."""
 
     def __init__(self, y, h, sigma, alpha, eps, lam, gamma, seed, net: Net | None = None,
-                 noise=True):
+                 noise=True, mask=None):
+        """mask (0/1 array of y's shape): inpainting, H = diag(mask), h unused."""
         self.y = _f64(y)
-        self.h = _f64(h)
+        self.h = _f64(h if h is not None else np.ones((1, 1)))
+        self.mask = _f64(mask) if mask is not None else None
         self.net = net
         self.s = _Problem(self.y.shape[0], self.y.shape[1], _dp(self.y), _dp(self.h),
                           self.h.shape[0], self.h.shape[1], float(sigma), float(alpha),
                           float(eps), float(lam), float(gamma), C.c_uint64(seed),
                           C.pointer(net.s) if net is not None else C.POINTER(_Net)(),
-                          int(bool(noise)))
+                          int(bool(noise)),
+                          _dp(self.mask) if self.mask is not None else C.POINTER(C.c_double)())
 
     @property
     def shape(self):

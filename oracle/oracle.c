@@ -244,6 +244,8 @@ void ora_stepsizes(double hnorm, double sigma, double alpha, double eps, double 
 /* ---------------------------------------------------------------------------
  * One PnP-ULA transition (Eq. 8, x-update of Algorithm 1 with f2 = 0):
  *   x+ = x - gamma H^T (H x - y) / sigma^2
+ * (H the circular blur h, or for inpainting the diagonal selection mask,
+ * H = H^T = diag(mask), Sec. IV-A)
  *          + (alpha gamma / eps^2) (D(x) - x)
  *          + (gamma / lambda) (proj_[0,1](x) - x)
  *          + sqrt(2 gamma) xi,     xi = normals(seed, t, chain)
@@ -255,9 +257,14 @@ void ora_langevin_step(const ora_problem* p, const double* x, uint32_t t, uint32
     double* g = (double*)malloc(sizeof(double) * N);
     double* d = p->net ? (double*)malloc(sizeof(double) * N) : NULL;
     double* xi = (double*)calloc(N, sizeof(double));
-    ora_blur(x, p->ny, p->nx, p->h, p->kh, p->kw, r);
-    for (int64_t n = 0; n < N; ++n) r[n] -= p->y[n];
-    ora_blur_adj(r, p->ny, p->nx, p->h, p->kh, p->kw, g);
+    if (p->mask) {
+        for (int64_t n = 0; n < N; ++n) r[n] = p->mask[n] * x[n] - p->y[n];
+        for (int64_t n = 0; n < N; ++n) g[n] = p->mask[n] * r[n];
+    } else {
+        ora_blur(x, p->ny, p->nx, p->h, p->kh, p->kw, r);
+        for (int64_t n = 0; n < N; ++n) r[n] -= p->y[n];
+        ora_blur_adj(r, p->ny, p->nx, p->h, p->kh, p->kw, g);
+    }
     if (d) ora_denoise(x, p->ny, p->nx, p->net, d);
     if (p->noise) ora_normals(p->seed, t, chain, N, xi);
     const double gam = p->gamma;

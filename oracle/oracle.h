@@ -61,6 +61,8 @@ typedef struct {
     uint64_t seed;           /* Philox key                                    */
     const ora_net* net;      /* NULL: no denoiser term                        */
     int noise;               /* 0: xi := 0 (deterministic recursion)          */
+    const double* mask;      /* NULL: H is the blur h; else H = diag(mask),
+                                mask[n] in {0, 1} (inpainting, Sec. IV-A)     */
 } ora_problem;
 
 void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

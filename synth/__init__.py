@@ -253,6 +253,51 @@ def make_poisson_problem(ny, nx, h, eta, gt_seed):
     return PoissonProblem(xbar=xbar, y=y, h=h, eta=float(eta), seed=gt_seed)
 
 
+@dataclass
+class InpaintingProblem:
+    """One Gaussian-noise inpainting problem (inputs only): y = M (xbar + sigma w)."""
+    xbar: np.ndarray           # ground truth [ny, nx] float64
+    mask: np.ndarray           # 1 observed / 0 missing [ny, nx] float64
+    y: np.ndarray              # observation, 0 where missing [ny, nx] float64 (float32-exact)
+    sigma: float
+    x0: np.ndarray             # chain initialisation: spline interpolant of y (float32-exact)
+    seed: int                  # chain seed (Philox key)
+
+    @property
+    def shape(self):
+        return self.y.shape
+
+
+def spline_init(y, mask):
+    """Initial state for inpainting: the piecewise-cubic (Clough-Tocher) scattered-
+    data interpolant of the observed pixels (scipy.interpolate.griddata), nearest
+    observed value outside their convex hull. It is the chain's starting point,
+    an input to the sampler, not part of its transition."""
+    from scipy.interpolate import griddata
+    ny, nx = y.shape
+    pts = np.argwhere(mask > 0)
+    vals = y[mask > 0]
+    gi, gj = np.mgrid[0:ny, 0:nx]
+    x0 = griddata(pts, vals, (gi, gj), method="cubic")
+    bad = ~np.isfinite(x0)
+    if bad.any():
+        x0[bad] = griddata(pts, vals, (gi[bad], gj[bad]), method="nearest")
+    return x0
+
+
+def make_inpainting_problem(ny, nx, frac, snr_db, gt_seed):
+    """A random mask keeping a fraction `frac` of the pixels (the paper keeps
+    M = 0.3 N), noise level from the input SNR over the observed pixels:
+    SNR = 10 log10(var(xbar[observed]) / sigma^2) (15 dB in the paper)."""
+    xbar = ground_truth(ny, nx, gt_seed)
+    rng = np.random.Generator(np.random.PCG64(gt_seed + 7919))
+    mask = (rng.random((ny, nx)) < frac).astype(np.float64)
+    sigma = float(np.float32(math.sqrt(xbar[mask > 0].var() / 10 ** (snr_db / 10))))
+    y = _f32(mask * (xbar + sigma * rng.standard_normal((ny, nx))))
+    x0 = _f32(spline_init(y, mask))
+    return InpaintingProblem(xbar=xbar, mask=mask, y=y, sigma=sigma, x0=x0, seed=gt_seed)
+
+
 def gt_seed(config: int, job: int = 0) -> int:
     return 1000 + config * 100 + job
 
