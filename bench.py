@@ -10,8 +10,11 @@ headline value is the BF16 denoiser form, with the FP32 plain form and the
 MMSE PSNR of both reported beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload deconv1024|deconv8192|deconv128|batch48|serve]
+                       [--workload deconv1024|deconv8192|deconv128|poisson1024|batch48|serve]
                        [--no-quality] [--jobs M]
+poisson1024: the Poisson-noise sampler (Sec. IV-B: AXDA split, x-update with
+the coupling gradients, PSGLA updates of z1 and z2) on 1024 x 1024 counts at
+peak eta = 250, same blur and denoiser as deconv1024.
 Multi-GPU (torchrun): every rank runs an independent replica of the workload
 (independent chains, no data-path collective); value = all ranks' pixel-
 iterations / max time over ranks.
@@ -44,7 +47,16 @@ WORKLOADS = {
     "deconv128": 1,    # 128^2, Gaussian 7x7 s=1.5, 30 dB, K=4 F=16, 2x2 blocks
     "batch48": 4,      # 48 problems, sizes log-uniform 256..2048, blur/BSNR mix, BF16
     "serve": 5,        # Poisson arrivals (20/s), sizes {512..4096}^2, 200 + 800 iterations
+    "poisson1024": 2,  # Poisson counts, eta = 250, rho1 = 10, rho2 = 1e-3; blur/denoiser of deconv1024
 }
+POISSON = dict(eta=250.0, rho1=10.0, rho2=1e-3)
+
+
+def poisson_problem(rank=0):
+    """Counts y ~ Poisson(eta H xbar) on the deconv1024 image and blur."""
+    w = synth.WORKLOADS[2]
+    return synth.make_poisson_problem(w["ny"], w["nx"], synth.blur_from_spec(w["blur"]),
+                                      POISSON["eta"], synth.gt_seed(2, rank) + 50)
 
 
 def ncu_traffic(kernel, workload, precision):
@@ -159,8 +171,19 @@ def replica_rate(pix_iters, seconds, ws, device="cuda"):
     return tot / slow / 1e6, slow
 
 
-def _oracle_setup(cfg_id, crop):
+def _oracle_setup(cfg_id, crop, poisson=False):
     import oracle
+    if poisson:
+        prob = poisson_problem()
+        dw = synth.workload_denoiser(cfg_id)
+        crop = min(crop, prob.shape[0], prob.shape[1])
+        lam, gam, k1, k2 = oracle.poisson_stepsizes(float(np.abs(prob.h).sum()), prob.eta,
+                                                    POISSON["rho1"], POISSON["rho2"], 1.0, 0.05,
+                                                    dw.lipschitz)
+        op = oracle.PoissonProblem(prob.y[:crop, :crop], prob.h, prob.eta, POISSON["rho1"],
+                                   POISSON["rho2"], k1, k2, 1.0, 0.05, lam, gam, prob.seed,
+                                   net=oracle.Net.from_weights(dw))
+        return oracle, prob, op, crop
     if cfg_id == 4:
         prob = synth.batched_problems(1, seed=4000)[0]
     elif cfg_id == 5:
@@ -178,17 +201,34 @@ def _oracle_setup(cfg_id, crop):
     return oracle, prob, op, crop
 
 
-def oracle_baseline(cfg_id, budget_s=20.0, crop=128):
+class _OracleChain:
+    """One oracle iteration at a time on the crop: the Gaussian x-update, or
+    the Poisson x-update followed by the z-updates."""
+
+    def __init__(self, oracle, op, crop, poisson):
+        self.o, self.op, self.poisson = oracle, op, poisson
+        self.x = np.zeros((crop, crop))
+        self.z1 = np.zeros((crop, crop))
+        self.z2 = np.zeros((crop, crop))
+
+    def step(self, t):
+        if self.poisson:
+            self.x, self.z1, self.z2 = self.o.poisson_step(self.op, self.x, self.z1, self.z2, t)
+        else:
+            self.x = self.o.langevin_step(self.op, self.x, t)
+
+
+def oracle_baseline(cfg_id, budget_s=20.0, crop=128, poisson=False):
     """The FP64 oracle as it stands, on a bounded sample of the workload:
     whole iterations on a crop of the image (same blur, noise level and
     network), on this host's cores."""
-    oracle, prob, op, crop = _oracle_setup(cfg_id, crop)
+    oracle, prob, op, crop = _oracle_setup(cfg_id, crop, poisson)
     ny, nx = prob.shape
-    x = np.zeros((crop, crop))
+    ch = _OracleChain(oracle, op, crop, poisson)
     t0 = time.perf_counter()
     it = 0
     while True:
-        x = oracle.langevin_step(op, x, it)
+        ch.step(it)
         it += 1
         if time.perf_counter() - t0 > budget_s or it >= 64:
             break
@@ -210,13 +250,14 @@ def run_reference(args):
     steps = max(1, args.steps)
     n = args.warmup + steps
     crop = 128 if n <= 60 else (64 if n <= 250 else 32)
-    oracle, prob, op, crop = _oracle_setup(cfg_id, crop)
-    x = np.zeros((crop, crop))
+    poisson = args.workload == "poisson1024"
+    oracle, prob, op, crop = _oracle_setup(cfg_id, crop, poisson)
+    ch = _OracleChain(oracle, op, crop, poisson)
     for it in range(args.warmup):
-        x = oracle.langevin_step(op, x, it)
+        ch.step(it)
     t0 = time.perf_counter()
     for it in range(args.warmup, n):
-        x = oracle.langevin_step(op, x, it)
+        ch.step(it)
     dt = time.perf_counter() - t0
     val = crop * crop * steps / dt / 1e6
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
@@ -225,7 +266,8 @@ def run_reference(args):
     line = dict(metric=METRIC, value=val, unit=UNIT, n_gpus=args.gpus, steps=steps,
                 warmup=args.warmup, ms_per_step=1e3 * dt / steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload=f"{w['name']} (oracle, bounded crop sample)"),
+                config=dict(workload=f"{args.workload if poisson else w['name']} "
+                                     "(oracle, bounded crop sample)"),
                 cpu_baseline=dict(kind="oracle", cores=cores, sample=sample, value=val, unit=UNIT),
                 e2e=dict(value=val, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
@@ -456,7 +498,8 @@ def main():
 
     cfg_id = WORKLOADS[args.workload]
     w = synth.WORKLOADS[cfg_id]
-    prob = synth.workload_problem(cfg_id, job=rank)
+    poisson = args.workload == "poisson1024"
+    prob = poisson_problem(rank) if poisson else synth.workload_problem(cfg_id, job=rank)
     dw = synth.workload_denoiser(cfg_id)
     den = P.Denoiser.from_weights(dw)
     ny, nx = prob.shape
@@ -472,12 +515,18 @@ def main():
     def barrier():
         rank_barrier(ws)
 
+    def make_problem(prec, burn_in):
+        kw = dict(blocks=w["blocks"], halo=0, seed=prob.seed, burn_in=burn_in, precision=prec,
+                  stream=stream.cuda_stream)
+        if poisson:
+            return P.Problem(prob.y, prob.h, 0.0, den, noise_model="poisson", eta=prob.eta,
+                             rho1=POISSON["rho1"], rho2=POISSON["rho2"], **kw)
+        return P.Problem(prob.y, prob.h, prob.sigma, den, **kw)
+
     results = {}
     clocks = None
     for prec in precs:
-        gp = P.Problem(prob.y, prob.h, prob.sigma, den, blocks=w["blocks"], halo=0,
-                       seed=prob.seed, burn_in=w["burn_in"], precision=prec,
-                       stream=stream.cuda_stream)
+        gp = make_problem(prec, w["burn_in"])
         steps = args.steps if prec == precs[0] else min(args.steps, 200)
         gp.step(args.warmup)
         torch.cuda.synchronize()
@@ -504,7 +553,7 @@ def main():
         name = "conv_fp32" if prec == "fp32" else "conv_tc"
         kms, kn = P.pnp_kernel_timer_read(name)
         tot = {k: P.pnp_kernel_timer_read(k) for k in ("blur", "update", "conv_fp32", "conv_tc",
-                                                        "conv_edge", "conv_last")}
+                                                        "conv_edge", "conv_last", "zupdate")}
         P.pnp_kernel_timer(False)
         results[prec]["kernel"] = dict(name=name, avg_ms=kms / max(kn, 1), launches=kn,
                                        breakdown={k: v[0] for k, v in tot.items()},
@@ -518,8 +567,7 @@ def main():
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    gp = P.Problem(prob.y, prob.h, prob.sigma, den, blocks=w["blocks"], halo=0, seed=prob.seed,
-                   burn_in=0, precision=prec0, stream=stream.cuda_stream)
+    gp = make_problem(prec0, 0)
     gp.run_chain(args.steps, 0)
     mm, sd, _ = gp.moments()
     e2e_rate, t_e2e = replica_rate(npix * args.steps, time.perf_counter() - t0, ws)
@@ -530,7 +578,7 @@ def main():
 
     # quality at equal PSNR: the full chain of the workload for each precision
     quality = None
-    if not args.no_quality and rank == 0 and cfg_id != 3:
+    if not args.no_quality and rank == 0 and cfg_id != 3 and not poisson:
         quality = {}
         for prec in precs:
             gq = P.Problem(prob.y, prob.h, prob.sigma, den, blocks=w["blocks"], halo=0,
@@ -574,9 +622,10 @@ def main():
                     kernel="k_conv3x3<64,64>", peak_kind="FP32 FFMA: 148 SM x 128 lanes x 2 x max clock")
     # stencils against HBM: algorithmic bytes per pixel = r = Hx - y: read x, y,
     # write r (12 B); update while sampling: read r, x, d, mean, m2, write x,
-    # mean, m2 (32 B)
+    # mean, m2 (32 B; Poisson also reads z2: 36 B); Poisson z-update: read x,
+    # z1, z2, y, write z1, z2 (24 B)
     stencils = {}
-    for kname, bpp in (("blur", 12), ("update", 32)):
+    for kname, bpp in (("blur", 12), ("update", 36 if poisson else 32), ("zupdate", 24)):
         n = kern["counts"].get(kname, 0)
         if n:
             avg = kern["breakdown"][kname] / n
@@ -593,7 +642,7 @@ def main():
     cpu = None
     if not args.no_cpu_baseline:
         try:
-            cpu = oracle_baseline(cfg_id, budget_s=15.0)
+            cpu = oracle_baseline(cfg_id, budget_s=15.0, poisson=poisson)
         except Exception as ex:  # report, never fake
             cpu = dict(value=None, unit=UNIT, cores=None, kind="oracle", sample=f"failed: {ex}")
     line = dict(
@@ -601,8 +650,12 @@ def main():
         warmup=args.warmup, ms_per_step=round(head["ms"] / args.steps, 4), higher_is_better=True,
         scaling="weak", vs_baseline=None, dtype=("bf16" if precs[0] == "bf16" else "f32"),
         data="synthetic",
-        config=dict(workload=f"{w['name']}: {ny}x{nx} grayscale, blur {w['blur'][0]} "
-                             f"{w['blur'][1]}x{w['blur'][1]}, {w['bsnr']} dB BSNR, DnCNN-form "
+        config=dict(workload=(f"poisson1024: {ny}x{nx} Poisson counts, peak eta={prob.eta:g}, "
+                              f"rho1={POISSON['rho1']:g}, rho2={POISSON['rho2']:g}, AXDA + PSGLA, "
+                              if poisson else
+                              f"{w['name']}: {ny}x{nx} grayscale, {w['bsnr']} dB BSNR, ")
+                             + f"blur {w['blur'][0]} "
+                             f"{w['blur'][1]}x{w['blur'][1]}, DnCNN-form "
                              f"K={K} F={F}, {w['blocks'][0]}x{w['blocks'][1]} blocks "
                              f"(halo-exchange-free), 1 chain per GPU",
                     precision=precs[0], l2="working set per step > 126 MB L2 (activation planes)",

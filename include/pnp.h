@@ -11,6 +11,14 @@
  * evaluated block-wise (Defs. 1-2), xi drawn from a counter-based Philox stream,
  * and MMSE / pixel-wise variance accumulated online after burn-in (Sec. III-C).
  *
+ * Poisson observations (Sec. IV-B) use the asymptotically exact data
+ * augmentation of Sec. III-A with two auxiliary variables, z1 (coupled to
+ * eta H x with tolerance rho1) and z2 (coupled to x with tolerance rho2); each
+ * iteration runs the x-update with the coupling gradients in place of the
+ * Gaussian data term, then one proximal Langevin (PSGLA) step per auxiliary
+ * variable: z1 through the proximal map of the Poisson negative log-likelihood,
+ * z2 through the projection onto the non-negative orthant.
+ *
  * Conventions for every entry point:
  *  - Return value is a pnp_status; PNP_OK on success. On failure nothing is
  *    left half-done on the host side and pnp_last_error() returns a
@@ -52,6 +60,11 @@ typedef enum {
     PNP_BF16 = 1,      /* BF16 operands, FP32 accumulation, tcgen05 tensor cores          */
     PNP_FP8 = 2        /* E4M3 operands with per-output-channel scales, FP32 accumulation */
 } pnp_precision;
+
+typedef enum {
+    PNP_GAUSSIAN = 0,  /* y = H x + sigma n, n ~ N(0, I): the x-update of Eq. 8                 */
+    PNP_POISSON = 1    /* y ~ Poisson(eta H x): AXDA split with z1 ~ eta H x, z2 ~ x (Sec. IV-B) */
+} pnp_noise_model;
 
 typedef struct pnp_denoiser pnp_denoiser;
 typedef struct pnp_problem pnp_problem;
@@ -157,6 +170,16 @@ pnp_status pnp_langevin_update(float* x, const float* r, const float* d, const f
                                uint64_t seed, uint32_t t, int noise, float* mean, float* m2,
                                int64_t n_kept, void* stream);
 
+/* Inpainting x-update (Eq. 8 with H = diag(mask), Sec. IV-A) for nchain
+ * chains: g = x - y at observed pixels and 0 at missing ones, then the same
+ * update, noise and Welford accumulation as pnp_langevin_update. y_obs:
+ * device [ny][nx] shared by the chains, NaN at missing pixels (the mask is
+ * read from it). x, d, mean, m2: device [nchain][ny][nx]. No stencil. */
+pnp_status pnp_inpaint_update(float* x, const float* y_obs, const float* d, int ny, int nx,
+                              int nchain, double sigma, double alpha, double eps, double lambda,
+                              double gamma, uint64_t seed, uint32_t t, int noise, float* mean,
+                              float* m2, int64_t n_kept, void* stream);
+
 /* Final FP64 moments (Sec. III-C footnote): mmse = mean, var = m2 / (n - 1),
  * out2 = var (want_var != 0) or sqrt(var). mean, m2: device FP32 [n];
  * mmse, out2: device FP64 [n]. */
@@ -169,6 +192,15 @@ pnp_status pnp_finalize_moments(const float* mean, const float* m2, int64_t npix
  * gamma = c / (3 (L + alpha L_eps / eps^2 + 1/lambda)), 0 < c < 1. */
 pnp_status pnp_stepsizes(double hnorm, double sigma, double alpha, double eps, double lip_eps,
                          double c, double* lambda, double* gamma);
+
+/* Step sizes of the Poisson setting (Eq. 12 with f1 = 0 and the AXDA
+ * couplings as the smooth term: ||H_2||^2 = eta^2 hnorm^2 / rho1 + 1 / rho2):
+ * lambda = 0.99 / (4 ||H_2||^2 + 2 alpha L_eps / eps^2),
+ * gamma = c / (3 (alpha L_eps / eps^2 + ||H_2||^2 + 1/lambda)),
+ * kappa_i = 0.99 rho_i (the PSGLA step of each auxiliary variable). */
+pnp_status pnp_stepsizes_poisson(double hnorm, double eta, double rho1, double rho2, double alpha,
+                                 double eps, double lip_eps, double c, double* lambda,
+                                 double* gamma, double* kappa1, double* kappa2);
 
 /* ------------------------------------------------------------------------
  * Problem: one posterior (Eq. 2 with the Gaussian-deconvolution likelihood)
@@ -194,6 +226,17 @@ typedef struct {
     const pnp_denoiser* D;      /* NULL: no prior term                                      */
     const float* x0;            /* host [nchain][ny*nx] or NULL (zeros)                     */
     void* stream;               /* stream for all work of this problem (NULL: own stream)  */
+    /* Poisson model (noise_model = PNP_POISSON; sigma is then ignored, eps <= 0 -> 0.05):
+     * y holds counts (>= 0); eta, rho1, rho2 > 0; kappa_i <= 0 -> 0.99 rho_i, else in
+     * (0, rho_i). z1, z2 start at zero. Zero-initialised descriptors are Gaussian.     */
+    pnp_noise_model noise_model;
+    double eta, rho1, rho2;
+    double kappa1, kappa2;
+    /* Inpainting (Sec. IV-A): host [ny*nx], 1 = observed, 0 = missing; copied. H is
+     * then diag(mask) (h, kh, kw ignored; hnorm <= 0 -> 1), y is read only where
+     * mask = 1, noise_model must be PNP_GAUSSIAN, and x0 is the caller's
+     * initialisation (the paper interpolates y). NULL: H is the blur h.            */
+    const float* mask;
 } pnp_problem_desc;
 
 pnp_status pnp_create_problem(const pnp_problem_desc* desc, pnp_problem** out);
@@ -215,6 +258,10 @@ pnp_status pnp_get_moments(pnp_problem* p, int chain, double* mmse, double* std_
 /* Chain state: x host [nchain][ny*nx], t = iterations done. Synchronous. */
 pnp_status pnp_get_state(pnp_problem* p, float* x, int64_t* t);
 pnp_status pnp_set_state(pnp_problem* p, const float* x, int64_t t);
+/* Auxiliary variables of a Poisson problem, host [nchain][ny*nx] each (either
+ * may be NULL). PNP_EINVAL for a Gaussian problem. Synchronous. */
+pnp_status pnp_get_aux_state(pnp_problem* p, float* z1, float* z2);
+pnp_status pnp_set_aux_state(pnp_problem* p, const float* z1, const float* z2);
 /* Device pointer of the chain state x [nchain][ny][nx] (valid until destroy). */
 float* pnp_problem_x_device(pnp_problem* p);
 /* Replay captured CUDA graphs (one of 8 iterations, plus a one-iteration graph
@@ -304,7 +351,8 @@ void pnp_server_destroy(pnp_server* s);
 /* ------------------------------------------------------------------------
  * Instrumentation: CUDA events around every launch of the hot kernels
  * ("blur", "update", "conv_fp32", "conv_tc", "conv_edge" = first layer and the
- * FP32 last layer, "conv_last" = tensor-core last layer). Enabling resets
+ * FP32 last layer, "conv_last" = tensor-core last layer, "zupdate" = the
+ * auxiliary-variable update of the Poisson model). Enabling resets
  * the counters and forces eager launches (no graph replay). Reading
  * synchronizes the device and returns the summed device time and launches.
  * ------------------------------------------------------------------------ */

@@ -12,7 +12,8 @@ import ctypes as C
 
 import numpy as np
 
-from ._lib import (PNP_BF16, PNP_FP8, PNP_FP32, PnpError, ProblemDesc, check, load)  # noqa: F401
+from ._lib import (PNP_BF16, PNP_FP8, PNP_FP32, PNP_GAUSSIAN, PNP_POISSON, PnpError,  # noqa: F401
+                   ProblemDesc, check, load)
 
 __all__ = ["Denoiser", "Problem", "Batch", "Server", "PnpError", "load", "version"]
 
@@ -73,6 +74,16 @@ def pnp_langevin_update(x, r, d, h, sigma, alpha, eps, lam, gamma, seed, t, nois
     return x
 
 
+def pnp_inpaint_update(x, y_obs, d, sigma, alpha, eps, lam, gamma, seed, t, noise=True,
+                       mean=None, m2=None, n_kept=0, stream=None):
+    """Inpainting x-update; y_obs holds NaN at missing pixels."""
+    n, ny, nx = x.shape
+    check(load().pnp_inpaint_update(_ptr(x), _ptr(y_obs), _ptr(d), ny, nx, n, sigma, alpha, eps,
+                                    lam, gamma, int(seed), int(t), int(bool(noise)), _ptr(mean),
+                                    _ptr(m2), int(n_kept), _stream(stream)))
+    return x
+
+
 def pnp_finalize_moments(mean, m2, n_kept, mmse, out2, want_var=False, stream=None):
     check(load().pnp_finalize_moments(_ptr(mean), _ptr(m2), mean.numel(), int(n_kept),
                                       int(bool(want_var)), _ptr(mmse), _ptr(out2),
@@ -84,6 +95,15 @@ def pnp_stepsizes(hnorm, sigma, alpha, eps, lip_eps, c=0.99):
     lam, gam = C.c_double(), C.c_double()
     check(load().pnp_stepsizes(hnorm, sigma, alpha, eps, lip_eps, c, C.byref(lam), C.byref(gam)))
     return lam.value, gam.value
+
+
+def pnp_stepsizes_poisson(hnorm, eta, rho1, rho2, alpha, eps, lip_eps, c=0.99):
+    """(lambda, gamma, kappa1, kappa2) of the Poisson setting."""
+    out = [C.c_double() for _ in range(4)]
+    check(load().pnp_stepsizes_poisson(float(hnorm), float(eta), float(rho1), float(rho2),
+                                       float(alpha), float(eps), float(lip_eps), float(c),
+                                       *[C.byref(o) for o in out]))
+    return tuple(o.value for o in out)
 
 
 def pnp_set_graph_mode(enable: bool):
@@ -174,10 +194,12 @@ class Denoiser:
 
 def make_desc(y, h, sigma, denoiser=None, *, alpha=-1.0, eps=0.0, lam=0.0, gamma=0.0,
               step_c=0.0, hnorm=0.0, blocks=(1, 1), halo=0, nchain=1, seed=0, burn_in=0,
-              precision="fp32", x0=None, stream=None):
-    """Fill a pnp_problem_desc; returns (desc, keep-alive host arrays)."""
+              precision="fp32", x0=None, stream=None, noise_model="gaussian", eta=0.0,
+              rho1=0.0, rho2=0.0, kappa1=0.0, kappa2=0.0, mask=None):
+    """Fill a pnp_problem_desc; returns (desc, keep-alive host arrays). With
+    noise_model="poisson" y holds counts and sigma is ignored (pass 0)."""
     y = np.ascontiguousarray(y, dtype=np.float32)
-    h = np.ascontiguousarray(h, dtype=np.float32)
+    h = np.ascontiguousarray(h if h is not None else np.ones((1, 1)), dtype=np.float32)
     d = ProblemDesc()
     d.ny, d.nx = y.shape
     d.y = _f32p(y)
@@ -195,6 +217,17 @@ def make_desc(y, h, sigma, denoiser=None, *, alpha=-1.0, eps=0.0, lam=0.0, gamma
         d.x0 = _f32p(x0a)
         keep.append(x0a)
     d.stream = C.c_void_p(int(stream)) if stream is not None else None
+    if noise_model not in ("gaussian", "poisson"):
+        raise ValueError(f"unknown noise model {noise_model!r}")
+    d.noise_model = PNP_POISSON if noise_model == "poisson" else PNP_GAUSSIAN
+    d.eta, d.rho1, d.rho2 = float(eta), float(rho1), float(rho2)
+    d.kappa1, d.kappa2 = float(kappa1), float(kappa2)
+    if mask is not None:
+        m = np.ascontiguousarray(mask, dtype=np.float32)
+        if m.shape != y.shape:
+            raise ValueError("mask must have the shape of y")
+        d.mask = _f32p(m)
+        keep.append(m)
     return d, keep
 
 
@@ -261,6 +294,19 @@ class Problem:
     def set_state(self, x, t):
         x = np.ascontiguousarray(np.broadcast_to(x, (self.nchain,) + self.shape), dtype=np.float32)
         check(load().pnp_set_state(self.handle, _f32p(x), int(t)))
+
+    def aux_state(self):
+        """(z1, z2) of a Poisson problem, each [nchain][ny][nx] FP32."""
+        z1 = np.empty((self.nchain,) + self.shape, np.float32)
+        z2 = np.empty_like(z1)
+        check(load().pnp_get_aux_state(self.handle, _f32p(z1), _f32p(z2)))
+        return z1, z2
+
+    def set_aux_state(self, z1, z2):
+        sh = (self.nchain,) + self.shape
+        z1 = np.ascontiguousarray(np.broadcast_to(z1, sh), dtype=np.float32)
+        z2 = np.ascontiguousarray(np.broadcast_to(z2, sh), dtype=np.float32)
+        check(load().pnp_set_aux_state(self.handle, _f32p(z1), _f32p(z2)))
 
     def x_device_ptr(self):
         return load().pnp_problem_x_device(self.handle)

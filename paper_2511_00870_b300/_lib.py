@@ -11,6 +11,7 @@ PNP_OK, PNP_EINVAL, PNP_ENOMEM, PNP_EBUSY, PNP_ECUDA, PNP_ETIMEOUT, PNP_ESTATE, 
 STATUS_NAMES = ["PNP_OK", "PNP_EINVAL", "PNP_ENOMEM", "PNP_EBUSY", "PNP_ECUDA", "PNP_ETIMEOUT",
                 "PNP_ESTATE", "PNP_ENOTSUP"]
 PNP_FP32, PNP_BF16, PNP_FP8 = 0, 1, 2
+PNP_GAUSSIAN, PNP_POISSON = 0, 1
 
 
 class PnpError(RuntimeError):
@@ -32,6 +33,10 @@ class ProblemDesc(C.Structure):
         ("D", C.c_void_p),
         ("x0", C.POINTER(C.c_float)),
         ("stream", C.c_void_p),
+        ("noise_model", C.c_int),
+        ("eta", C.c_double), ("rho1", C.c_double), ("rho2", C.c_double),
+        ("kappa1", C.c_double), ("kappa2", C.c_double),
+        ("mask", C.POINTER(C.c_float)),
     ]
 
 
@@ -54,8 +59,11 @@ SIGNATURES = {
     "pnp_denoise_noalloc": ([vp, i32, vp, i32, i32, i32, vp, vp], i32),
     "pnp_langevin_update": ([vp, vp, vp, vp, i32, i32, i32, i32, i32, f64, f64, f64, f64, f64,
                              u64, u32, i32, vp, vp, i64, vp], i32),
+    "pnp_inpaint_update": ([vp, vp, vp, i32, i32, i32, f64, f64, f64, f64, f64, u64, u32, i32,
+                            vp, vp, i64, vp], i32),
     "pnp_finalize_moments": ([vp, vp, i64, i64, i32, vp, vp, vp], i32),
     "pnp_stepsizes": ([f64, f64, f64, f64, f64, f64, dp, dp], i32),
+    "pnp_stepsizes_poisson": ([f64, f64, f64, f64, f64, f64, f64, f64, dp, dp, dp, dp], i32),
     "pnp_create_problem": ([C.POINTER(ProblemDesc), C.POINTER(vp)], i32),
     "pnp_destroy_problem": ([vp], None),
     "pnp_problem_params": ([vp, dp, dp, dp, dp], i32),
@@ -65,6 +73,8 @@ SIGNATURES = {
     "pnp_get_moments": ([vp, i32, dp, dp, C.POINTER(i64), i32], i32),
     "pnp_get_state": ([vp, fp, C.POINTER(i64)], i32),
     "pnp_set_state": ([vp, fp, i64], i32),
+    "pnp_get_aux_state": ([vp, fp, fp], i32),
+    "pnp_set_aux_state": ([vp, fp, fp], i32),
     "pnp_problem_x_device": ([vp], vp),
     "pnp_set_graph_mode": ([i32], i32),
     "pnp_set_pdl": ([i32], i32),

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -47,7 +48,8 @@ static TimerSlot g_timers[T_COUNT];
 static bool g_timing = false;
 static bool g_pdl = true;
 bool pdl_enabled() { return g_pdl; }
-static const char* g_timer_names[T_COUNT] = {"blur", "update", "conv_fp32", "conv_tc", "conv_edge", "conv_last"};
+static const char* g_timer_names[T_COUNT] = {"blur", "update", "conv_fp32", "conv_tc", "conv_edge", "conv_last",
+                                              "zupdate"};
 
 bool timer_enabled() { return g_timing; }
 void timer_begin(int id, cudaStream_t s) {
@@ -137,6 +139,24 @@ extern "C" pnp_status pnp_stepsizes(double hnorm, double sigma, double alpha, do
     const double lam = 0.99 / (4.0 * L + 2.0 * prior);
     *lambda = lam;
     *gamma = c / (3.0 * (L + prior + 1.0 / lam));
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_stepsizes_poisson(double hnorm, double eta, double rho1, double rho2,
+                                            double alpha, double eps, double lip_eps, double c,
+                                            double* lambda, double* gamma, double* kappa1,
+                                            double* kappa2) {
+    if (!(hnorm > 0) || !(eta > 0) || !(rho1 > 0) || !(rho2 > 0) || !(eps > 0) || alpha < 0 ||
+        lip_eps < 0 || !(c > 0) || !(c < 1) || !lambda || !gamma || !kappa1 || !kappa2)
+        return fail(PNP_EINVAL, "pnp_stepsizes_poisson: need hnorm, eta, rho1, rho2, eps > 0, "
+                                "alpha, L_eps >= 0, 0 < c < 1");
+    const double c1 = eta * hnorm * eta * hnorm / rho1, c2 = 1.0 / rho2;
+    const double prior = alpha * lip_eps / (eps * eps);
+    const double lam = 0.99 / (4.0 * c1 + 4.0 * c2 + 2.0 * prior);
+    *lambda = lam;
+    *gamma = c / (3.0 * (prior + c1 + c2 + 1.0 / lam));
+    *kappa1 = 0.99 * rho1;
+    *kappa2 = 0.99 * rho2;
     return PNP_OK;
 }
 
@@ -526,6 +546,8 @@ static pnp_status fill_update_params(UpdateParams& u, float* x, const float* r, 
     u.arrive = nullptr;
     u.tile = -1;
     u.hsep = nullptr;
+    u.z2 = nullptr;
+    u.c_z2 = 0.f;
     return PNP_OK;
 }
 
@@ -544,6 +566,25 @@ extern "C" pnp_status pnp_langevin_update(float* x, const float* r, const float*
     u.m2 = m2;
     u.inv_n = n_kept > 0 ? (float)(1.0 / (double)n_kept) : 0.f;
     PNP_CUDA_TRY(launch_langevin_update(u, (cudaStream_t)stream));
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_inpaint_update(float* x, const float* y_obs, const float* d, int ny,
+                                         int nx, int nchain, double sigma, double alpha,
+                                         double eps, double lambda, double gamma, uint64_t seed,
+                                         uint32_t t, int noise, float* mean, float* m2,
+                                         int64_t n_kept, void* stream) {
+    if (!x || !y_obs || ny < 1 || nx < 1 || nchain < 1)
+        return fail(PNP_EINVAL, "pnp_inpaint_update: need x, y_obs and positive sizes");
+    if (n_kept > 0 && (!mean || !m2)) return fail(PNP_EINVAL, "moments requested without buffers");
+    UpdateParams u;
+    PNP_TRY(fill_update_params(u, x, y_obs, d, nullptr, 1, 1, ny, nx, nchain, sigma, alpha, eps,
+                               lambda, gamma, seed, noise));
+    u.t = t;
+    u.mean = mean;
+    u.m2 = m2;
+    u.inv_n = n_kept > 0 ? (float)(1.0 / (double)n_kept) : 0.f;
+    PNP_CUDA_TRY(launch_update_mask(u, (cudaStream_t)stream));
     return PNP_OK;
 }
 
@@ -567,7 +608,7 @@ extern "C" void pnp_destroy_problem(pnp_problem* p) {
     for (void* q : {(void*)p->y, (void*)p->h, (void*)p->x, (void*)p->r, (void*)p->d,
                     (void*)p->mean, (void*)p->m2, (void*)p->blocks, (void*)p->tiles,
                     (void*)p->dtiles, (void*)p->rects, p->scratch, (void*)p->st,
-                    (void*)p->hsep})
+                    (void*)p->hsep, (void*)p->z1, (void*)p->z2})
         dfree(q);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
     delete p;
@@ -576,8 +617,15 @@ extern "C" void pnp_destroy_problem(pnp_problem* p) {
 namespace pnp {
 
 pnp_status problem_pre(pnp_problem* p, cudaStream_t s) {
-    PNP_CUDA_TRY(launch_blur(p->x, p->y, p->h, p->kh, p->kw, p->ny, p->nx, p->nchain, p->r, s,
-                             p->blur_tile, p->hsep));
+    if (p->inpaint) return PNP_OK;   // H = diag(mask): the update forms x - y itself
+    if (p->poisson) {
+        // r = eta H x - z1 (per chain)
+        PNP_CUDA_TRY(launch_blur(p->x, p->z1, p->h, p->kh, p->kw, p->ny, p->nx, p->nchain, p->r, s,
+                                 p->blur_tile, p->hsep, (float)p->eta, p->N));
+    } else {
+        PNP_CUDA_TRY(launch_blur(p->x, p->y, p->h, p->kh, p->kw, p->ny, p->nx, p->nchain, p->r, s,
+                                 p->blur_tile, p->hsep));
+    }
     return PNP_OK;
 }
 
@@ -585,8 +633,11 @@ pnp_status problem_pre(pnp_problem* p, cudaStream_t s) {
 // step counter from the device and its last block advances it.
 static pnp_status problem_update_params(const pnp_problem* p, UpdateParams& u) {
     const bool prior = p->D && p->alpha != 0.0;
-    PNP_TRY(fill_update_params(u, p->x, p->r, prior ? p->d : nullptr, p->h, p->kh, p->kw, p->ny,
-                               p->nx, p->nchain, p->sigma, p->alpha, p->eps, p->lambda, p->gamma,
+    // Poisson: the H^T r coefficient eta / rho1 takes the place of 1 / sigma^2
+    const double sig = p->poisson ? std::sqrt(p->rho1 / p->eta) : p->sigma;
+    PNP_TRY(fill_update_params(u, p->x, p->inpaint ? p->y : p->r, prior ? p->d : nullptr, p->h,
+                               p->kh, p->kw, p->ny,
+                               p->nx, p->nchain, sig, p->alpha, p->eps, p->lambda, p->gamma,
                                p->seed, 1));
     u.t_dev = &p->st->t;
     u.burn_dev = &p->st->burn_in;
@@ -596,13 +647,50 @@ static pnp_status problem_update_params(const pnp_problem* p, UpdateParams& u) {
     u.d_residual = p->prec != PNP_FP32;   // the tensor-core denoisers hand over G = x - D(x)
     u.tile = p->update_tile;
     u.hsep = p->hsep;
+    if (p->poisson) {
+        u.inv_s2 = (float)(p->eta / p->rho1);
+        u.z2 = p->z2;
+        u.c_z2 = (float)(p->gamma / p->rho2);
+        u.arrive = nullptr;   // the z-update, the iteration's last kernel, advances t
+    }
     return PNP_OK;
+}
+
+static ZParams problem_z_params(const pnp_problem* p) {
+    ZParams z;
+    z.x = p->x;
+    z.z1 = p->z1;
+    z.z2 = p->z2;
+    z.y = p->y;
+    z.h = p->h;
+    z.hsep = p->hsep;
+    z.kh = p->kh;
+    z.kw = p->kw;
+    z.ny = p->ny;
+    z.nx = p->nx;
+    z.nchain = p->nchain;
+    z.eta = (float)p->eta;
+    z.a1 = (float)(p->kappa1 / p->rho1);
+    z.a2 = (float)(p->kappa2 / p->rho2);
+    z.s1 = (float)std::sqrt(2.0 * p->kappa1);
+    z.s2 = (float)std::sqrt(2.0 * p->kappa2);
+    z.kappa1 = (float)p->kappa1;
+    z.noise = 1;
+    z.key0 = (uint32_t)(p->seed & 0xffffffffu);
+    z.key1 = (uint32_t)(p->seed >> 32);
+    z.t = 0;
+    z.t_dev = &p->st->t;
+    z.arrive = &p->st->arrive;
+    z.tile = p->update_tile;
+    return z;
 }
 
 pnp_status problem_post(pnp_problem* p, cudaStream_t s) {
     UpdateParams u;
     PNP_TRY(problem_update_params(p, u));
-    PNP_CUDA_TRY(launch_langevin_update(u, s));
+    if (p->inpaint) PNP_CUDA_TRY(launch_update_mask(u, s));
+    else PNP_CUDA_TRY(launch_langevin_update(u, s));
+    if (p->poisson) PNP_CUDA_TRY(launch_zupdate(problem_z_params(p), s));
     return PNP_OK;
 }
 
@@ -686,10 +774,30 @@ static bool separable_taps(const float* h, int kh, int kw, std::vector<float>& o
 extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_problem** out) {
     if (!dsc || !out) return fail(PNP_EINVAL, "pnp_create_problem: NULL argument");
     *out = nullptr;
-    const pnp_problem_desc& q = *dsc;
+    pnp_problem_desc q = *dsc;
+    const bool inpaint = q.mask != nullptr;
+    static const float unit_tap = 1.0f;
+    if (inpaint) {
+        // H = diag(mask): h is not used; a 1 x 1 unit tap keeps the blur fields valid
+        q.h = &unit_tap;
+        q.kh = q.kw = 1;
+        if (!(q.hnorm > 0)) q.hnorm = 1.0;
+        if (q.noise_model != PNP_GAUSSIAN)
+            return fail(PNP_EINVAL, "inpainting takes the Gaussian noise model");
+    }
     if (q.ny < 1 || q.nx < 1 || !q.y || !q.h) return fail(PNP_EINVAL, "need ny, nx >= 1, y and h");
     PNP_TRY(check_blur_args(q.y, q.h, q.kh, q.kw, q.ny, q.nx, 1, q.y, "pnp_create_problem"));
-    if (!(q.sigma > 0) || !std::isfinite(q.sigma)) return fail(PNP_EINVAL, "sigma must be > 0");
+    const bool poisson = q.noise_model == PNP_POISSON;
+    if (q.noise_model != PNP_GAUSSIAN && !poisson) return fail(PNP_EINVAL, "unknown noise model");
+    if (!poisson && (!(q.sigma > 0) || !std::isfinite(q.sigma)))
+        return fail(PNP_EINVAL, "sigma must be > 0");
+    if (poisson) {
+        if (!(q.eta > 0) || !(q.rho1 > 0) || !(q.rho2 > 0) || !std::isfinite(q.eta) ||
+            !std::isfinite(q.rho1) || !std::isfinite(q.rho2))
+            return fail(PNP_EINVAL, "Poisson model: need eta, rho1, rho2 > 0");
+        if ((q.kappa1 > 0 && !(q.kappa1 < q.rho1)) || (q.kappa2 > 0 && !(q.kappa2 < q.rho2)))
+            return fail(PNP_EINVAL, "Poisson model: need kappa_i in (0, rho_i)");
+    }
     if (q.nchain < 1) return fail(PNP_EINVAL, "nchain must be >= 1");
     if (q.blocks_y < 1 || q.blocks_x < 1 || q.blocks_y > q.ny || q.blocks_x > q.nx)
         return fail(PNP_EINVAL, "blocks must be in [1, image size]");
@@ -701,8 +809,13 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
     if (q.D && q.precision != PNP_FP32 && q.D->dev.F != 64)
         return fail(PNP_EINVAL, "BF16/FP8 denoiser needs F = 64");
     const int64_t N = (int64_t)q.ny * q.nx;
-    for (int64_t i = 0; i < N; ++i)
+    for (int64_t i = 0; i < N; ++i) {
+        if (inpaint && q.mask[i] != 0.f && q.mask[i] != 1.f)
+            return fail(PNP_EINVAL, "mask entries must be 0 or 1");
+        if (inpaint && q.mask[i] == 0.f) continue;   // y is not read at missing pixels
         if (!std::isfinite(q.y[i])) return fail(PNP_EINVAL, "y contains NaN or Inf");
+        if (poisson && q.y[i] < 0) return fail(PNP_EINVAL, "Poisson counts y must be >= 0");
+    }
     double hsum = 0.0;
     for (int i = 0; i < q.kh * q.kw; ++i) {
         if (!std::isfinite(q.h[i])) return fail(PNP_EINVAL, "h contains NaN or Inf");
@@ -716,9 +829,19 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
     p->nchain = q.nchain;
     p->kh = q.kh;
     p->kw = q.kw;
-    p->sigma = q.sigma;
+    p->sigma = poisson ? 0.0 : q.sigma;
+    p->poisson = poisson;
+    p->inpaint = inpaint;
+    if (poisson) {
+        p->eta = q.eta;
+        p->rho1 = q.rho1;
+        p->rho2 = q.rho2;
+        p->kappa1 = q.kappa1 > 0 ? q.kappa1 : 0.99 * q.rho1;
+        p->kappa2 = q.kappa2 > 0 ? q.kappa2 : 0.99 * q.rho2;
+    }
     p->alpha = q.alpha < 0 ? 1.0 : q.alpha;
-    p->eps = q.eps > 0 ? q.eps : q.sigma;
+    // the paper's Poisson setting takes eps = 0.05; the Gaussian one eps = sigma
+    p->eps = q.eps > 0 ? q.eps : (poisson ? 0.05 : q.sigma);
     p->hnorm = q.hnorm > 0 ? q.hnorm : hsum;
     p->seed = q.seed;
     p->burn_in = q.burn_in;
@@ -731,9 +854,12 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
     const double alpha_eff = q.D ? p->alpha : 0.0;
     double lam = q.lambda, gam = q.gamma;
     if (!(lam > 0) || !(gam > 0)) {
-        double l2, g2;
-        pnp_status st = pnp_stepsizes(p->hnorm, p->sigma, alpha_eff, p->eps, lip,
-                                      q.step_c > 0 ? q.step_c : 0.99, &l2, &g2);
+        double l2, g2, k1, k2;
+        pnp_status st = poisson
+            ? pnp_stepsizes_poisson(p->hnorm, p->eta, p->rho1, p->rho2, alpha_eff, p->eps, lip,
+                                    q.step_c > 0 ? q.step_c : 0.99, &l2, &g2, &k1, &k2)
+            : pnp_stepsizes(p->hnorm, p->sigma, alpha_eff, p->eps, lip,
+                            q.step_c > 0 ? q.step_c : 0.99, &l2, &g2);
         if (st != PNP_OK) {
             delete p;
             return st;
@@ -743,11 +869,15 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
     }
     p->lambda = lam;
     p->gamma = gam;
-    // Eq. 10 (with H_2 = 0) must hold for the parameters actually used
+    // Eq. 12 must hold for the parameters actually used: Gaussian L = ||H||^2 /
+    // sigma^2 and H_2 = 0; Poisson f1 = 0 and ||H_2||^2 = ||eta H||^2 / rho1 + 1 / rho2
     {
-        const double L = p->hnorm * p->hnorm / (p->sigma * p->sigma);
+        const double L = poisson ? 0.0 : p->hnorm * p->hnorm / (p->sigma * p->sigma);
+        const double h2 = poisson ? p->eta * p->hnorm * p->eta * p->hnorm / p->rho1 + 1.0 / p->rho2
+                                  : 0.0;
         const double prior = alpha_eff * lip / (p->eps * p->eps);
-        if (!(3.0 * gam * (L + 1.0 / lam + prior) < 1.0) || !(2.0 * L + prior <= 0.5 / lam * (1 + 1e-12))) {
+        if (!(3.0 * gam * (L + h2 + 1.0 / lam + prior) < 1.0) ||
+            !(2.0 * (L + h2) + prior <= 0.5 / lam * (1 + 1e-12))) {
             delete p;
             return fail(PNP_EINVAL, "step sizes violate the conditions of Eq. 10");
         }
@@ -767,6 +897,10 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
     ALLOC(p->mean, NC);
     ALLOC(p->m2, NC);
     ALLOC(p->st, 1);
+    if (poisson) {
+        ALLOC(p->z1, NC);
+        ALLOC(p->z2, NC);
+    }
     if (q.stream) {
         p->stream = (cudaStream_t)q.stream;
     } else {
@@ -801,7 +935,15 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
         cudaMemset(p->scratch, 0, p->scratch_bytes);
     }
 #undef ALLOC
-    cudaMemcpy(p->y, q.y, N * 4, cudaMemcpyHostToDevice);
+    if (inpaint) {
+        // missing pixels hold NaN: the masked update reads the mask from y
+        std::vector<float> yo(q.y, q.y + N);
+        for (int64_t i = 0; i < N; ++i)
+            if (q.mask[i] == 0.f) yo[i] = std::numeric_limits<float>::quiet_NaN();
+        cudaMemcpy(p->y, yo.data(), N * 4, cudaMemcpyHostToDevice);
+    } else {
+        cudaMemcpy(p->y, q.y, N * 4, cudaMemcpyHostToDevice);
+    }
     cudaMemcpy(p->h, q.h, (size_t)q.kh * q.kw * 4, cudaMemcpyHostToDevice);
     {
         std::vector<float> sep;
@@ -822,7 +964,7 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
         cudaMemset(p->m2, 0, NC * 4);
         UpdateParams u;
         pnp_status us = problem_update_params(p, u);
-        if (us == PNP_OK) {
+        if (us == PNP_OK && !inpaint) {
             u.t_dev = nullptr;
             u.burn_dev = nullptr;
             u.arrive = nullptr;
@@ -843,12 +985,27 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
     cudaMemset(p->m2, 0, NC * 4);
     cudaMemset(p->r, 0, NC * 4);
     cudaMemset(p->d, 0, NC * 4);
+    if (poisson) {
+        // auxiliary variables start at zero (Sec. IV-B)
+        cudaMemset(p->z1, 0, NC * 4);
+        cudaMemset(p->z2, 0, NC * 4);
+    }
     StepState s0{0u, (int32_t)q.burn_in, 0u};
     cudaMemcpy(p->st, &s0, sizeof(s0), cudaMemcpyHostToDevice);
     if (q.D && q.precision == PNP_FP8 && !q.D->dev.fp8_calibrated) {
-        // static activation scales from the observation y (x = y)
-        pnp_status cs = pnp_denoiser_calibrate_fp8(const_cast<pnp_denoiser*>(q.D), p->y, q.ny, q.nx, 1,
+        // static activation scales from an image of the signal's range: the
+        // observation y (x = y), the counts over eta (Poisson), or the
+        // initial state (inpainting: y is zero at 70 % of the pixels)
+        const float* src = p->y;
+        if (poisson || (inpaint && q.x0)) {
+            std::vector<float> c(N);
+            for (int64_t i = 0; i < N; ++i) c[i] = poisson ? (float)(q.y[i] / q.eta) : q.x0[i];
+            cudaMemcpy(p->r, c.data(), N * 4, cudaMemcpyHostToDevice);
+            src = p->r;
+        }
+        pnp_status cs = pnp_denoiser_calibrate_fp8(const_cast<pnp_denoiser*>(q.D), src, q.ny, q.nx, 1,
                                                    p->stream);
+        if (src != p->y) cudaMemsetAsync(p->r, 0, NC * 4, p->stream);
         if (cs != PNP_OK) {
             pnp_destroy_problem(p);
             return cs;
@@ -1027,6 +1184,24 @@ extern "C" pnp_status pnp_set_state(pnp_problem* p, const float* x, int64_t t) {
     PNP_CUDA_TRY(cudaMemcpyAsync(p->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, p->stream));
     PNP_CUDA_TRY(cudaStreamSynchronize(p->stream));
     p->t = t;
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_get_aux_state(pnp_problem* p, float* z1, float* z2) {
+    if (!p || !p->poisson) return fail(PNP_EINVAL, "pnp_get_aux_state: not a Poisson problem");
+    const size_t bytes = (size_t)p->N * p->nchain * 4;
+    if (z1) PNP_CUDA_TRY(cudaMemcpyAsync(z1, p->z1, bytes, cudaMemcpyDeviceToHost, p->stream));
+    if (z2) PNP_CUDA_TRY(cudaMemcpyAsync(z2, p->z2, bytes, cudaMemcpyDeviceToHost, p->stream));
+    PNP_CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_set_aux_state(pnp_problem* p, const float* z1, const float* z2) {
+    if (!p || !p->poisson) return fail(PNP_EINVAL, "pnp_set_aux_state: not a Poisson problem");
+    const size_t bytes = (size_t)p->N * p->nchain * 4;
+    if (z1) PNP_CUDA_TRY(cudaMemcpyAsync(p->z1, z1, bytes, cudaMemcpyHostToDevice, p->stream));
+    if (z2) PNP_CUDA_TRY(cudaMemcpyAsync(p->z2, z2, bytes, cudaMemcpyHostToDevice, p->stream));
+    PNP_CUDA_TRY(cudaStreamSynchronize(p->stream));
     return PNP_OK;
 }
 

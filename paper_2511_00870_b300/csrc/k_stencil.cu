@@ -292,11 +292,14 @@ __device__ __forceinline__ void stencil_tile(const float* img, int ny, int nx, i
     }
 }
 
+// out = (a (h * x) - y) scale; y is shared by the images (y_img_stride 0) or
+// one plane per image (the Poisson sampler's z1).
 template <int KW, int R, bool SEP>
 __global__ void __launch_bounds__(256) k_blur(const float* __restrict__ x,
                                               const float* __restrict__ y,
                                               const float* __restrict__ h, int kh, int ny, int nx,
-                                              float scale, int adjoint, float* __restrict__ out) {
+                                              float scale, int adjoint, float* __restrict__ out,
+                                              float a, int64_t y_img_stride) {
     extern __shared__ float4 sm4[];
     const int rows = R * blockDim.y;
     const int64_t plane = (int64_t)ny * nx;
@@ -312,6 +315,7 @@ __global__ void __launch_bounds__(256) k_blur(const float* __restrict__ x,
     stencil_tile<KW, R, SEP>(x + img * plane, ny, nx, i0, j0, kh, rows, h, !adjoint,
                              reinterpret_cast<float*>(sm4), active, acc);
     if (!active) return;
+    if (y) y += img * y_img_stride;
     // 128-bit accesses when rows are whole float4s (then j + 3 < nx) and aligned
     const bool vec = (nx & 3) == 0 && ((reinterpret_cast<uintptr_t>(out) |
                                         reinterpret_cast<uintptr_t>(y)) & 15) == 0;
@@ -321,7 +325,7 @@ __global__ void __launch_bounds__(256) k_blur(const float* __restrict__ x,
         if (i >= ny) break;
         const int64_t n = (int64_t)i * nx + j;
         if (vec) {
-            float4 v = make_float4(acc[o][0], acc[o][1], acc[o][2], acc[o][3]);
+            float4 v = make_float4(a * acc[o][0], a * acc[o][1], a * acc[o][2], a * acc[o][3]);
             if (y) {
                 const float4 yv = __ldg(reinterpret_cast<const float4*>(y + n));
                 v.x -= yv.x; v.y -= yv.y; v.z -= yv.z; v.w -= yv.w;
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(256) k_blur(const float* __restrict__ x,
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if (j + q < nx) {
-                    float v = acc[o][q];
+                    float v = a * acc[o][q];
                     if (y) v -= __ldg(y + n + q);
                     out[img * plane + n + q] = v * scale;
                 }
@@ -349,18 +353,18 @@ __global__ void __launch_bounds__(256) k_blur(const float* __restrict__ x,
 // With `arrive` set, the last block to finish advances the device step counter
 // (every block has read t by then).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void normals4(const UpdateParams& p, int64_t n0, uint32_t t,
-                                         uint32_t chain, float z[4]) {
+__device__ __forceinline__ void normals4(uint32_t key0, uint32_t key1, int64_t n0, uint32_t t,
+                                         uint32_t chain, float z[4], uint32_t stream = 0) {
     // normals of the 4 pixels n0..n0+3 (flat row-major index): 1 or 2 Philox groups
     const uint32_t m0 = (uint32_t)(n0 >> 2);
     float za[4];
-    normals_group(m0, t, chain, p.key0, p.key1, za);
+    normals_group(m0, t, chain, key0, key1, za, stream);
     const int off = (int)(n0 & 3);
     if (off == 0) {
         z[0] = za[0]; z[1] = za[1]; z[2] = za[2]; z[3] = za[3];
     } else {
         float zb[4];
-        normals_group(m0 + 1, t, chain, p.key0, p.key1, zb);
+        normals_group(m0 + 1, t, chain, key0, key1, zb, stream);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int k = off + q;
@@ -372,8 +376,9 @@ __device__ __forceinline__ void normals4(const UpdateParams& p, int64_t n0, uint
 }
 
 __device__ __forceinline__ float update1(const UpdateParams& p, float xv, float gq, float dv,
-                                         float zq) {
+                                         float zq, float z2v) {
     float v = xv - p.gamma * (gq * p.inv_s2);
+    if (p.z2) v -= p.c_z2 * (xv - z2v);   // Poisson: (gamma / rho2)(x - z2)
     if (p.d) v += p.d_residual ? -p.c_prior * dv : p.c_prior * (dv - xv);
     const float pr = fminf(fmaxf(xv, 0.f), 1.f);
     v += p.c_proj * (pr - xv);
@@ -417,24 +422,26 @@ __global__ void __launch_bounds__(256) k_update(UpdateParams p) {
         float* qc = p.m2 ? p.m2 + chain * plane : nullptr;
         const bool vec = (nx & 3) == 0 &&
                          ((reinterpret_cast<uintptr_t>(p.x) | reinterpret_cast<uintptr_t>(p.d) |
-                           reinterpret_cast<uintptr_t>(p.mean) | reinterpret_cast<uintptr_t>(p.m2)) &
-                          15) == 0;
+                           reinterpret_cast<uintptr_t>(p.mean) | reinterpret_cast<uintptr_t>(p.m2) |
+                           reinterpret_cast<uintptr_t>(p.z2)) & 15) == 0;
 #pragma unroll
         for (int o = 0; o < R; ++o) {
             const int i = i0 + ty * R + o;
             if (i >= ny) break;
             const int64_t n0 = (int64_t)i * nx + j;
             float z[4] = {0.f, 0.f, 0.f, 0.f};
-            if (p.c_noise != 0.f) normals4(p, n0, t, (uint32_t)chain, z);
+            if (p.c_noise != 0.f) normals4(p.key0, p.key1, n0, t, (uint32_t)chain, z);
             if (vec) {
                 float4 xv = *reinterpret_cast<const float4*>(xc + n0);
                 float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (dc) dv = __ldg(reinterpret_cast<const float4*>(dc + n0));
+                float4 z2v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (p.z2) z2v = __ldg(reinterpret_cast<const float4*>(p.z2 + chain * plane + n0));
                 float4 v;
-                v.x = update1(p, xv.x, g[o][0], dv.x, z[0]);
-                v.y = update1(p, xv.y, g[o][1], dv.y, z[1]);
-                v.z = update1(p, xv.z, g[o][2], dv.z, z[2]);
-                v.w = update1(p, xv.w, g[o][3], dv.w, z[3]);
+                v.x = update1(p, xv.x, g[o][0], dv.x, z[0], z2v.x);
+                v.y = update1(p, xv.y, g[o][1], dv.y, z[1], z2v.y);
+                v.z = update1(p, xv.z, g[o][2], dv.z, z[2], z2v.z);
+                v.w = update1(p, xv.w, g[o][3], dv.w, z[3], z2v.w);
                 *reinterpret_cast<float4*>(xc + n0) = v;
                 if (inv_n > 0.f) {
                     float4 mo = *reinterpret_cast<const float4*>(mc + n0);
@@ -451,7 +458,8 @@ __global__ void __launch_bounds__(256) k_update(UpdateParams p) {
                 for (int q = 0; q < 4; ++q) {
                     if (j + q >= nx) break;
                     const int64_t n = n0 + q;
-                    const float v = update1(p, xc[n], g[o][q], dc ? __ldg(dc + n) : 0.f, z[q]);
+                    const float v = update1(p, xc[n], g[o][q], dc ? __ldg(dc + n) : 0.f, z[q],
+                                            p.z2 ? __ldg(p.z2 + chain * plane + n) : 0.f);
                     xc[n] = v;
                     if (inv_n > 0.f) {
                         float mo = mc[n], qo = qc[n];
@@ -475,16 +483,180 @@ __global__ void __launch_bounds__(256) k_update(UpdateParams p) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Poisson sampler, auxiliary variables (Eq. 14, PSGLA transition of z from the
+// new x, Algorithm 1's z-update): w = eta (h * x+) from the shared-memory
+// window of x+ (the forward operator: correlation with the flipped taps), then
+//   z1+ = prox_{kappa1 KL(y || .)}( z1 - (kappa1 / rho1)(z1 - w) + sqrt(2 kappa1) zeta1 )
+//   z2+ = max( z2 - (kappa2 / rho2)(z2 - x+) + sqrt(2 kappa2) zeta2, 0 )
+// with zeta1, zeta2 from Philox streams 1 and 2. The KL prox is the positive
+// root of u^2 + (kappa - v) u - kappa y = 0, evaluated as (a + s) / 2 for
+// a = v - kappa >= 0 and as 2 kappa y / (s - a) otherwise (s = sqrt(a^2 + 4
+// kappa y)), which avoids the cancellation of the first form for a < 0. With
+// `arrive` set, the last block advances the step counter (this is the last
+// kernel of a Poisson iteration).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float kl_prox(float v, float y, float kappa) {
+    const float a = v - kappa;
+    const float s = sqrtf(fmaf(a, a, 4.0f * kappa * y));
+    return a >= 0.f ? 0.5f * (a + s) : (2.0f * kappa * y) / (s - a);
+}
+
+template <int KW, int R, bool SEP>
+__global__ void __launch_bounds__(256) k_zupdate(ZParams p) {
+    extern __shared__ float4 sm4[];
+    const int kh = p.kh, ny = p.ny, nx = p.nx;
+    const int rows = R * blockDim.y;
+    const int64_t plane = (int64_t)ny * nx;
+    const int chain = blockIdx.z;
+    const int i0 = blockIdx.y * rows, j0 = blockIdx.x * ST_TX;
+    pdl_wait();
+    pdl_launch_dependents();
+    const uint32_t t = p.t_dev ? *p.t_dev : p.t;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int j = j0 + 4 * tx;
+    const bool active = j < nx && i0 + ty * R < ny;
+    float hx[R][4];
+    // forward operator on x+: correlation with the flipped kernel
+    stencil_tile<KW, R, SEP>(p.x + chain * plane, ny, nx, i0, j0, kh, rows, SEP ? p.hsep : p.h,
+                             true, reinterpret_cast<float*>(sm4), active, hx);
+    if (active) {
+        const float* xc = p.x + chain * plane;
+        float* z1c = p.z1 + chain * plane;
+        float* z2c = p.z2 + chain * plane;
+#pragma unroll
+        for (int o = 0; o < R; ++o) {
+            const int i = i0 + ty * R + o;
+            if (i >= ny) break;
+            const int64_t n0 = (int64_t)i * nx + j;
+            float e1[4] = {0.f, 0.f, 0.f, 0.f}, e2[4] = {0.f, 0.f, 0.f, 0.f};
+            if (p.noise) {
+                normals4(p.key0, p.key1, n0, t, (uint32_t)chain, e1, 1u);
+                normals4(p.key0, p.key1, n0, t, (uint32_t)chain, e2, 2u);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (j + q >= nx) break;
+                const int64_t n = n0 + q;
+                const float w = p.eta * hx[o][q];
+                const float z1 = z1c[n];
+                const float v1 = z1 - p.a1 * (z1 - w) + p.s1 * e1[q];
+                z1c[n] = kl_prox(v1, __ldg(p.y + n), p.kappa1);
+                const float z2 = z2c[n];
+                const float v2 = z2 - p.a2 * (z2 - __ldg(xc + n)) + p.s2 * e2[q];
+                z2c[n] = fmaxf(v2, 0.f);
+            }
+        }
+    }
+    if (p.arrive) {
+        __syncthreads();
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+            if (atomicAdd(p.arrive, 1u) == nblk - 1) {
+                *p.arrive = 0u;
+                *const_cast<uint32_t*>(p.t_dev) = t + 1u;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Inpainting x-update (Eq. 8 with H = diag(mask), Sec. IV-A): H^T (H x - y) is
+// x - y at an observed pixel and 0 at a missing one, so there is no stencil
+// and no residual plane. y holds NaN at missing pixels (the mask costs no
+// extra bytes). Each thread updates 4 consecutive pixels of one chain:
+// 16 B (x, y, d read; x written) during burn-in, 32 B while sampling.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_update_mask(UpdateParams p) {
+    const int64_t plane = (int64_t)p.ny * p.nx;
+    const int chain = blockIdx.y;
+    const int64_t n0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    pdl_wait();
+    pdl_launch_dependents();
+    const uint32_t t = p.t_dev ? *p.t_dev : p.t;
+    if (n0 < plane) {
+        float inv_n = p.inv_n;
+        if (p.burn_dev) {
+            const int64_t n = (int64_t)t + 1 - *p.burn_dev;
+            inv_n = n > 0 ? 1.0f / (float)n : 0.0f;
+        }
+        float* xc = p.x + chain * plane;
+        const float* dc = p.d ? p.d + chain * plane : nullptr;
+        float* mc = p.mean ? p.mean + chain * plane : nullptr;
+        float* qc = p.m2 ? p.m2 + chain * plane : nullptr;
+        float z[4] = {0.f, 0.f, 0.f, 0.f};
+        if (p.c_noise != 0.f) normals4(p.key0, p.key1, n0, t, (uint32_t)chain, z);
+        const bool vec = (plane & 3) == 0 &&
+                         ((reinterpret_cast<uintptr_t>(p.x) | reinterpret_cast<uintptr_t>(p.d) |
+                           reinterpret_cast<uintptr_t>(p.r) | reinterpret_cast<uintptr_t>(p.mean) |
+                           reinterpret_cast<uintptr_t>(p.m2)) & 15) == 0;
+        if (vec) {
+            const float4 xv = *reinterpret_cast<const float4*>(xc + n0);
+            const float4 yv = __ldg(reinterpret_cast<const float4*>(p.r + n0));
+            float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (dc) dv = __ldg(reinterpret_cast<const float4*>(dc + n0));
+            float4 v;
+            v.x = update1(p, xv.x, isnan(yv.x) ? 0.f : xv.x - yv.x, dv.x, z[0], 0.f);
+            v.y = update1(p, xv.y, isnan(yv.y) ? 0.f : xv.y - yv.y, dv.y, z[1], 0.f);
+            v.z = update1(p, xv.z, isnan(yv.z) ? 0.f : xv.z - yv.z, dv.z, z[2], 0.f);
+            v.w = update1(p, xv.w, isnan(yv.w) ? 0.f : xv.w - yv.w, dv.w, z[3], 0.f);
+            *reinterpret_cast<float4*>(xc + n0) = v;
+            if (inv_n > 0.f) {
+                float4 mo = *reinterpret_cast<const float4*>(mc + n0);
+                float4 qo = *reinterpret_cast<const float4*>(qc + n0);
+                welford1(v.x, inv_n, mo.x, qo.x);
+                welford1(v.y, inv_n, mo.y, qo.y);
+                welford1(v.z, inv_n, mo.z, qo.z);
+                welford1(v.w, inv_n, mo.w, qo.w);
+                *reinterpret_cast<float4*>(mc + n0) = mo;
+                *reinterpret_cast<float4*>(qc + n0) = qo;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t n = n0 + q;
+                if (n >= plane) break;
+                const float xv = xc[n], yv = __ldg(p.r + n);
+                const float v = update1(p, xv, isnan(yv) ? 0.f : xv - yv, dc ? __ldg(dc + n) : 0.f,
+                                        z[q], 0.f);
+                xc[n] = v;
+                if (inv_n > 0.f) {
+                    float mo = mc[n], qo = qc[n];
+                    welford1(v, inv_n, mo, qo);
+                    mc[n] = mo;
+                    qc[n] = qo;
+                }
+            }
+        }
+    }
+    if (p.arrive) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+            if (atomicAdd(p.arrive, 1u) == nblk - 1) {
+                *p.arrive = 0u;
+                *const_cast<uint32_t*>(p.t_dev) = t + 1u;
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ dispatch
 
 using BlurFn = void (*)(const float*, const float*, const float*, int, int, int, float, int,
-                        float*);
+                        float*, float, int64_t);
 using UpdFn = void (*)(UpdateParams);
+using ZFn = void (*)(ZParams);
 
 template <int KW>
 static BlurFn blur_fn_r(int R, bool sep) {
     if (sep) return R == 1 ? k_blur<KW, 1, true> : R == 2 ? k_blur<KW, 2, true> : k_blur<KW, 4, true>;
     return R == 1 ? k_blur<KW, 1, false> : R == 2 ? k_blur<KW, 2, false> : k_blur<KW, 4, false>;
+}
+template <int KW>
+static ZFn z_fn_r(int R, bool sep) {
+    if (sep) return R == 1 ? k_zupdate<KW, 1, true> : R == 2 ? k_zupdate<KW, 2, true> : k_zupdate<KW, 4, true>;
+    return R == 1 ? k_zupdate<KW, 1, false> : R == 2 ? k_zupdate<KW, 2, false> : k_zupdate<KW, 4, false>;
 }
 template <int KW>
 static UpdFn upd_fn_r(int R, bool sep) {
@@ -505,6 +677,7 @@ static UpdFn upd_fn_r(int R, bool sep) {
 
 static BlurFn blur_fn(int kw, int R, bool sep) { PNP_KW_CASES(blur_fn_r) }
 static UpdFn upd_fn(int kw, int R, bool sep) { PNP_KW_CASES(upd_fn_r) }
+static ZFn z_fn(int kw, int R, bool sep) { PNP_KW_CASES(z_fn_r) }
 #undef PNP_KW_CASES
 
 // Tiles whose shared memory exceeds the 48 KB default need the opt-in, once
@@ -531,7 +704,8 @@ static int resolve_tile(int tile) {
 
 static cudaError_t blur_raw(const float* x, const float* y, const float* h, const float* hsep,
                             int kh, int kw, int ny, int nx, int nimg, float scale, bool adjoint,
-                            float* out, int tile, cudaStream_t s) {
+                            float* out, int tile, cudaStream_t s, float a = 1.0f,
+                            int64_t y_img_stride = 0) {
     const TileShape ts = kTiles[tile];
     const int rows = ts.R * ts.BY;
     const bool sep = hsep != nullptr;
@@ -542,7 +716,20 @@ static cudaError_t blur_raw(const float* x, const float* y, const float* h, cons
     if (e != cudaSuccess) return e;
     dim3 grid(ceil_div(nx, ST_TX), ceil_div(ny, rows), nimg);
     return launch_pdl(fn, grid, dim3(16, ts.BY), smem, s, x, y, sep ? hsep : h, kh, ny, nx, scale,
-                      adjoint ? 1 : 0, out);
+                      adjoint ? 1 : 0, out, a, y_img_stride);
+}
+
+static cudaError_t zupdate_raw(const ZParams& p, int tile, cudaStream_t s) {
+    const TileShape ts = kTiles[tile];
+    const int rows = ts.R * ts.BY;
+    const bool sep = p.hsep != nullptr;
+    ZFn fn = z_fn(p.kw, ts.R, sep);
+    if (!fn || p.kh > ST_MAXK) return cudaErrorInvalidValue;
+    const size_t smem = tile_smem(p.kw, p.kh, rows, sep);
+    cudaError_t e = allow_smem(fn, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(ceil_div(p.nx, ST_TX), ceil_div(p.ny, rows), p.nchain);
+    return launch_pdl(fn, grid, dim3(16, ts.BY), smem, s, p);
 }
 
 static cudaError_t update_raw(const UpdateParams& p, int tile, cudaStream_t s) {
@@ -559,10 +746,11 @@ static cudaError_t update_raw(const UpdateParams& p, int tile, cudaStream_t s) {
 }
 
 cudaError_t launch_blur(const float* x, const float* y, const float* h, int kh, int kw, int ny,
-                        int nx, int nimg, float* r, cudaStream_t s, int tile, const float* hsep) {
+                        int nx, int nimg, float* r, cudaStream_t s, int tile, const float* hsep,
+                        float a, int64_t y_img_stride) {
     timer_begin(T_BLUR, s);
     cudaError_t e = blur_raw(x, y, h, hsep, kh, kw, ny, nx, nimg, 1.0f, false, r,
-                             resolve_tile(tile), s);
+                             resolve_tile(tile), s, a, y_img_stride);
     timer_end(T_BLUR, s);
     return e;
 }
@@ -577,6 +765,23 @@ cudaError_t launch_langevin_update(const UpdateParams& p, cudaStream_t s) {
     timer_begin(T_UPDATE, s);
     cudaError_t e = update_raw(p, resolve_tile(p.tile), s);
     timer_end(T_UPDATE, s);
+    return e;
+}
+
+cudaError_t launch_update_mask(const UpdateParams& p, cudaStream_t s) {
+    timer_begin(T_UPDATE, s);
+    const int64_t plane = (int64_t)p.ny * p.nx;
+    const int64_t groups = (plane + 3) / 4;
+    dim3 grid((unsigned)((groups + 255) / 256), p.nchain, 1);
+    cudaError_t e = launch_pdl(k_update_mask, grid, dim3(256), 0, s, p);
+    timer_end(T_UPDATE, s);
+    return e;
+}
+
+cudaError_t launch_zupdate(const ZParams& p, cudaStream_t s) {
+    timer_begin(T_ZUPDATE, s);
+    cudaError_t e = zupdate_raw(p, resolve_tile(p.tile), s);
+    timer_end(T_ZUPDATE, s);
     return e;
 }
 

@@ -53,10 +53,12 @@ __device__ __forceinline__ void sincos_2pi_uniform(uint32_t w, float* s, float* 
     sincospif(a, s, c);
 }
 
-// The four normals of group m: Box-Muller on (w0, w1) and (w2, w3).
+// The four normals of group m: Box-Muller on (w0, w1) and (w2, w3). `stream`
+// is the counter's last word: 0 drives the x-update's xi, 1 and 2 the
+// auxiliary variables' zeta_1 and zeta_2 of the Poisson sampler.
 __device__ __forceinline__ void normals_group(uint32_t m, uint32_t t, uint32_t chain, uint32_t k0,
-                                              uint32_t k1, float z[4]) {
-    const U4 r = philox4x32_10(U4{m, t, chain, 0u}, k0, k1);
+                                              uint32_t k1, float z[4], uint32_t stream = 0) {
+    const U4 r = philox4x32_10(U4{m, t, chain, stream}, k0, k1);
     float s, c;
     float rad = sqrtf(-2.0f * log_uniform(r.x));
     sincos_2pi_uniform(r.y, &s, &c);

@@ -40,7 +40,8 @@ int num_sms();
 bool timer_enabled();
 void timer_begin(int id, cudaStream_t s);
 void timer_end(int id, cudaStream_t s);
-enum TimerId { T_BLUR = 0, T_UPDATE = 1, T_CONV_FP32 = 2, T_CONV_TC = 3, T_CONV_EDGE = 4, T_CONV_LAST = 5, T_COUNT = 6 };
+enum TimerId { T_BLUR = 0, T_UPDATE = 1, T_CONV_FP32 = 2, T_CONV_TC = 3, T_CONV_EDGE = 4, T_CONV_LAST = 5,
+               T_ZUPDATE = 6, T_COUNT = 7 };
 
 // Programmatic dependent launch for the kernels of one iteration (stencils,
 // tensor-core conv layers): a kernel launched this way may start while its
@@ -130,9 +131,10 @@ namespace pnp {
 // Stencils take a tile-shape index (stencil_autotune's choice; -1 = default);
 // every shape gives bitwise the same results.
 // hsep (optional): separable taps [u | v | u flipped | v flipped] of a rank-one h.
+// r = a (h * x) - y per image; y shared (y_img_stride 0) or one plane per image.
 cudaError_t launch_blur(const float* x, const float* y, const float* h, int kh, int kw, int ny,
                         int nx, int nimg, float* r, cudaStream_t s, int tile = -1,
-                        const float* hsep = nullptr);
+                        const float* hsep = nullptr, float a = 1.0f, int64_t y_img_stride = 0);
 cudaError_t launch_blur_adjoint(const float* r, const float* h, int kh, int kw, int ny, int nx,
                                 int nimg, float scale, float* g, cudaStream_t s, int tile = -1);
 int stencil_tile_count();
@@ -161,7 +163,34 @@ struct UpdateParams {
     uint32_t* arrive;          // if non-null: the last block advances *t_dev (graph replay)
     int tile;                  // stencil tile shape (-1 = default)
     const float* hsep;         // separable taps of a rank-one h (nullptr: 2-D taps)
+    const float* z2;           // Poisson: auxiliary z2 [chain][N]; adds -c_z2 (x - z2)
+    float c_z2;                // gamma / rho2
 };
+
+// Auxiliary-variable update of the Poisson sampler (k_zupdate).
+struct ZParams {
+    const float* x;            // new x [chain][N]
+    float* z1;                 // [chain][N], updated in place
+    float* z2;                 // [chain][N], updated in place
+    const float* y;            // counts [N]
+    const float* h;
+    const float* hsep;
+    int kh, kw, ny, nx, nchain;
+    float eta;
+    float a1, a2;              // kappa_i / rho_i
+    float s1, s2;              // sqrt(2 kappa_i)
+    float kappa1;
+    int noise;
+    uint32_t key0, key1;
+    uint32_t t;
+    const uint32_t* t_dev;
+    uint32_t* arrive;          // if non-null: the last block advances *t_dev
+    int tile;
+};
+cudaError_t launch_zupdate(const ZParams& p, cudaStream_t s);
+// Inpainting x-update: p.r is the observation with NaN at missing pixels
+// (shared by the chains); no stencil, p.h unused.
+cudaError_t launch_update_mask(const UpdateParams& p, cudaStream_t s);
 cudaError_t launch_langevin_update(const UpdateParams& p, cudaStream_t s);
 // Times the stencil tile shapes for r = H x - y and for the update `u` (which it
 // runs, overwriting u.x / u.mean / u.m2) and returns the fastest of each.
@@ -274,6 +303,13 @@ struct pnp_problem {
     pnp::StepState* st = nullptr;
     int64_t t = 0;
     int blur_tile = -1, update_tile = -1;   // autotuned stencil tile shapes
+    // Poisson model (AXDA + PSGLA): z1 ~ eta H x, z2 ~ x, [chain][N] each
+    bool poisson = false;
+    double eta = 0, rho1 = 0, rho2 = 0, kappa1 = 0, kappa2 = 0;
+    float* z1 = nullptr;
+    float* z2 = nullptr;
+    // inpainting (H = diag(mask)): y holds NaN at missing pixels, no blur
+    bool inpaint = false;
     float* hsep = nullptr;                  // separable taps when h is rank one
     cudaGraphExec_t graph = nullptr;         // one iteration
     cudaGraphExec_t graph_batch = nullptr;   // kGraphBatch iterations

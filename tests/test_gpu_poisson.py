@@ -1,0 +1,276 @@
+"""GPU parity of the Poisson sampler (AXDA split + PnP-ULA x-update + PSGLA
+z-updates, Sec. IV-B) against the FP64 oracle, through the problem API.
+
+One-step bound (FP32 path): from the same state (x, z1, z2) at step t, each of
+the GPU's x+, z1+, z2+ is within 1e-5 * max|ref| of the oracle's. The error
+budget: FP32 rounding of eta H x (values up to ~ eta) enters z1+ at a few ulp
+of eta, and x+ through gamma eta / rho1 ~ 2e-4, both far below the bound.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+ETA, RHO1, RHO2 = 250.0, 10.0, 1e-3     # the paper's Poisson setting
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_00870_b300 as P
+    return P
+
+
+def _state(prob, seed):
+    """A plausible mid-chain state: x near the truth, z1 near eta H x (some
+    entries clipped to 0), z2 near x, all non-negative where the sampler keeps them."""
+    rng = np.random.default_rng(seed)
+    x = np.clip(prob.xbar + 0.05 * rng.standard_normal(prob.shape), -0.1, 1.1)
+    z1 = np.maximum(ETA * synth.fft_circular_blur(x, prob.h) + 5.0 * rng.standard_normal(prob.shape), 0)
+    z2 = np.maximum(x + 0.02 * rng.standard_normal(prob.shape), 0)
+    f = lambda a: a.astype(np.float32)
+    return f(x), f(z1), f(z2)
+
+
+def _gpu_problem(P, prob, den, **kw):
+    return P.Problem(prob.y, prob.h, 0.0, den, noise_model="poisson", eta=prob.eta, rho1=RHO1,
+                     rho2=RHO2, seed=prob.seed, **kw)
+
+
+def _oracle(orc, prob, prm, net):
+    k1, k2 = 0.99 * RHO1, 0.99 * RHO2
+    return orc.PoissonProblem(prob.y, prob.h, prob.eta, RHO1, RHO2, k1, k2,
+                              prm["alpha"] if net else 0.0, prm["eps"], prm["lam"], prm["gamma"],
+                              prob.seed, net=net)
+
+
+def _check(got, ref, rel=1e-5, extra=0.0, what=""):
+    for g, r, name in zip(got, ref, ("x", "z1", "z2")):
+        err = np.abs(g - r).max()
+        tol = rel * np.abs(r).max() + (extra[name] if isinstance(extra, dict) else extra)
+        assert err <= tol, (what, name, err, tol)
+
+
+@pytest.mark.parametrize("kernel", ["uniform5", "motion7"])
+def test_poisson_one_step_fp32(P, orc, kernel):
+    """Ragged 72 x 136 image, FP32 denoiser, separable and non-separable blur;
+    the step index enters the three Philox streams."""
+    h = synth.uniform_kernel(5) if kernel == "uniform5" else synth.motion_kernel(7, 0.6)
+    prob = synth.make_poisson_problem(72, 136, h, ETA, 4242)
+    dw = synth.workload_denoiser(1)
+    gp = _gpu_problem(P, prob, P.Denoiser.from_weights(dw))
+    prm = gp.params()
+    op = _oracle(orc, prob, prm, orc.Net.from_weights(dw))
+    x, z1, z2 = _state(prob, 1)
+    for t in (0, 7):
+        gp.set_state(x, t)
+        gp.set_aux_state(z1, z2)
+        gp.step(1)
+        xg, tt = gp.state()
+        z1g, z2g = gp.aux_state()
+        assert tt == t + 1
+        ref = orc.poisson_step(op, x, z1, z2, t)
+        _check((xg[0], z1g[0], z2g[0]), ref, what=(kernel, t))
+
+
+def test_poisson_steps_chain_through_t(P, orc):
+    """Three consecutive GPU steps, the oracle stepped from the GPU state at
+    every t: the device step counter advances once per iteration (the x- and
+    z-updates of one iteration share t), and z starts at zero."""
+    prob = synth.make_poisson_problem(64, 96, synth.gaussian_kernel(7, 1.5), ETA, 77)
+    gp = _gpu_problem(P, prob, None)
+    prm = gp.params()
+    op = _oracle(orc, prob, prm, None)
+    z1g, z2g = gp.aux_state()
+    assert not z1g.any() and not z2g.any()
+    x = np.clip(prob.xbar, 0, 1).astype(np.float32)
+    gp.set_state(x, 0)
+    z1 = z2 = np.zeros(prob.shape, np.float32)
+    for t in range(3):
+        gp.step(1)
+        xg, tt = gp.state()
+        z1g, z2g = gp.aux_state()
+        assert tt == t + 1
+        ref = orc.poisson_step(op, x, z1, z2, t)
+        _check((xg[0], z1g[0], z2g[0]), ref, what=t)
+        x, z1, z2 = xg[0], z1g[0], z2g[0]
+
+
+def test_poisson_graph_equals_eager_and_chains(P):
+    """Graph replay equals eager launches bitwise; chain c of a 2-chain
+    problem equals the same chain run alone for c = 0."""
+    prob = synth.make_poisson_problem(96, 80, synth.uniform_kernel(9), ETA, 31)
+    dw = synth.workload_denoiser(1)
+    den = P.Denoiser.from_weights(dw)
+    out = []
+    for graph in (True, False):
+        P.pnp_set_graph_mode(graph)
+        gp = _gpu_problem(P, prob, den, nchain=2, burn_in=2)
+        gp.run_chain(11, 2)
+        out.append((gp.state()[0], gp.aux_state(), gp.moments(want_var=True)))
+    P.pnp_set_graph_mode(True)
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1][0], out[1][1][0])
+    np.testing.assert_array_equal(out[0][1][1], out[1][1][1])
+    np.testing.assert_array_equal(out[0][2][0], out[1][2][0])
+    assert not np.array_equal(out[0][0][0], out[0][0][1])
+    solo = _gpu_problem(P, prob, den, nchain=1, burn_in=2)
+    solo.run_chain(11, 2)
+    np.testing.assert_array_equal(solo.state()[0][0], out[0][0][0])
+    np.testing.assert_array_equal(solo.aux_state()[0][0], out[0][1][0][0])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_poisson_block_split_invariance(P, prec):
+    prob = synth.make_poisson_problem(128, 128, synth.uniform_kernel(9), ETA, 55)
+    dw = synth.workload_denoiser(2)
+    den = P.Denoiser.from_weights(dw)
+    res = []
+    for blocks, halo in [((1, 1), 0), ((4, 4), 8), ((2, 3), 8)]:
+        gp = _gpu_problem(P, prob, den, blocks=blocks, halo=halo, burn_in=1, precision=prec)
+        gp.run_chain(5, 1)
+        res.append((gp.state()[0], gp.aux_state()[0]))
+    for r in res[1:]:
+        np.testing.assert_array_equal(res[0][0], r[0])
+        np.testing.assert_array_equal(res[0][1], r[1])
+
+
+def test_poisson_batch_equals_single(P):
+    """Poisson jobs of different sizes in one batch (BF16 tensor-core layers
+    over all jobs' rows) give the same chains as each job alone."""
+    dw = synth.workload_denoiser(2)
+    den = P.Denoiser.from_weights(dw)
+    probs = [synth.make_poisson_problem(n, m, synth.uniform_kernel(5), ETA, 600 + k)
+             for k, (n, m) in enumerate([(64, 64), (96, 136), (128, 72)])]
+    jobs = [dict(y=p.y, h=p.h, sigma=0.0, noise_model="poisson", eta=p.eta, rho1=RHO1, rho2=RHO2,
+                 seed=p.seed, burn_in=1) for p in probs]
+    b = P.Batch(jobs, den, precision="bf16")
+    b.run(6, 1)
+    for k, p in enumerate(probs):
+        solo = _gpu_problem(P, p, den, burn_in=1, precision="bf16")
+        solo.run_chain(6, 1)
+        np.testing.assert_array_equal(b.job(k).state()[0], solo.state()[0])
+        np.testing.assert_array_equal(b.job(k).aux_state()[0], solo.aux_state()[0])
+
+
+def test_poisson_full_size_no_prior_every_element(P, orc):
+    """1024 x 1024, 9 x 9 uniform blur, prior off: every element of x+, z1+,
+    z2+ against the oracle's full-image step."""
+    prob = synth.make_poisson_problem(1024, 1024, synth.uniform_kernel(9), ETA, 1201)
+    gp = _gpu_problem(P, prob, None)
+    prm = gp.params()
+    op = _oracle(orc, prob, prm, None)
+    x, z1, z2 = _state(prob, 2)
+    gp.set_state(x, 499)
+    gp.set_aux_state(z1, z2)
+    gp.step(1)
+    xg, _ = gp.state()
+    z1g, z2g = gp.aux_state()
+    ref = orc.poisson_step(op, x, z1, z2, 499)
+    _check((xg[0], z1g[0], z2g[0]), ref)
+
+
+def _crop_wrap(a, i, j, r):
+    ny, nx = a.shape
+    return np.take(np.take(a, np.arange(i - r, i + r + 1) % ny, axis=0),
+                   np.arange(j - r, j + r + 1) % nx, axis=1)
+
+
+def _segments(idx):
+    """Split wrapped indices into runs of consecutive values: [(positions, lo, hi)]."""
+    runs, start = [], 0
+    for k in range(1, len(idx) + 1):
+        if k == len(idx) or idx[k] != idx[k - 1] + 1:
+            runs.append((np.arange(start, k), idx[start], idx[k - 1]))
+            start = k
+    return runs
+
+
+def _denoise_window(orc, net, x, ii, jj):
+    """D(x) at the wrapped window ii x jj: zero padding at the image border,
+    computed on unwrapped crops with K pixels of margin."""
+    ny, nx = x.shape
+    K = net.K
+    out = np.empty((len(ii), len(jj)))
+    for pr, r0, r1 in _segments(ii):
+        for pc, c0, c1 in _segments(jj):
+            a0, a1 = max(0, r0 - K), min(ny, r1 + K + 1)
+            b0, b1 = max(0, c0 - K), min(nx, c1 + K + 1)
+            dd = orc.denoise(x[a0:a1, b0:b1], net)
+            out[np.ix_(pr, pc)] = dd[r0 - a0:r1 - a0 + 1, c0 - b0:c1 - b0 + 1]
+    return out
+
+
+def poisson_step_at(orc, prm, prob, net, x, z1, z2, t, pix):
+    """The oracle's step at single pixels from wrapped crops, composed from its
+    blur, adjoint, denoiser, Philox streams and KL prox: x+ on the blur window
+    around the pixel (radius r: needs x at radius 3r and z1 at radius 2r; the
+    circular blur of a crop is exact at distance >= r from its edge), then z1+,
+    z2+ at the pixel."""
+    ny, nx = x.shape
+    rr = prob.h.shape[0] // 2
+    N = ny * nx
+    xi, ze1, ze2 = (orc.normals_stream(prob.seed, t, 0, s, N).reshape(ny, nx) for s in range(3))
+    gam, lam, eps, alpha = prm["gamma"], prm["lam"], prm["eps"], prm["alpha"]
+    k1, k2 = 0.99 * RHO1, 0.99 * RHO2
+    out = []
+    gmax = 0.0
+    for (i, j) in pix:
+        xc = _crop_wrap(x, i, j, 3 * rr)
+        r = ETA * orc.blur(xc, prob.h) - _crop_wrap(z1, i, j, 3 * rr)
+        g = orc.blur_adj(r, prob.h)[2 * rr:4 * rr + 1, 2 * rr:4 * rr + 1]   # radius r
+        xw = xc[2 * rr:4 * rr + 1, 2 * rr:4 * rr + 1]
+        z2w = _crop_wrap(z2, i, j, rr)
+        ii = np.arange(i - rr, i + rr + 1) % ny
+        jj = np.arange(j - rr, j + rr + 1) % nx
+        xp = xw - gam * ((ETA / RHO1) * g + (xw - z2w) / RHO2)
+        if net is not None:
+            G = xw - _denoise_window(orc, net, x, ii, jj)
+            gmax = max(gmax, np.abs(G).max())
+            xp -= alpha * gam / eps ** 2 * G
+        xp += gam / lam * (np.clip(xw, 0, 1) - xw)
+        xp += np.sqrt(2 * gam) * xi[np.ix_(ii, jj)]
+        w = ETA * orc.blur(xp, prob.h)[rr, rr]
+        v1 = z1[i, j] - k1 / RHO1 * (z1[i, j] - w) + np.sqrt(2 * k1) * ze1[i, j]
+        v2 = z2[i, j] - k2 / RHO2 * (z2[i, j] - xp[rr, rr]) + np.sqrt(2 * k2) * ze2[i, j]
+        out.append((xp[rr, rr], orc.kl_prox(v1, prob.y[i, j], k1), max(v2, 0.0)))
+    return np.array(out).T, gmax
+
+
+def test_poisson_full_size_sampled_bf16(P, orc):
+    """1024 x 1024, 9 x 9 uniform blur, 8L x 64ch BF16 denoiser, direct layout
+    (the benchmark's launch configuration): x+, z1+, z2+ at sampled pixels
+    (corners, edges, interior). Bound: the BF16 prior error c_prior |G_bf16 -
+    G| <= c_prior 3 % max|G| in x+, carried into z1+ by at most (kappa1 / rho1)
+    eta ||h||_1 (the KL prox is non-expansive) and into z2+ by kappa2 / rho2."""
+    prob = synth.make_poisson_problem(1024, 1024, synth.uniform_kernel(9), ETA, 1201)
+    dw = synth.workload_denoiser(2)
+    net = orc.Net.from_weights(dw)
+    gp = _gpu_problem(P, prob, P.Denoiser.from_weights(dw), precision="bf16")
+    prm = gp.params()
+    x, z1, z2 = _state(prob, 3)
+    rng = np.random.default_rng(1)
+    pix = [(0, 0), (0, 1023), (1023, 0), (1023, 1023), (2, 511), (511, 1021), (300, 700)] + \
+        [tuple(v) for v in rng.integers(0, 1024, size=(5, 2))]
+    t = 1999
+    gp.set_state(x, t)
+    gp.set_aux_state(z1, z2)
+    gp.step(1)
+    xg, _ = gp.state()
+    z1g, z2g = gp.aux_state()
+    (rx, r1, r2), gmax = poisson_step_at(orc, prm, prob, net, x.astype(np.float64),
+                                         z1.astype(np.float64), z2.astype(np.float64), t, pix)
+    c_prior = prm["alpha"] * prm["gamma"] / prm["eps"] ** 2
+    dx = c_prior * 3e-2 * gmax + 1e-5 * np.abs(rx).max()
+    gx = np.array([xg[0][i, j] for i, j in pix])
+    g1 = np.array([z1g[0][i, j] for i, j in pix])
+    g2 = np.array([z2g[0][i, j] for i, j in pix])
+    assert np.abs(gx - rx).max() <= dx, (np.abs(gx - rx).max(), dx)
+    d1 = 0.99 * ETA * np.abs(prob.h).sum() * dx + 1e-5 * np.abs(r1).max()
+    assert np.abs(g1 - r1).max() <= d1, (np.abs(g1 - r1).max(), d1)
+    d2 = 0.99 * dx + 1e-5 * max(np.abs(r2).max(), 1.0)
+    assert np.abs(g2 - r2).max() <= d2, (np.abs(g2 - r2).max(), d2)
