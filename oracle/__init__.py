@@ -44,7 +44,13 @@ class _Problem(C.Structure):
                 ("h", C.POINTER(C.c_double)), ("kh", C.c_int), ("kw", C.c_int),
                 ("sigma", C.c_double), ("alpha", C.c_double), ("eps", C.c_double),
                 ("lam", C.c_double), ("gamma", C.c_double), ("seed", C.c_uint64),
-                ("net", C.POINTER(_Net)), ("noise", C.c_int), ("mask", C.POINTER(C.c_double))]
+                ("net", C.POINTER(_Net)), ("noise", C.c_int), ("ddfb", C.c_void_p),
+                ("mask", C.POINTER(C.c_double))]
+
+
+class _Ddfb(C.Structure):
+    _fields_ = [("K", C.c_int), ("P", C.c_int), ("ks", C.c_int), ("w", C.POINTER(C.c_double)),
+                ("gamma", C.POINTER(C.c_double)), ("ht", C.c_double)]
 
 
 class _Poisson(C.Structure):
@@ -81,6 +87,9 @@ def lib():
         _lib.ora_kl_prox.restype = C.c_double
         _lib.ora_poisson_stepsizes.argtypes = [C.c_double] * 8 + [d] * 4
         _lib.ora_poisson_step.argtypes = [C.POINTER(_Poisson), d, d, d, u32, u32, d, d, d]
+        _lib.ora_ddfb_W.argtypes = [d, i, i, d, i, i, d]
+        _lib.ora_ddfb_Wt.argtypes = [d, i, i, d, i, i, d]
+        _lib.ora_ddfb_denoise.argtypes = [d, i, i, C.POINTER(_Ddfb), d]
     return _lib
 
 
@@ -191,8 +200,9 @@ class Problem:
     """Holds the FP64 arrays alive for the C struct."""
 
     def __init__(self, y, h, sigma, alpha, eps, lam, gamma, seed, net: Net | None = None,
-                 noise=True, mask=None):
-        """mask (0/1 array of y's shape): inpainting, H = diag(mask), h unused."""
+                 noise=True, mask=None, ddfb=None):
+        """mask (0/1 array of y's shape): inpainting, H = diag(mask), h unused.
+        ddfb (a Ddfb): the DDFB denoiser in place of the DnCNN-form net."""
         self.y = _f64(y)
         self.h = _f64(h if h is not None else np.ones((1, 1)))
         self.mask = _f64(mask) if mask is not None else None
@@ -202,7 +212,9 @@ class Problem:
                           float(eps), float(lam), float(gamma), C.c_uint64(seed),
                           C.pointer(net.s) if net is not None else C.POINTER(_Net)(),
                           int(bool(noise)),
+                          C.cast(C.pointer(ddfb.s), C.c_void_p) if ddfb is not None else None,
                           _dp(self.mask) if self.mask is not None else C.POINTER(C.c_double)())
+        self.ddfb = ddfb
 
     @property
     def shape(self):
@@ -300,3 +312,36 @@ def psnr(xhat, xbar):
     """PSNR with peak 1 on the unclipped estimate."""
     mse = float(np.mean((np.asarray(xhat, np.float64) - xbar) ** 2))
     return 10.0 * np.log10(1.0 / mse)
+
+
+class Ddfb:
+    """DDFB denoiser: w [K][P][ks][ks] analysis filters, gamma [K] steps, ht the
+    hard-tanh threshold."""
+
+    def __init__(self, w, gamma, ht):
+        self.w = _f64(w)
+        self.gamma = _f64(gamma)
+        self.K, self.P, self.ks = self.w.shape[0], self.w.shape[1], self.w.shape[2]
+        self.s = _Ddfb(self.K, self.P, self.ks, _dp(self.w), _dp(self.gamma), float(ht))
+
+
+def ddfb_W(v, wk):
+    """W_k v for one layer's filters wk [P][ks][ks] -> [P][ny][nx]."""
+    v, wk = _f64(v), _f64(wk)
+    u = np.empty((wk.shape[0],) + v.shape)
+    lib().ora_ddfb_W(_dp(v), v.shape[0], v.shape[1], _dp(wk), wk.shape[0], wk.shape[1], _dp(u))
+    return u
+
+
+def ddfb_Wt(u, wk):
+    u, wk = _f64(u), _f64(wk)
+    v = np.empty(u.shape[1:])
+    lib().ora_ddfb_Wt(_dp(u), u.shape[1], u.shape[2], _dp(wk), wk.shape[0], wk.shape[1], _dp(v))
+    return v
+
+
+def ddfb_denoise(v, net: Ddfb):
+    v = _f64(v)
+    out = np.empty_like(v)
+    lib().ora_ddfb_denoise(_dp(v), v.shape[0], v.shape[1], C.byref(net.s), _dp(out))
+    return out

@@ -255,7 +255,7 @@ void ora_langevin_step(const ora_problem* p, const double* x, uint32_t t, uint32
     const int64_t N = (int64_t)p->ny * p->nx;
     double* r = (double*)malloc(sizeof(double) * N);
     double* g = (double*)malloc(sizeof(double) * N);
-    double* d = p->net ? (double*)malloc(sizeof(double) * N) : NULL;
+    double* d = (p->net || p->ddfb) ? (double*)malloc(sizeof(double) * N) : NULL;
     double* xi = (double*)calloc(N, sizeof(double));
     if (p->mask) {
         for (int64_t n = 0; n < N; ++n) r[n] = p->mask[n] * x[n] - p->y[n];
@@ -265,7 +265,8 @@ void ora_langevin_step(const ora_problem* p, const double* x, uint32_t t, uint32
         for (int64_t n = 0; n < N; ++n) r[n] -= p->y[n];
         ora_blur_adj(r, p->ny, p->nx, p->h, p->kh, p->kw, g);
     }
-    if (d) ora_denoise(x, p->ny, p->nx, p->net, d);
+    if (d && p->net) ora_denoise(x, p->ny, p->nx, p->net, d);
+    else if (d) ora_ddfb_denoise(x, p->ny, p->nx, p->ddfb, d);
     if (p->noise) ora_normals(p->seed, t, chain, N, xi);
     const double gam = p->gamma;
     const double s2 = p->sigma * p->sigma;
@@ -421,4 +422,72 @@ void ora_moments_two_pass(const double* samples, int64_t n, int64_t npix,
         mean[j] = m;
         var[j] = n > 1 ? q / (double)(n - 1) : 0.0;
     }
+}
+
+/* ---------------------------------------------------------------------------
+ * DDFB denoiser (Sec. II-B, Example 2).
+ *   W_k v:    u_p(i,j) = sum_{a,b} w_k[p][a][b] v(i + a - r, j + b - r)
+ *   W_k^* u:  v(i,j)   = sum_p sum_{a,b} w_k[p][a][b] u_p(i - a + r, j - b + r)
+ * (r = ks / 2, zero outside the image), the exact adjoint of the first.
+ * ------------------------------------------------------------------------- */
+void ora_ddfb_W(const double* v, int ny, int nx, const double* wk, int P, int ks, double* u) {
+    const int r = ks / 2;
+    const int64_t plane = (int64_t)ny * nx;
+    for (int p = 0; p < P; ++p)
+        for (int i = 0; i < ny; ++i)
+            for (int j = 0; j < nx; ++j) {
+                double s = 0.0;
+                for (int a = 0; a < ks; ++a)
+                    for (int b = 0; b < ks; ++b) {
+                        const int ii = i + a - r, jj = j + b - r;
+                        if (ii < 0 || ii >= ny || jj < 0 || jj >= nx) continue;
+                        s += wk[(p * ks + a) * ks + b] * v[(int64_t)ii * nx + jj];
+                    }
+                u[p * plane + (int64_t)i * nx + j] = s;
+            }
+}
+
+void ora_ddfb_Wt(const double* u, int ny, int nx, const double* wk, int P, int ks, double* v) {
+    const int r = ks / 2;
+    const int64_t plane = (int64_t)ny * nx;
+    for (int i = 0; i < ny; ++i)
+        for (int j = 0; j < nx; ++j) {
+            double s = 0.0;
+            for (int p = 0; p < P; ++p)
+                for (int a = 0; a < ks; ++a)
+                    for (int b = 0; b < ks; ++b) {
+                        const int ii = i - a + r, jj = j - b + r;
+                        if (ii < 0 || ii >= ny || jj < 0 || jj >= nx) continue;
+                        s += wk[(p * ks + a) * ks + b] * u[p * plane + (int64_t)ii * nx + jj];
+                    }
+            v[(int64_t)i * nx + j] = s;
+        }
+}
+
+static double clip01(double v) { return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v); }
+
+void ora_ddfb_denoise(const double* v, int ny, int nx, const ora_ddfb* net, double* out) {
+    const int64_t plane = (int64_t)ny * nx;
+    const int K = net->K, P = net->P, ks = net->ks;
+    const int64_t wsz = (int64_t)P * ks * ks;
+    double* u = (double*)malloc(sizeof(double) * P * plane);
+    double* wu = (double*)malloc(sizeof(double) * P * plane);
+    double* s = (double*)malloc(sizeof(double) * plane);
+    /* dual variable initialised at W_K v */
+    ora_ddfb_W(v, ny, nx, net->w + (K - 1) * wsz, P, ks, u);
+    for (int k = 0; k < K - 1; ++k) {
+        const double* wk = net->w + k * wsz;
+        ora_ddfb_Wt(u, ny, nx, wk, P, ks, s);
+        for (int64_t n = 0; n < plane; ++n) s[n] = clip01(v[n] - s[n]);
+        ora_ddfb_W(s, ny, nx, wk, P, ks, wu);
+        for (int64_t n = 0; n < P * plane; ++n) {
+            const double a = u[n] + net->gamma[k] * wu[n];
+            u[n] = a < -net->ht ? -net->ht : (a > net->ht ? net->ht : a);
+        }
+    }
+    ora_ddfb_Wt(u, ny, nx, net->w + (K - 1) * wsz, P, ks, s);
+    for (int64_t n = 0; n < plane; ++n) out[n] = clip01(v[n] - net->gamma[K - 1] * s[n]);
+    free(u);
+    free(wu);
+    free(s);
 }

@@ -28,6 +28,14 @@
  *                          law; projection and linear-prior fixed points)
  *   ora_run_chain moments  pinned (two-pass vs Welford, stored samples)
  *   ora_stepsizes          pinned (Eq. 10 inequalities)
+ *   mask operator (inpainting) pinned (per-pixel closed form and stationary law,
+ *                          masked linear-prior fixed point)
+ *   ora_kl_prox, ora_normals_stream, ora_poisson_stepsizes, ora_poisson_step
+ *                          pinned (scalar minimisation, stream statistics, Eq. 12,
+ *                          augmented-objective fixed point)
+ *   ora_ddfb_W / ora_ddfb_Wt pinned (library conv2d / conv_transpose2d)
+ *   ora_ddfb_denoise       pinned (linear regime vs dense library operators;
+ *                          identity analysis operator -> clip(soft(v, ht), 0, 1))
  */
 #ifndef PNP_ORACLE_H
 #define PNP_ORACLE_H
@@ -61,6 +69,7 @@ typedef struct {
     uint64_t seed;           /* Philox key                                    */
     const ora_net* net;      /* NULL: no denoiser term                        */
     int noise;               /* 0: xi := 0 (deterministic recursion)          */
+    const struct ora_ddfb_s* ddfb;   /* DDFB denoiser (used when net is NULL)  */
     const double* mask;      /* NULL: H is the blur h; else H = diag(mask),
                                 mask[n] in {0, 1} (inpainting, Sec. IV-A)     */
 } ora_problem;
@@ -132,6 +141,23 @@ void ora_poisson_stepsizes(double hnorm, double eta, double rho1, double rho2, d
 /* One transition t -> t + 1: x by Eq. 13, then z by Eq. 14 from the new x. */
 void ora_poisson_step(const ora_poisson* p, const double* x, const double* z1, const double* z2,
                       uint32_t t, uint32_t chain, double* xnew, double* z1new, double* z2new);
+
+/* DDFB denoiser (Sec. II-B, Example 2): an unrolled dual forward-backward
+ * algorithm with K layers. W_k maps the image to P feature channels (a ks x ks
+ * cross-correlation with zero padding), W_k^* is its adjoint, gamma_k its step
+ * and HT the hard-tanh (clip to [-ht, ht]):
+ *   D(v) = proj_[0,1]( v - gamma_K W_K^* G(W_K v) ),  G = T_{K-1} o ... o T_1,
+ *   T_k(u) = HT( u + gamma_k W_k proj_[0,1](v - W_k^* u) ). */
+typedef struct ora_ddfb_s {
+    int K, P, ks;
+    const double* w;         /* [K][P][ks*ks]                                 */
+    const double* gamma;     /* [K]                                           */
+    double ht;               /* hard-tanh threshold                           */
+} ora_ddfb;
+
+void ora_ddfb_W(const double* v, int ny, int nx, const double* wk, int P, int ks, double* u);
+void ora_ddfb_Wt(const double* u, int ny, int nx, const double* wk, int P, int ks, double* v);
+void ora_ddfb_denoise(const double* v, int ny, int nx, const ora_ddfb* net, double* out);
 
 #ifdef __cplusplus
 }
