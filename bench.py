@@ -10,8 +10,13 @@ headline value is the BF16 denoiser form, with the FP32 plain form and the
 MMSE PSNR of both reported beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload deconv1024|deconv8192|deconv128|poisson1024|batch48|serve]
+                       [--workload deconv1024|deconv8192|deconv128|motion2048|motion4096|
+                                   inpaint1024|poisson1024|batch48|serve]
                        [--no-quality] [--jobs M]
+ddfb1024: the deconv1024 posterior with the DDFB denoiser (Sec. II-B, Example
+2: K = 4 unrolled dual forward-backward layers, P = 64 filters) in FP32.
+inpaint1024: Gaussian-noise inpainting (Sec. IV-A: H = diag(mask), 30 % of the
+pixels observed, 15 dB input SNR, x started at the cubic interpolant of y).
 poisson1024: the Poisson-noise sampler (Sec. IV-B: AXDA split, x-update with
 the coupling gradients, PSGLA updates of z1 and z2) on 1024 x 1024 counts at
 peak eta = 250, same blur and denoiser as deconv1024.
@@ -48,6 +53,10 @@ WORKLOADS = {
     "batch48": 4,      # 48 problems, sizes log-uniform 256..2048, blur/BSNR mix, BF16
     "serve": 5,        # Poisson arrivals (20/s), sizes {512..4096}^2, 200 + 800 iterations
     "poisson1024": 2,  # Poisson counts, eta = 250, rho1 = 10, rho2 = 1e-3; blur/denoiser of deconv1024
+    "inpaint1024": 2,  # 30 % observed pixels, 15 dB input SNR, spline start; denoiser of deconv1024
+    "ddfb1024": 2,     # the deconv1024 posterior with the DDFB prior (K=4, P=64), FP32
+    "motion2048": 6,   # 2048^2, 65x65 motion blur, 25 dB, K=8 F=64 (paper scale)
+    "motion4096": 7,   # 4096^2, 129x129 motion blur, 25 dB, K=8 F=64 (paper scale)
 }
 POISSON = dict(eta=250.0, rho1=10.0, rho2=1e-3)
 
@@ -171,8 +180,27 @@ def replica_rate(pix_iters, seconds, ws, device="cuda"):
     return tot / slow / 1e6, slow
 
 
-def _oracle_setup(cfg_id, crop, poisson=False):
+def inpainting_problem(rank=0):
+    w = synth.WORKLOADS[2]
+    return synth.make_inpainting_problem(w["ny"], w["nx"], 0.3, 15.0, synth.gt_seed(2, rank) + 50)
+
+
+def ddfb_net(P_=None):
+    dd = synth.ddfb_weights(4, 64, 11)
+    return dd
+
+
+def _oracle_setup(cfg_id, crop, poisson=False, inpaint=False, ddfb=False):
     import oracle
+    if inpaint:
+        prob = inpainting_problem()
+        dw = synth.workload_denoiser(cfg_id)
+        crop = min(crop, prob.shape[0], prob.shape[1])
+        lam, gam = oracle.stepsizes(1.0, prob.sigma, 1.0, prob.sigma, dw.lipschitz)
+        op = oracle.Problem(prob.y[:crop, :crop], None, prob.sigma, 1.0, prob.sigma, lam, gam,
+                            prob.seed, net=oracle.Net.from_weights(dw),
+                            mask=prob.mask[:crop, :crop])
+        return oracle, prob, op, crop
     if poisson:
         prob = poisson_problem()
         dw = synth.workload_denoiser(cfg_id)
@@ -192,10 +220,17 @@ def _oracle_setup(cfg_id, crop, poisson=False):
     else:
         prob = synth.workload_problem(cfg_id)
     dw = synth.workload_denoiser(cfg_id)
-    crop = min(crop, prob.shape[0], prob.shape[1])
+    # the crop holds at least two kernel widths (the paper's 129 x 129 blur)
+    crop = min(max(crop, 2 * prob.h.shape[0]), prob.shape[0], prob.shape[1])
     y = prob.y[:crop, :crop]
     lam, gam = oracle.stepsizes(float(np.abs(prob.h).sum()), prob.sigma, 1.0, prob.sigma,
                                 dw.lipschitz)
+    if ddfb:
+        dd = ddfb_net()
+        lam, gam = oracle.stepsizes(float(np.abs(prob.h).sum()), prob.sigma, 1.0, prob.sigma, 1.0)
+        op = oracle.Problem(y, prob.h, prob.sigma, 1.0, prob.sigma, lam, gam, prob.seed,
+                            ddfb=oracle.Ddfb(dd.filters, dd.gammas, dd.ht))
+        return oracle, prob, op, crop
     op = oracle.Problem(y, prob.h, prob.sigma, 1.0, prob.sigma, lam, gam, prob.seed,
                         net=oracle.Net.from_weights(dw))
     return oracle, prob, op, crop
@@ -205,9 +240,9 @@ class _OracleChain:
     """One oracle iteration at a time on the crop: the Gaussian x-update, or
     the Poisson x-update followed by the z-updates."""
 
-    def __init__(self, oracle, op, crop, poisson):
+    def __init__(self, oracle, op, crop, poisson, x0=None):
         self.o, self.op, self.poisson = oracle, op, poisson
-        self.x = np.zeros((crop, crop))
+        self.x = np.zeros((crop, crop)) if x0 is None else np.array(x0[:crop, :crop], np.float64)
         self.z1 = np.zeros((crop, crop))
         self.z2 = np.zeros((crop, crop))
 
@@ -218,13 +253,13 @@ class _OracleChain:
             self.x = self.o.langevin_step(self.op, self.x, t)
 
 
-def oracle_baseline(cfg_id, budget_s=20.0, crop=128, poisson=False):
+def oracle_baseline(cfg_id, budget_s=20.0, crop=128, poisson=False, inpaint=False, ddfb=False):
     """The FP64 oracle as it stands, on a bounded sample of the workload:
     whole iterations on a crop of the image (same blur, noise level and
     network), on this host's cores."""
-    oracle, prob, op, crop = _oracle_setup(cfg_id, crop, poisson)
+    oracle, prob, op, crop = _oracle_setup(cfg_id, crop, poisson, inpaint, ddfb)
     ny, nx = prob.shape
-    ch = _OracleChain(oracle, op, crop, poisson)
+    ch = _OracleChain(oracle, op, crop, poisson, prob.x0 if inpaint else None)
     t0 = time.perf_counter()
     it = 0
     while True:
@@ -251,8 +286,10 @@ def run_reference(args):
     n = args.warmup + steps
     crop = 128 if n <= 60 else (64 if n <= 250 else 32)
     poisson = args.workload == "poisson1024"
-    oracle, prob, op, crop = _oracle_setup(cfg_id, crop, poisson)
-    ch = _OracleChain(oracle, op, crop, poisson)
+    inpaint = args.workload == "inpaint1024"
+    oracle, prob, op, crop = _oracle_setup(cfg_id, crop, poisson, inpaint,
+                                           args.workload == "ddfb1024")
+    ch = _OracleChain(oracle, op, crop, poisson, prob.x0 if inpaint else None)
     for it in range(args.warmup):
         ch.step(it)
     t0 = time.perf_counter()
@@ -266,7 +303,7 @@ def run_reference(args):
     line = dict(metric=METRIC, value=val, unit=UNIT, n_gpus=args.gpus, steps=steps,
                 warmup=args.warmup, ms_per_step=1e3 * dt / steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload=f"{args.workload if poisson else w['name']} "
+                config=dict(workload=f"{args.workload if poisson or inpaint or args.workload == 'ddfb1024' else w['name']} "
                                      "(oracle, bounded crop sample)"),
                 cpu_baseline=dict(kind="oracle", cores=cores, sample=sample, value=val, unit=UNIT),
                 e2e=dict(value=val, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
@@ -499,9 +536,16 @@ def main():
     cfg_id = WORKLOADS[args.workload]
     w = synth.WORKLOADS[cfg_id]
     poisson = args.workload == "poisson1024"
-    prob = poisson_problem(rank) if poisson else synth.workload_problem(cfg_id, job=rank)
+    inpaint = args.workload == "inpaint1024"
+    prob = (poisson_problem(rank) if poisson else inpainting_problem(rank) if inpaint
+            else synth.workload_problem(cfg_id, job=rank))
     dw = synth.workload_denoiser(cfg_id)
-    den = P.Denoiser.from_weights(dw)
+    ddfb = args.workload == "ddfb1024"
+    if ddfb:
+        dd = ddfb_net()
+        den = P.Denoiser.ddfb(dd.filters, dd.gammas, dd.ht)
+    else:
+        den = P.Denoiser.from_weights(dw)
     ny, nx = prob.shape
     npix = ny * nx
     # a dedicated stream: the problems enqueue on it and the events are recorded on it
@@ -509,7 +553,7 @@ def main():
     torch.cuda.set_stream(stream)
     peaks = load_peaks()
     precs = [p for p in args.precisions.split(",") if p]
-    if w["F"] != 64:
+    if w["F"] != 64 or ddfb:
         precs = ["fp32"]
 
     def barrier():
@@ -521,6 +565,8 @@ def main():
         if poisson:
             return P.Problem(prob.y, prob.h, 0.0, den, noise_model="poisson", eta=prob.eta,
                              rho1=POISSON["rho1"], rho2=POISSON["rho2"], **kw)
+        if inpaint:
+            return P.Problem(prob.y, None, prob.sigma, den, mask=prob.mask, x0=prob.x0, **kw)
         return P.Problem(prob.y, prob.h, prob.sigma, den, **kw)
 
     results = {}
@@ -573,17 +619,16 @@ def main():
     e2e_rate, t_e2e = replica_rate(npix * args.steps, time.perf_counter() - t0, ws)
     gp.close()
     e2e = dict(value=e2e_rate, unit=UNIT,
-               h2d_bytes_per_step=(prob.y.size * 4 + prob.h.size * 4) / args.steps,
+               h2d_bytes_per_step=(prob.y.size * 4 + (prob.mask.size * 4 + prob.x0.size * 4 if inpaint
+                                                       else prob.h.size * 4)) / args.steps,
                d2h_bytes_per_step=2 * npix * 8 / args.steps)
 
     # quality at equal PSNR: the full chain of the workload for each precision
     quality = None
-    if not args.no_quality and rank == 0 and cfg_id != 3 and not poisson:
+    if not args.no_quality and rank == 0 and cfg_id in (1, 2):
         quality = {}
         for prec in precs:
-            gq = P.Problem(prob.y, prob.h, prob.sigma, den, blocks=w["blocks"], halo=0,
-                           seed=prob.seed, burn_in=w["burn_in"], precision=prec,
-                           stream=stream.cuda_stream)
+            gq = make_problem(prec, w["burn_in"])
             gq.run_chain(w["T"], w["burn_in"])
             mq, _, _ = gq.moments()
             quality[f"psnr_{prec}_db"] = round(10 * math.log10(1.0 / float(np.mean((mq - prob.xbar) ** 2))), 4)
@@ -613,6 +658,16 @@ def main():
                     frac=round(achieved / pk, 4), traffic=ncu_traffic(ktag, args.workload, precs[0]),
                     kernel=ktag, peak_kind=f"{precs[0]} sustained ({peaks['src']}"
                                                   + (", bf16 x nominal ratio 2)" if precs[0] == "fp8" else ")"))
+    elif ddfb:
+        # dual layers stream the P-channel dual variable: the first writes it
+        # (reads v), the others read and write it; bytes averaged over the
+        # K - 1 launches the timer covers
+        Kd, Pd = 4, 64
+        bpp = ((4 + 4 * Pd) + (Kd - 2) * (4 + 8 * Pd)) / (Kd - 1)
+        gbs = bpp * pix_per_launch / (kern["avg_ms"] * 1e-3) / 1e9
+        roof = dict(bound="hbm", achieved=round(gbs, 1), peak=peaks["hbm"], unit="GB/s",
+                    frac=round(gbs / peaks["hbm"], 4), traffic=None, kernel="k_ddfb<64,0|1>",
+                    bytes_per_pixel=round(bpp, 1), peak_kind=f"HBM copy ({peaks['src']})")
     else:
         flop = 2.0 * F * F * 9 * pix_per_launch
         achieved = flop / (kern["avg_ms"] * 1e-3) / 1e12
@@ -632,6 +687,13 @@ def main():
             gbs = bpp * npix / (avg * 1e-3) / 1e9
             stencils[kname] = dict(avg_us=round(avg * 1e3, 2), bytes_per_pixel=bpp,
                                    achieved_gbs=round(gbs, 1), frac=round(gbs / peaks["hbm"], 4))
+            if not poisson and not inpaint and max(prob.h.shape) > 31 and kname != "zupdate":
+                # wide stencil: 2 FLOP per nonzero tap and pixel against the FFMA peak
+                nnz = int(np.count_nonzero(prob.h.astype(np.float32)))
+                tf = 2.0 * nnz * npix / (avg * 1e-3) / 1e12
+                alu = 148 * 128 * 2 * peaks["sm_max"] / 1e6
+                stencils[kname].update(nonzero_taps=nnz, achieved_tflops=round(tf, 2),
+                                       alu_frac=round(tf / alu, 4), alu_peak_tflops=round(alu, 1))
     if stencils:
         stencils["peak_gbs"] = peaks["hbm"]
         stencils["peak_kind"] = f"HBM copy ({peaks['src']})"
@@ -642,7 +704,7 @@ def main():
     cpu = None
     if not args.no_cpu_baseline:
         try:
-            cpu = oracle_baseline(cfg_id, budget_s=15.0, poisson=poisson)
+            cpu = oracle_baseline(cfg_id, budget_s=15.0, poisson=poisson, inpaint=inpaint, ddfb=ddfb)
         except Exception as ex:  # report, never fake
             cpu = dict(value=None, unit=UNIT, cores=None, kind="oracle", sample=f"failed: {ex}")
     line = dict(
@@ -652,11 +714,18 @@ def main():
         data="synthetic",
         config=dict(workload=(f"poisson1024: {ny}x{nx} Poisson counts, peak eta={prob.eta:g}, "
                               f"rho1={POISSON['rho1']:g}, rho2={POISSON['rho2']:g}, AXDA + PSGLA, "
+                              f"blur {w['blur'][0]} {w['blur'][1]}x{w['blur'][1]}, "
                               if poisson else
-                              f"{w['name']}: {ny}x{nx} grayscale, {w['bsnr']} dB BSNR, ")
-                             + f"blur {w['blur'][0]} "
-                             f"{w['blur'][1]}x{w['blur'][1]}, DnCNN-form "
-                             f"K={K} F={F}, {w['blocks'][0]}x{w['blocks'][1]} blocks "
+                              f"inpaint1024: {ny}x{nx} grayscale, 30 % of the pixels observed, "
+                              "15 dB input SNR, cubic-interpolant start, "
+                              if inpaint else
+                              f"ddfb1024: {ny}x{nx} grayscale, {w['bsnr']} dB BSNR, DDFB prior "
+                              f"K=4 P=64 (FP32), blur {w['blur'][0]} {w['blur'][1]}x{w['blur'][1]}, "
+                              if ddfb else
+                              f"{w['name']}: {ny}x{nx} grayscale, {w['bsnr']} dB BSNR, "
+                              f"blur {w['blur'][0]} {w['blur'][1]}x{w['blur'][1]}, ")
+                             + ("" if ddfb else f"DnCNN-form K={K} F={F}, ")
+                             + f"{w['blocks'][0]}x{w['blocks'][1]} blocks "
                              f"(halo-exchange-free), 1 chain per GPU",
                     precision=precs[0], l2="working set per step > 126 MB L2 (activation planes)",
                     graph="one CUDA graph per iteration"),

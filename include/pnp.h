@@ -187,6 +187,20 @@ pnp_status pnp_finalize_moments(const float* mean, const float* m2, int64_t npix
                                 int64_t n_kept, int want_var, double* mmse, double* out2,
                                 void* stream);
 
+/* DDFB denoiser (Sec. II-B, Example 2): an unrolled dual forward-backward
+ * algorithm with K layers, each with P analysis filters W_k (1 -> P channel
+ * 3 x 3 cross-correlation, zero padding) and its adjoint W_k^*:
+ *   u_0 = W_K v,
+ *   u_k = HT(u_{k-1} + gamma_k W_k proj_[0,1](v - W_k^* u_{k-1})),  k = 1 .. K-1,
+ *   D(v) = proj_[0,1](v - gamma_K W_K^* u_{K-1}),
+ * HT = clip to [-ht, ht]. filters: host [K][P][3][3], gammas: host [K] (> 0);
+ * both copied. 2 <= K <= 32, P in {16, 32, 64}, ht > 0. The result is a
+ * pnp_denoiser for pnp_denoise / problems with PNP_FP32 and halo = 0 (its
+ * FP32 kernels stream the P-channel dual variable; other precisions give
+ * PNP_ENOTSUP). Its L_eps for the step sizes is 1 (Id - D is nonexpansive). */
+pnp_status pnp_create_ddfb(int K, int P, const float* filters, const float* gammas, double ht,
+                           pnp_denoiser** out);
+
 /* Step sizes of the Gaussian-noise setting (Eq. 10 with H_2 = 0):
  * L = hnorm^2/sigma^2, lambda = 0.99 / (4L + 2 alpha L_eps / eps^2),
  * gamma = c / (3 (L + alpha L_eps / eps^2 + 1/lambda)), 0 < c < 1. */

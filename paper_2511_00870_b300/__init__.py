@@ -156,6 +156,19 @@ class Denoiser:
     def from_weights(cls, dw):
         return cls(dw.weights, dw.biases, dw.lipschitz)
 
+    @classmethod
+    def ddfb(cls, filters, gammas, ht):
+        """DDFB denoiser (pnp_create_ddfb): filters [K][P][3][3], gammas [K], ht > 0."""
+        f = np.ascontiguousarray(filters, dtype=np.float32)
+        g = np.ascontiguousarray(gammas, dtype=np.float32)
+        obj = cls.__new__(cls)
+        obj.K, obj.F = int(f.shape[0]), int(f.shape[1])
+        h = C.c_void_p()
+        check(load().pnp_create_ddfb(obj.K, obj.F, _f32p(f), _f32p(g), float(ht), C.byref(h)))
+        obj.handle = h
+        obj.lipschitz = 1.0
+        return obj
+
     def denoise(self, x, out=None, precision="fp32", blocks=(1, 1), halo=0, stream=None):
         """pnp_denoise on x [n, ny, nx] (CUDA float32)."""
         import torch

@@ -52,6 +52,7 @@ SIGNATURES = {
     "pnp_version": ([], C.c_char_p),
     "pnp_create_denoiser": ([i32, i32, fp, fp, f64, C.POINTER(vp)], i32),
     "pnp_destroy_denoiser": ([vp], None),
+    "pnp_create_ddfb": ([i32, i32, fp, fp, f64, C.POINTER(vp)], i32),
     "pnp_denoiser_calibrate_fp8": ([vp, vp, i32, i32, i32, vp], i32),
     "pnp_blur": ([vp, vp, vp, i32, i32, i32, i32, i32, vp, vp], i32),
     "pnp_blur_adjoint": ([vp, vp, i32, i32, i32, i32, i32, f32, vp, vp], i32),

@@ -325,9 +325,38 @@ extern "C" pnp_status pnp_create_denoiser(int K, int F, const float* weights, co
     return PNP_OK;
 }
 
+extern "C" pnp_status pnp_create_ddfb(int K, int P, const float* filters, const float* gammas,
+                                      double ht, pnp_denoiser** out) {
+    if (!out) return fail(PNP_EINVAL, "pnp_create_ddfb: out is NULL");
+    *out = nullptr;
+    if (K < 2 || K > 32 || !(P == 16 || P == 32 || P == 64) || !filters || !gammas ||
+        !(ht > 0) || !std::isfinite(ht))
+        return fail(PNP_EINVAL, "pnp_create_ddfb: need 2 <= K <= 32, P in {16,32,64}, filters, "
+                                "gammas and ht > 0");
+    for (int i = 0; i < K * P * 9; ++i)
+        if (!std::isfinite(filters[i])) return fail(PNP_EINVAL, "pnp_create_ddfb: filters not finite");
+    for (int k = 0; k < K; ++k)
+        if (!(gammas[k] > 0) || !std::isfinite(gammas[k]))
+            return fail(PNP_EINVAL, "pnp_create_ddfb: gammas must be > 0");
+    pnp_denoiser* den = new pnp_denoiser();
+    DenoiserDev& D = den->dev;
+    cudaGetDevice(&den->device);
+    D.K = K;
+    D.F = P;
+    D.lip = 1.0;   // D is a (relaxed) proximity operator: Id - D is nonexpansive
+    D.ddfb = true;
+    D.ddfb_w = new float[(size_t)K * P * 9];
+    memcpy(D.ddfb_w, filters, sizeof(float) * K * P * 9);
+    for (int k = 0; k < K; ++k) D.ddfb_gamma[k] = gammas[k];
+    D.ddfb_ht = (float)ht;
+    *out = den;
+    return PNP_OK;
+}
+
 extern "C" void pnp_destroy_denoiser(pnp_denoiser* den) {
     if (!den) return;
     DenoiserDev& D = den->dev;
+    delete[] D.ddfb_w;
     dfree(D.w32);
     dfree(D.b32);
     dfree(D.wtc);
@@ -350,8 +379,8 @@ static pnp_status check_blur_args(const void* x, const void* h, int kh, int kw, 
                                   int nimg, const void* out, const char* who) {
     if (!x || !h || !out) return fail(PNP_EINVAL, std::string(who) + ": NULL pointer");
     if (ny < 1 || nx < 1 || nimg < 1) return fail(PNP_EINVAL, std::string(who) + ": empty image");
-    if (kh < 1 || kw < 1 || !(kh & 1) || !(kw & 1) || kh > 31 || kw > 31)
-        return fail(PNP_EINVAL, std::string(who) + ": kernel sizes must be odd and <= 31");
+    if (kh < 1 || kw < 1 || !(kh & 1) || !(kw & 1) || kh > WIDE_MAXK || kw > WIDE_MAXK)
+        return fail(PNP_EINVAL, std::string(who) + ": kernel sizes must be odd and <= 129");
     if (kh > ny || kw > nx)
         return fail(PNP_EINVAL, std::string(who) + ": kernel larger than the image");
     return PNP_OK;
@@ -413,6 +442,10 @@ static pnp_status check_denoise_args(const pnp_denoiser* den, pnp_precision prec
     if (ny < 1 || nx < 1 || nimg < 1) return fail(PNP_EINVAL, "empty image");
     if (prec != PNP_FP32 && prec != PNP_BF16 && prec != PNP_FP8)
         return fail(PNP_ENOTSUP, "unknown precision");
+    if (den->dev.ddfb && prec != PNP_FP32)
+        return fail(PNP_ENOTSUP, "the DDFB denoiser runs in FP32");
+    if (den->dev.ddfb && halo > 0)
+        return fail(PNP_EINVAL, "the DDFB denoiser uses the direct layout (halo = 0)");
     if (prec != PNP_FP32 && den->dev.F != 64) return fail(PNP_EINVAL, "BF16/FP8 paths need F = 64");
     if (halo < 0) return fail(PNP_EINVAL, "halo must be >= 0");
     if (halo > 0 && (by < 1 || bx < 1 || by > ny || bx > nx))
@@ -548,6 +581,8 @@ static pnp_status fill_update_params(UpdateParams& u, float* x, const float* r, 
     u.hsep = nullptr;
     u.z2 = nullptr;
     u.c_z2 = 0.f;
+    u.wtaps = nullptr;
+    u.nwtaps = 0;
     return PNP_OK;
 }
 
@@ -608,7 +643,8 @@ extern "C" void pnp_destroy_problem(pnp_problem* p) {
     for (void* q : {(void*)p->y, (void*)p->h, (void*)p->x, (void*)p->r, (void*)p->d,
                     (void*)p->mean, (void*)p->m2, (void*)p->blocks, (void*)p->tiles,
                     (void*)p->dtiles, (void*)p->rects, p->scratch, (void*)p->st,
-                    (void*)p->hsep, (void*)p->z1, (void*)p->z2})
+                    (void*)p->hsep, (void*)p->z1, (void*)p->z2, (void*)p->wt_fwd,
+                    (void*)p->wt_adj})
         dfree(q);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
     delete p;
@@ -616,15 +652,23 @@ extern "C" void pnp_destroy_problem(pnp_problem* p) {
 
 namespace pnp {
 
+// Poisson: r = eta H x - z1 for the current state. The z-update of every
+// iteration writes it for the next one (it has eta H x+ at hand), so an
+// iteration launches no blur; this refresh runs only when the host changes x
+// or z1 (creation, pnp_set_state, pnp_set_aux_state).
+static pnp_status poisson_refresh_r(pnp_problem* p) {
+    PNP_CUDA_TRY(launch_blur(p->x, p->z1, p->h, p->kh, p->kw, p->ny, p->nx, p->nchain, p->r,
+                             p->stream, p->blur_tile, p->hsep, (float)p->eta, p->N));
+    return PNP_OK;
+}
+
 pnp_status problem_pre(pnp_problem* p, cudaStream_t s) {
     if (p->inpaint) return PNP_OK;   // H = diag(mask): the update forms x - y itself
     if (p->poisson) {
-        // r = eta H x - z1 (per chain)
-        PNP_CUDA_TRY(launch_blur(p->x, p->z1, p->h, p->kh, p->kw, p->ny, p->nx, p->nchain, p->r, s,
-                                 p->blur_tile, p->hsep, (float)p->eta, p->N));
+        return PNP_OK;               // r = eta H x - z1 was written by the last z-update
     } else {
         PNP_CUDA_TRY(launch_blur(p->x, p->y, p->h, p->kh, p->kw, p->ny, p->nx, p->nchain, p->r, s,
-                                 p->blur_tile, p->hsep));
+                                 p->blur_tile, p->hsep, 1.0f, 0, p->wt_fwd, p->nwt));
     }
     return PNP_OK;
 }
@@ -647,6 +691,8 @@ static pnp_status problem_update_params(const pnp_problem* p, UpdateParams& u) {
     u.d_residual = p->prec != PNP_FP32;   // the tensor-core denoisers hand over G = x - D(x)
     u.tile = p->update_tile;
     u.hsep = p->hsep;
+    u.wtaps = p->wt_adj;
+    u.nwtaps = p->nwt;
     if (p->poisson) {
         u.inv_s2 = (float)(p->eta / p->rho1);
         u.z2 = p->z2;
@@ -682,6 +728,7 @@ static ZParams problem_z_params(const pnp_problem* p) {
     z.t_dev = &p->st->t;
     z.arrive = &p->st->arrive;
     z.tile = p->update_tile;
+    z.r_out = p->r;
     return z;
 }
 
@@ -791,6 +838,8 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
     if (q.noise_model != PNP_GAUSSIAN && !poisson) return fail(PNP_EINVAL, "unknown noise model");
     if (!poisson && (!(q.sigma > 0) || !std::isfinite(q.sigma)))
         return fail(PNP_EINVAL, "sigma must be > 0");
+    if (poisson && is_wide(q.kh, q.kw))
+        return fail(PNP_ENOTSUP, "Poisson model: blur kernels up to 31 x 31");
     if (poisson) {
         if (!(q.eta > 0) || !(q.rho1 > 0) || !(q.rho2 > 0) || !std::isfinite(q.eta) ||
             !std::isfinite(q.rho1) || !std::isfinite(q.rho2))
@@ -806,6 +855,10 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
         return fail(PNP_EINVAL, "halo must cover the receptive field (halo >= K)");
     if (q.precision != PNP_FP32 && q.precision != PNP_BF16 && q.precision != PNP_FP8)
         return fail(PNP_ENOTSUP, "unknown precision");
+    if (q.D && q.D->dev.ddfb && q.precision != PNP_FP32)
+        return fail(PNP_ENOTSUP, "the DDFB denoiser runs in FP32");
+    if (q.D && q.D->dev.ddfb && q.halo > 0)
+        return fail(PNP_EINVAL, "the DDFB denoiser uses the direct layout (halo = 0)");
     if (q.D && q.precision != PNP_FP32 && q.D->dev.F != 64)
         return fail(PNP_EINVAL, "BF16/FP8 denoiser needs F = 64");
     const int64_t N = (int64_t)q.ny * q.nx;
@@ -945,9 +998,22 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
         cudaMemcpy(p->y, q.y, N * 4, cudaMemcpyHostToDevice);
     }
     cudaMemcpy(p->h, q.h, (size_t)q.kh * q.kw * 4, cudaMemcpyHostToDevice);
+    if (is_wide(q.kh, q.kw)) {
+        // large kernel: nonzero taps as window offsets, forward and adjoint
+        const std::vector<WTap> f = wide_taps(q.h, q.kh, q.kw, false);
+        const std::vector<WTap> a = wide_taps(q.h, q.kh, q.kw, true);
+        p->nwt = (int)f.size();
+        const size_t nt = std::max<size_t>(f.size(), 1);
+        if ((st = dalloc(&p->wt_fwd, nt)) != PNP_OK || (st = dalloc(&p->wt_adj, nt)) != PNP_OK) {
+            pnp_destroy_problem(p);
+            return st;
+        }
+        cudaMemcpy(p->wt_fwd, f.data(), f.size() * sizeof(WTap), cudaMemcpyHostToDevice);
+        cudaMemcpy(p->wt_adj, a.data(), a.size() * sizeof(WTap), cudaMemcpyHostToDevice);
+    }
     {
         std::vector<float> sep;
-        if (separable_taps(q.h, q.kh, q.kw, sep)) {
+        if (!is_wide(q.kh, q.kw) && separable_taps(q.h, q.kh, q.kw, sep)) {
             if ((st = dalloc(&p->hsep, sep.size())) != PNP_OK) {
                 pnp_destroy_problem(p);
                 return st;
@@ -964,7 +1030,7 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
         cudaMemset(p->m2, 0, NC * 4);
         UpdateParams u;
         pnp_status us = problem_update_params(p, u);
-        if (us == PNP_OK && !inpaint) {
+        if (us == PNP_OK && !inpaint && !is_wide(q.kh, q.kw)) {
             u.t_dev = nullptr;
             u.burn_dev = nullptr;
             u.arrive = nullptr;
@@ -1009,6 +1075,13 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
         if (cs != PNP_OK) {
             pnp_destroy_problem(p);
             return cs;
+        }
+    }
+    if (poisson) {
+        pnp_status rs = poisson_refresh_r(p);
+        if (rs != PNP_OK) {
+            pnp_destroy_problem(p);
+            return rs;
         }
     }
     cudaError_t e = cudaDeviceSynchronize();
@@ -1182,6 +1255,7 @@ extern "C" pnp_status pnp_set_state(pnp_problem* p, const float* x, int64_t t) {
     }
     StepState s0{(uint32_t)t, (int32_t)p->burn_in, 0u};
     PNP_CUDA_TRY(cudaMemcpyAsync(p->st, &s0, sizeof(s0), cudaMemcpyHostToDevice, p->stream));
+    if (p->poisson && x) PNP_TRY(poisson_refresh_r(p));
     PNP_CUDA_TRY(cudaStreamSynchronize(p->stream));
     p->t = t;
     return PNP_OK;
@@ -1201,6 +1275,7 @@ extern "C" pnp_status pnp_set_aux_state(pnp_problem* p, const float* z1, const f
     const size_t bytes = (size_t)p->N * p->nchain * 4;
     if (z1) PNP_CUDA_TRY(cudaMemcpyAsync(p->z1, z1, bytes, cudaMemcpyHostToDevice, p->stream));
     if (z2) PNP_CUDA_TRY(cudaMemcpyAsync(p->z2, z2, bytes, cudaMemcpyHostToDevice, p->stream));
+    if (z1) PNP_TRY(poisson_refresh_r(p));
     PNP_CUDA_TRY(cudaStreamSynchronize(p->stream));
     return PNP_OK;
 }

@@ -293,6 +293,7 @@ size_t denoise_fp32_scratch(const DenoiserDev& D, int ny, int nx, int nimg) {
 
 cudaError_t denoise_fp32(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
                          const Rect* rects, float* d, float* scratch, cudaStream_t s) {
+    if (D.ddfb) return ddfb_forward(D, x, ny, nx, nimg, rects, d, scratch, s);
     switch (D.F) {
         case 16: return denoise_fp32_F<16>(D, x, ny, nx, nimg, rects, d, scratch, s);
         case 32: return denoise_fp32_F<32>(D, x, ny, nx, nimg, rects, d, scratch, s);

@@ -493,8 +493,9 @@ __global__ void __launch_bounds__(256) k_update(UpdateParams p) {
 // root of u^2 + (kappa - v) u - kappa y = 0, evaluated as (a + s) / 2 for
 // a = v - kappa >= 0 and as 2 kappa y / (s - a) otherwise (s = sqrt(a^2 + 4
 // kappa y)), which avoids the cancellation of the first form for a < 0. With
-// `arrive` set, the last block advances the step counter (this is the last
-// kernel of a Poisson iteration).
+// r_out set it also writes the next iteration's residual eta H x+ - z1+ (the
+// iteration then needs no blur launch). With `arrive` set, the last block
+// advances the step counter (this is the last kernel of a Poisson iteration).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float kl_prox(float v, float y, float kappa) {
     const float a = v - kappa;
@@ -541,7 +542,9 @@ __global__ void __launch_bounds__(256) k_zupdate(ZParams p) {
                 const float w = p.eta * hx[o][q];
                 const float z1 = z1c[n];
                 const float v1 = z1 - p.a1 * (z1 - w) + p.s1 * e1[q];
-                z1c[n] = kl_prox(v1, __ldg(p.y + n), p.kappa1);
+                const float z1n = kl_prox(v1, __ldg(p.y + n), p.kappa1);
+                z1c[n] = z1n;
+                if (p.r_out) p.r_out[chain * plane + n] = w - z1n;
                 const float z2 = z2c[n];
                 const float v2 = z2 - p.a2 * (z2 - __ldg(xc + n)) + p.s2 * e2[q];
                 z2c[n] = fmaxf(v2, 0.f);
@@ -639,6 +642,245 @@ __global__ void __launch_bounds__(256) k_update_mask(UpdateParams p) {
             }
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Wide stencil for large kernels (up to 129 x 129). A block of 32 x 8 threads
+// owns a 64-row x 128-column output tile; the window (64 + kh + 2) x (128 +
+// kw - 1) is filled once with circular wrap (195 KB at 129 x 129). Thread (tx,
+// ty) accumulates rows 8 ty .. 8 ty + 7 at columns tx + 32 q (q = 0..3): for a
+// fixed offset the 32 lanes of a warp read 32 consecutive window words, so the
+// loads are free of bank conflicts for any pitch. Taps come in groups of four
+// on consecutive rows of one window column: a thread loads the 8 + 3 window
+// values of a column once and applies all four taps to its 8 rows (32
+// multiply-adds per 11 shared-memory loads instead of one per load, the
+// shared-memory pipe being the bound). Only groups holding a nonzero tap are
+// visited (a motion blur of length L has O(L) of its L^2 entries). Sums run
+// over window columns in order, rows ascending; the operator entry points pass
+// no group list and the kernel walks h in groups of four rows itself, in the
+// same order (zero taps add exactly nothing), so both give the same sums.
+// ---------------------------------------------------------------------------
+constexpr int WD_TW = 128, WD_R = 8, WD_BY = 8, WD_TR = WD_R * WD_BY;
+
+static size_t wide_smem(int kh, int kw) {
+    return sizeof(float) * (size_t)(WD_TR + kh + 2) * (WD_TW + kw - 1);
+}
+
+__device__ __forceinline__ void wide_tile(const float* __restrict__ img, int ny, int nx, int i0,
+                                          int j0, int kh, int kw, const WTap* __restrict__ taps,
+                                          int ntaps, const float* __restrict__ h, bool adjoint,
+                                          float* win, float acc[WD_R][4]) {
+    const int ay = kh >> 1, ax = kw >> 1;
+    const int wy = WD_TR + kh + 2, wp = WD_TW + kw - 1;   // + 3 rows read by the last group
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int it = tid; it < wy * wp; it += 256) {
+        const int r = it / wp, c = it - r * wp;
+        int gi = (i0 - ay + r) % ny;
+        if (gi < 0) gi += ny;
+        int gj = (j0 - ax + c) % nx;
+        if (gj < 0) gj += nx;
+        win[it] = __ldg(img + (int64_t)gi * nx + gj);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int o = 0; o < WD_R; ++o)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[o][q] = 0.f;
+    const float* base = win + threadIdx.y * WD_R * wp + threadIdx.x;
+    auto group = [&](int off, float w0, float w1, float w2, float w3) {
+        const float* b = base + off;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float v[WD_R + 3];
+#pragma unroll
+            for (int o = 0; o < WD_R + 3; ++o) v[o] = b[o * wp + 32 * q];
+#pragma unroll
+            for (int o = 0; o < WD_R; ++o) {
+                float s = acc[o][q];
+                s = fmaf(w0, v[o], s);
+                s = fmaf(w1, v[o + 1], s);
+                s = fmaf(w2, v[o + 2], s);
+                s = fmaf(w3, v[o + 3], s);
+                acc[o][q] = s;
+            }
+        }
+    };
+    if (taps) {
+        for (int k = 0; k < ntaps; ++k) {
+            const float4 w = __ldg(reinterpret_cast<const float4*>(taps[k].w));
+            group(__ldg(&taps[k].off), w.x, w.y, w.z, w.w);
+        }
+    } else {
+        // window row wr, column wc hold tap (wr, wc) of the adjoint and tap
+        // (2 ay - wr, 2 ax - wc) of the forward operator
+        for (int wc = 0; wc < kw; ++wc)
+            for (int r0 = 0; r0 < kh; r0 += 4) {
+                float w[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int wr = r0 + t;
+                    const int a = adjoint ? wr : 2 * ay - wr, b = adjoint ? wc : 2 * ax - wc;
+                    w[t] = wr < kh ? __ldg(h + a * kw + b) : 0.f;
+                }
+                if (w[0] == 0.f && w[1] == 0.f && w[2] == 0.f && w[3] == 0.f) continue;
+                group(r0 * wp + wc, w[0], w[1], w[2], w[3]);
+            }
+    }
+}
+
+// out = (a (h * x) - y) scale (forward) or scale (h^T x) (adjoint).
+__global__ void __launch_bounds__(256) k_blur_wide(const float* __restrict__ x,
+                                                   const float* __restrict__ y,
+                                                   const float* __restrict__ h,
+                                                   const WTap* __restrict__ taps, int ntaps,
+                                                   int kh, int kw, int ny, int nx, float scale,
+                                                   int adjoint, float* __restrict__ out, float a,
+                                                   int64_t y_img_stride) {
+    extern __shared__ float4 sm4[];
+    const int64_t plane = (int64_t)ny * nx;
+    const int img = blockIdx.z;
+    const int i0 = blockIdx.y * WD_TR, j0 = blockIdx.x * WD_TW;
+    pdl_wait();
+    pdl_launch_dependents();
+    float acc[WD_R][4];
+    wide_tile(x + img * plane, ny, nx, i0, j0, kh, kw, taps, ntaps, h, adjoint != 0,
+              reinterpret_cast<float*>(sm4), acc);
+    if (y) y += img * y_img_stride;
+#pragma unroll
+    for (int o = 0; o < WD_R; ++o) {
+        const int i = i0 + threadIdx.y * WD_R + o;
+        if (i >= ny) break;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + threadIdx.x + 32 * q;
+            if (j >= nx) continue;
+            const int64_t n = (int64_t)i * nx + j;
+            float v = a * acc[o][q];
+            if (y) v -= __ldg(y + n);
+            out[img * plane + n] = v * scale;
+        }
+    }
+}
+
+// Fused x-update with g = H^T r from the wide stencil: the tile's gradient is
+// staged in shared memory, then each thread updates 4 consecutive pixels of a
+// row (the Philox group layout and 16-byte accesses of k_update).
+__global__ void __launch_bounds__(256) k_update_wide(UpdateParams p) {
+    extern __shared__ float4 sm4[];
+    float* win = reinterpret_cast<float*>(sm4);
+    const int ny = p.ny, nx = p.nx;
+    const int64_t plane = (int64_t)ny * nx;
+    const int chain = blockIdx.z;
+    const int i0 = blockIdx.y * WD_TR, j0 = blockIdx.x * WD_TW;
+    pdl_wait();
+    pdl_launch_dependents();
+    const uint32_t t = p.t_dev ? *p.t_dev : p.t;
+    float acc[WD_R][4];
+    wide_tile(p.r + chain * plane, ny, nx, i0, j0, p.kh, p.kw, p.wtaps, p.nwtaps, p.h, true, win,
+              acc);
+    __syncthreads();   // every warp is done with the window: reuse it for the gradient
+    float* G = win;    // [WD_TR][WD_TW]
+#pragma unroll
+    for (int o = 0; o < WD_R; ++o)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            G[(threadIdx.y * WD_R + o) * WD_TW + threadIdx.x + 32 * q] = acc[o][q];
+    __syncthreads();
+    float inv_n = p.inv_n;
+    if (p.burn_dev) {
+        const int64_t n = (int64_t)t + 1 - *p.burn_dev;
+        inv_n = n > 0 ? 1.0f / (float)n : 0.0f;
+    }
+    float* xc = p.x + chain * plane;
+    const float* dc = p.d ? p.d + chain * plane : nullptr;
+    float* mc = p.mean ? p.mean + chain * plane : nullptr;
+    float* qc = p.m2 ? p.m2 + chain * plane : nullptr;
+    const float* z2c = p.z2 ? p.z2 + chain * plane : nullptr;
+    const bool vec = (nx & 3) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(p.x) | reinterpret_cast<uintptr_t>(p.d) |
+                       reinterpret_cast<uintptr_t>(p.mean) | reinterpret_cast<uintptr_t>(p.m2) |
+                       reinterpret_cast<uintptr_t>(p.z2)) & 15) == 0;
+    const int j = j0 + 4 * threadIdx.x;
+    for (int o = 0; o < WD_R; ++o) {
+        const int li = threadIdx.y * WD_R + o, i = i0 + li;
+        if (i >= ny || j >= nx) break;
+        const float4 g4 = *reinterpret_cast<const float4*>(G + li * WD_TW + 4 * threadIdx.x);
+        const float g[4] = {g4.x, g4.y, g4.z, g4.w};
+        const int64_t n0 = (int64_t)i * nx + j;
+        float z[4] = {0.f, 0.f, 0.f, 0.f};
+        if (p.c_noise != 0.f) normals4(p.key0, p.key1, n0, t, (uint32_t)chain, z);
+        if (vec) {
+            const float4 xv = *reinterpret_cast<const float4*>(xc + n0);
+            float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (dc) dv = __ldg(reinterpret_cast<const float4*>(dc + n0));
+            float4 z2v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (z2c) z2v = __ldg(reinterpret_cast<const float4*>(z2c + n0));
+            float4 v;
+            v.x = update1(p, xv.x, g[0], dv.x, z[0], z2v.x);
+            v.y = update1(p, xv.y, g[1], dv.y, z[1], z2v.y);
+            v.z = update1(p, xv.z, g[2], dv.z, z[2], z2v.z);
+            v.w = update1(p, xv.w, g[3], dv.w, z[3], z2v.w);
+            *reinterpret_cast<float4*>(xc + n0) = v;
+            if (inv_n > 0.f) {
+                float4 mo = *reinterpret_cast<const float4*>(mc + n0);
+                float4 qo = *reinterpret_cast<const float4*>(qc + n0);
+                welford1(v.x, inv_n, mo.x, qo.x);
+                welford1(v.y, inv_n, mo.y, qo.y);
+                welford1(v.z, inv_n, mo.z, qo.z);
+                welford1(v.w, inv_n, mo.w, qo.w);
+                *reinterpret_cast<float4*>(mc + n0) = mo;
+                *reinterpret_cast<float4*>(qc + n0) = qo;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (j + q >= nx) break;
+                const int64_t n = n0 + q;
+                const float v = update1(p, xc[n], g[q], dc ? __ldg(dc + n) : 0.f, z[q],
+                                        z2c ? __ldg(z2c + n) : 0.f);
+                xc[n] = v;
+                if (inv_n > 0.f) {
+                    float mo = mc[n], qo = qc[n];
+                    welford1(v, inv_n, mo, qo);
+                    mc[n] = mo;
+                    qc[n] = qo;
+                }
+            }
+        }
+    }
+    if (p.arrive) {
+        __syncthreads();
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+            if (atomicAdd(p.arrive, 1u) == nblk - 1) {
+                *p.arrive = 0u;
+                *const_cast<uint32_t*>(p.t_dev) = t + 1u;
+            }
+        }
+    }
+}
+
+std::vector<WTap> wide_taps(const float* h, int kh, int kw, bool adjoint) {
+    const int wp = WD_TW + kw - 1, ay = kh / 2, ax = kw / 2;
+    auto tap = [&](int wr, int wc) {
+        if (wr >= kh) return 0.f;
+        const int a = adjoint ? wr : 2 * ay - wr, b = adjoint ? wc : 2 * ax - wc;
+        return h[a * kw + b];
+    };
+    std::vector<WTap> t;
+    for (int wc = 0; wc < kw; ++wc)
+        for (int wr = 0; wr < kh;) {
+            if (tap(wr, wc) == 0.f) {
+                ++wr;
+                continue;
+            }
+            WTap g = {};
+            for (int q = 0; q < 4; ++q) g.w[q] = tap(wr + q, wc);
+            g.off = wr * wp + wc;
+            t.push_back(g);
+            wr += 4;
+        }
+    return t;
 }
 
 // ------------------------------------------------------------ dispatch
@@ -745,25 +987,51 @@ static cudaError_t update_raw(const UpdateParams& p, int tile, cudaStream_t s) {
     return launch_pdl(fn, grid, dim3(16, ts.BY), smem, s, p);
 }
 
+static cudaError_t blur_wide(const float* x, const float* y, const float* h, const WTap* wt,
+                             int nwt, int kh, int kw, int ny, int nx, int nimg, float scale,
+                             bool adjoint, float* out, cudaStream_t s, float a,
+                             int64_t y_img_stride) {
+    if (kh > WIDE_MAXK || kw > WIDE_MAXK) return cudaErrorInvalidValue;
+    const size_t smem = wide_smem(kh, kw);
+    cudaError_t e = allow_smem(k_blur_wide, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(ceil_div(nx, WD_TW), ceil_div(ny, WD_TR), nimg);
+    return launch_pdl(k_blur_wide, grid, dim3(32, WD_BY), smem, s, x, y, h, wt, nwt, kh, kw, ny,
+                      nx, scale, adjoint ? 1 : 0, out, a, y_img_stride);
+}
+
 cudaError_t launch_blur(const float* x, const float* y, const float* h, int kh, int kw, int ny,
                         int nx, int nimg, float* r, cudaStream_t s, int tile, const float* hsep,
-                        float a, int64_t y_img_stride) {
+                        float a, int64_t y_img_stride, const WTap* wt, int nwt) {
     timer_begin(T_BLUR, s);
-    cudaError_t e = blur_raw(x, y, h, hsep, kh, kw, ny, nx, nimg, 1.0f, false, r,
-                             resolve_tile(tile), s, a, y_img_stride);
+    cudaError_t e = is_wide(kh, kw)
+        ? blur_wide(x, y, h, wt, nwt, kh, kw, ny, nx, nimg, 1.0f, false, r, s, a, y_img_stride)
+        : blur_raw(x, y, h, hsep, kh, kw, ny, nx, nimg, 1.0f, false, r, resolve_tile(tile), s, a,
+                   y_img_stride);
     timer_end(T_BLUR, s);
     return e;
 }
 
 cudaError_t launch_blur_adjoint(const float* r, const float* h, int kh, int kw, int ny, int nx,
                                 int nimg, float scale, float* g, cudaStream_t s, int tile) {
+    if (is_wide(kh, kw))
+        return blur_wide(r, nullptr, h, nullptr, 0, kh, kw, ny, nx, nimg, scale, true, g, s, 1.0f, 0);
     return blur_raw(r, nullptr, h, nullptr, kh, kw, ny, nx, nimg, scale, true, g,
                     resolve_tile(tile), s);
 }
 
+static cudaError_t update_wide(const UpdateParams& p, cudaStream_t s) {
+    if (p.kh > WIDE_MAXK || p.kw > WIDE_MAXK) return cudaErrorInvalidValue;
+    const size_t smem = wide_smem(p.kh, p.kw);
+    cudaError_t e = allow_smem(k_update_wide, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(ceil_div(p.nx, WD_TW), ceil_div(p.ny, WD_TR), p.nchain);
+    return launch_pdl(k_update_wide, grid, dim3(32, WD_BY), smem, s, p);
+}
+
 cudaError_t launch_langevin_update(const UpdateParams& p, cudaStream_t s) {
     timer_begin(T_UPDATE, s);
-    cudaError_t e = update_raw(p, resolve_tile(p.tile), s);
+    cudaError_t e = is_wide(p.kh, p.kw) ? update_wide(p, s) : update_raw(p, resolve_tile(p.tile), s);
     timer_end(T_UPDATE, s);
     return e;
 }

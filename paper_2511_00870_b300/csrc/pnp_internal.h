@@ -13,6 +13,20 @@
 
 namespace pnp {
 
+// Large blur kernels (kh or kw above 31, up to 129: the paper's 65^2-129^2
+// motion blurs) run on a wide-window stencil that visits only the nonzero
+// taps, in groups of up to four taps on consecutive rows of one window column:
+// the group's weights (zero where h is zero) and the window offset of its
+// first tap (row * pitch + col, pitch = 128 + kw - 1).
+struct alignas(16) WTap {
+    float w[4];
+    int off;
+    int pad[3];
+};
+constexpr int STENCIL_MAXK = 31;     // template (small-kernel) stencils
+constexpr int WIDE_MAXK = 129;
+inline bool is_wide(int kh, int kw) { return kh > STENCIL_MAXK || kw > STENCIL_MAXK; }
+
 // Thread-local error message, set by fail().
 void set_error(const std::string& msg);
 pnp_status fail(pnp_status st, const std::string& msg);
@@ -105,6 +119,12 @@ struct DenoiserDev {
     // host copies (FP32, OIHW) for reference / re-packing
     float* hw = nullptr;
     float* hb = nullptr;
+    // DDFB form (ddfb = true): K layers of F = P analysis filters (host,
+    // [K][P][3][3]), steps gamma_k and the hard-tanh threshold
+    bool ddfb = false;
+    float* ddfb_w = nullptr;
+    float ddfb_gamma[32] = {0};
+    float ddfb_ht = 0.f;
 };
 
 // Step counter read by the update kernel during graph replay; the update's
@@ -127,14 +147,21 @@ struct pnp_denoiser {
 
 namespace pnp {
 
+// Tap groups of h for the forward operator (convolution) or its adjoint
+// (correlation): window columns in order, rows ascending within a column.
+std::vector<WTap> wide_taps(const float* h, int kh, int kw, bool adjoint);
+
 // ---------------------------------------------------------------- kernels
 // Stencils take a tile-shape index (stencil_autotune's choice; -1 = default);
 // every shape gives bitwise the same results.
 // hsep (optional): separable taps [u | v | u flipped | v flipped] of a rank-one h.
 // r = a (h * x) - y per image; y shared (y_img_stride 0) or one plane per image.
+// Large kernels (is_wide) take the wide stencil with the forward taps wt (or,
+// when wt is NULL, every nonzero entry of the device array h in the same order).
 cudaError_t launch_blur(const float* x, const float* y, const float* h, int kh, int kw, int ny,
                         int nx, int nimg, float* r, cudaStream_t s, int tile = -1,
-                        const float* hsep = nullptr, float a = 1.0f, int64_t y_img_stride = 0);
+                        const float* hsep = nullptr, float a = 1.0f, int64_t y_img_stride = 0,
+                        const WTap* wt = nullptr, int nwt = 0);
 cudaError_t launch_blur_adjoint(const float* r, const float* h, int kh, int kw, int ny, int nx,
                                 int nimg, float scale, float* g, cudaStream_t s, int tile = -1);
 int stencil_tile_count();
@@ -165,6 +192,8 @@ struct UpdateParams {
     const float* hsep;         // separable taps of a rank-one h (nullptr: 2-D taps)
     const float* z2;           // Poisson: auxiliary z2 [chain][N]; adds -c_z2 (x - z2)
     float c_z2;                // gamma / rho2
+    const WTap* wtaps;         // large kernels: adjoint taps (NULL: read h)
+    int nwtaps;
 };
 
 // Auxiliary-variable update of the Poisson sampler (k_zupdate).
@@ -181,6 +210,7 @@ struct ZParams {
     float s1, s2;              // sqrt(2 kappa_i)
     float kappa1;
     int noise;
+    float* r_out;              // if non-null: eta H x+ - z1+ [chain][N], the next iteration's r
     uint32_t key0, key1;
     uint32_t t;
     const uint32_t* t_dev;
@@ -208,6 +238,9 @@ cudaError_t launch_finalize_moments(const float* mean, const float* m2, int64_t 
 cudaError_t denoise_fp32(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
                          const Rect* rects, float* d, float* scratch, cudaStream_t s);
 size_t denoise_fp32_scratch(const DenoiserDev& D, int ny, int nx, int nimg);
+// DDFB denoiser, direct layout (rects must be NULL); scratch as denoise_fp32.
+cudaError_t ddfb_forward(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
+                         const Rect* rects, float* d, float* scratch, cudaStream_t s);
 
 // One job of a tensor-core conv launch: the images of one size that share a
 // tensor map (input activations) and an output plane; row_begin/rows place
@@ -311,6 +344,9 @@ struct pnp_problem {
     // inpainting (H = diag(mask)): y holds NaN at missing pixels, no blur
     bool inpaint = false;
     float* hsep = nullptr;                  // separable taps when h is rank one
+    pnp::WTap* wt_fwd = nullptr;            // large kernels: forward / adjoint taps
+    pnp::WTap* wt_adj = nullptr;
+    int nwt = 0;
     cudaGraphExec_t graph = nullptr;         // one iteration
     cudaGraphExec_t graph_batch = nullptr;   // kGraphBatch iterations
 };

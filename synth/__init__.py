@@ -311,6 +311,12 @@ WORKLOADS = {
             K=8, F=64, blocks=(4, 4), halo=8, T=2000, burn_in=500),
     3: dict(name="deconv8192_gauss13_K8F64", ny=8192, nx=8192, blur=("gaussian", 13, 3.0), bsnr=30.0,
             K=8, F=64, blocks=(16, 16), halo=8, T=1000, burn_in=200),
+    # the paper's Gaussian-deconvolution scale: normalised motion blur whose
+    # size grows with the image (65^2 at 2048^2, 129^2 at 4096^2), 25 dB
+    6: dict(name="deconv2048_motion65_K8F64", ny=2048, nx=2048, blur=("motion", 65, 0.9),
+            bsnr=25.0, K=8, F=64, blocks=(8, 8), halo=8, T=1000, burn_in=200),
+    7: dict(name="deconv4096_motion129_K8F64", ny=4096, nx=4096, blur=("motion", 129, 0.9),
+            bsnr=25.0, K=8, F=64, blocks=(16, 16), halo=8, T=1000, burn_in=200),
 }
 
 
@@ -327,7 +333,7 @@ def blur_from_spec(spec, seed=0):
 
 
 def workload_problem(config: int, job: int = 0, shrink: int = 1) -> Problem:
-    """Problem of workload `config` (1..3); `shrink` divides the image size."""
+    """Problem of workload `config` (1..3, 6, 7); `shrink` divides the image size."""
     w = WORKLOADS[config]
     h = blur_from_spec(w["blur"])
     return make_problem(w["ny"] // shrink, w["nx"] // shrink, h, w["bsnr"], gt_seed(config, job),
@@ -338,6 +344,30 @@ def workload_problem(config: int, job: int = 0, shrink: int = 1) -> Problem:
 def workload_denoiser(config: int) -> DenoiserWeights:
     w = WORKLOADS.get(config, WORKLOADS[2])
     return denoiser_weights(w["K"], w["F"], seed=77 + w["K"] * 1000 + w["F"])
+
+
+@dataclass
+class DdfbWeights:
+    filters: np.ndarray      # [K][P][3][3] float64 (float32-exact)
+    gammas: np.ndarray       # [K]
+    ht: float
+
+
+def ddfb_weights(K: int, P: int, seed: int, ht: float = 0.05) -> DdfbWeights:
+    """Seeded DDFB parameters: zero-mean 3 x 3 analysis filters (high-pass, as
+    a learned sparsifying frame) with the layer operator norm ||W_k|| = 1
+    computed from the DFT of the filters, and steps gamma_k = 1.8 inside
+    (0, 2 / ||W_k||^2)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    f = rng.standard_normal((K, P, 3, 3))
+    f -= f.mean(axis=(2, 3), keepdims=True)
+    for k in range(K):
+        # ||W_k||^2 = max over frequencies of sum_p |DFT(w_p)|^2 (1 -> P channels)
+        pad = np.zeros((P, 64, 64))
+        pad[:, :3, :3] = f[k]
+        nrm = math.sqrt(float((np.abs(np.fft.fft2(pad)) ** 2).sum(axis=0).max()))
+        f[k] /= nrm
+    return DdfbWeights(filters=_f32(f), gammas=np.full(K, 1.8), ht=float(ht))
 
 
 def random_blur(rng: np.random.Generator):

@@ -82,6 +82,36 @@ def test_problem_rejects_bad_descriptors_without_gpu(lib):
         Problem(y, h, 0.1, blocks=(17, 1))              # more blocks than rows
     with pytest.raises(PnpError):
         Problem(y, h, 0.1, gamma=10.0)                  # violates Eq. 10
+    big = np.zeros((200, 200), np.float32)
+    with pytest.raises(PnpError):
+        Problem(big, np.ones((131, 131), np.float32) / 131 ** 2, 0.1)   # kernel above 129
+    with pytest.raises(PnpError) as e:
+        Problem(big, np.ones((33, 33), np.float32) / 33 ** 2, 0.0, noise_model="poisson",
+                eta=250.0, rho1=10.0, rho2=1e-3)        # Poisson with a large kernel
+    assert e.value.status == 7
+    with pytest.raises(PnpError):
+        Problem(y, h, 0.0, noise_model="poisson", eta=250.0, rho1=10.0, rho2=1e-3,
+                kappa1=20.0)                            # kappa1 >= rho1
+    neg = y.copy()
+    neg[0, 0] = -1.0
+    with pytest.raises(PnpError):
+        Problem(neg, h, 0.0, noise_model="poisson", eta=250.0, rho1=10.0, rho2=1e-3)
+    with pytest.raises(PnpError):
+        Problem(y, None, 0.1, mask=np.full(y.shape, 0.5))   # mask entries not 0/1
+    with pytest.raises(PnpError):
+        Problem(y, h, 0.1, noise_model="poisson", eta=250.0, rho1=10.0, rho2=1e-3,
+                mask=np.ones(y.shape))                  # inpainting is Gaussian
+    from paper_2511_00870_b300 import Denoiser
+    import synth
+    dw = synth.ddfb_weights(4, 16, 1)
+    den = Denoiser.ddfb(dw.filters, dw.gammas, dw.ht)       # host-only creation
+    with pytest.raises(PnpError) as e:
+        Problem(y, h, 0.1, den, precision="bf16")       # DDFB runs in FP32
+    assert e.value.status == 7
+    with pytest.raises(PnpError):
+        Problem(y, h, 0.1, den, blocks=(2, 2), halo=8)  # DDFB uses the direct layout
+    with pytest.raises(PnpError):
+        Denoiser.ddfb(dw.filters, -dw.gammas, dw.ht)     # gamma_k <= 0
 
 
 def test_stencil_tile_override_is_validated_on_the_host(lib):

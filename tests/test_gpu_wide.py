@@ -1,0 +1,163 @@
+"""Large blur kernels (the paper's 65^2-129^2 motion blurs, Sec. IV-A) on the
+wide-window stencil, against the FP64 oracle's direct circular sums.
+
+Bounds: r = Hx - y and H^T r within 2e-6 * max|ref| (FP32 sums of up to a few
+thousand taps of a normalised kernel); the one-step x-update within
+1e-5 * max|x+| as for small kernels. The problem API (host-built list of
+nonzero taps) and the operator entry points (walk of h skipping zeros) use
+the same order, so they agree bitwise.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_00870_b300 as P
+    return P
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _kernel(kind, L, seed=0):
+    if kind == "motion":
+        return synth.motion_kernel(L, 0.3 + 0.4 * seed)
+    rng = np.random.default_rng(seed)
+    h = rng.random((L, L + 2))            # dense, non-square, not rank one
+    return h / h.sum()
+
+
+@pytest.mark.parametrize("ny,nx,kind,L", [(150, 210, "motion", 65), (97, 131, "dense", 33),
+                                          (256, 256, "motion", 129), (130, 140, "motion", 129)])
+def test_blur_and_adjoint_against_oracle(P, orc, ny, nx, kind, L):
+    h = _kernel(kind, L, 1).astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(ny)
+    x = rng.random((2, ny, nx))
+    y = rng.random((ny, nx))
+    r = torch.empty((2, ny, nx), device="cuda")
+    g = torch.empty_like(r)
+    P.pnp_blur(dev(x), dev(y), dev(h), r)
+    P.pnp_blur_adjoint(r, dev(h), g, scale=0.5)
+    torch.cuda.synchronize()
+    for c in range(2):
+        xf = x[c].astype(np.float32).astype(np.float64)
+        rr = orc.blur(xf, h) - y.astype(np.float32)
+        got = r[c].cpu().numpy()
+        np.testing.assert_allclose(got, rr, rtol=0, atol=2e-6 * np.abs(rr).max())
+        gg = 0.5 * orc.blur_adj(got.astype(np.float64), h)
+        np.testing.assert_allclose(g[c].cpu().numpy(), gg, rtol=0, atol=2e-6 * np.abs(gg).max())
+
+
+def test_problem_step_equals_operators_and_oracle(P, orc):
+    """Ragged 200 x 300, motion 65, FP32 denoiser: the problem's step equals
+    pnp_blur + pnp_langevin_update on the same state bitwise (prior off), and
+    the oracle's within 1e-5 (prior on)."""
+    prob = synth.make_problem(200, 300, synth.motion_kernel(65, 0.7), 25.0, 77)
+    x0 = np.clip(prob.y + 0.02, 0, 1).astype(np.float32)
+    # prior off: problem vs operators
+    gp = P.Problem(prob.y, prob.h, prob.sigma, None, seed=prob.seed)
+    prm = gp.params()
+    gp.set_state(x0, 4)
+    gp.step(1)
+    xp, _ = gp.state()
+    x = dev(x0[None])
+    r = torch.empty_like(x)
+    P.pnp_blur(x, dev(prob.y), dev(prob.h), r)
+    P.pnp_langevin_update(x, r, None, dev(prob.h), prob.sigma, 0.0, prm["eps"], prm["lam"],
+                          prm["gamma"], prob.seed, 4)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(x.cpu().numpy()[0], xp[0])
+    op0 = orc.Problem(prob.y, prob.h, prob.sigma, 0.0, prm["eps"], prm["lam"], prm["gamma"],
+                      prob.seed)
+    ref0 = orc.langevin_step(op0, x0.astype(np.float64), 4)
+    assert np.abs(xp[0] - ref0).max() <= 1e-5 * np.abs(ref0).max()
+    # prior on
+    dw = synth.workload_denoiser(1)
+    gq = P.Problem(prob.y, prob.h, prob.sigma, P.Denoiser.from_weights(dw), seed=prob.seed,
+                   burn_in=0)
+    prq = gq.params()
+    gq.set_state(x0, 11)
+    gq.step(1)
+    xq, _ = gq.state()
+    op = orc.Problem(prob.y, prob.h, prob.sigma, prq["alpha"], prq["eps"], prq["lam"],
+                     prq["gamma"], prob.seed, net=orc.Net.from_weights(dw))
+    ref = orc.langevin_step(op, x0.astype(np.float64), 11)
+    assert np.abs(xq[0] - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_graph_eager_and_batch_with_wide_kernels(P):
+    prob = synth.make_problem(160, 192, synth.motion_kernel(65, 1.1), 25.0, 78)
+    dw = synth.workload_denoiser(2)
+    den = P.Denoiser.from_weights(dw)
+    out = []
+    for graph in (True, False):
+        P.pnp_set_graph_mode(graph)
+        gp = P.Problem(prob.y, prob.h, prob.sigma, den, seed=3, burn_in=2, precision="bf16")
+        gp.run_chain(9, 2)
+        out.append((gp.state()[0], gp.moments(want_var=True)[1]))
+    P.pnp_set_graph_mode(True)
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    b = P.Batch([dict(y=prob.y, h=prob.h, sigma=prob.sigma, seed=3, burn_in=2),
+                 dict(y=prob.y[:96, :128], h=synth.uniform_kernel(9), sigma=prob.sigma, seed=4)],
+                den, precision="bf16")
+    b.run(9, 2)
+    np.testing.assert_array_equal(b.job(0).state()[0], out[0][0])
+
+
+def _crop_wrap(a, i, j, r):
+    ny, nx = a.shape
+    return np.take(np.take(a, np.arange(i - r, i + r + 1) % ny, axis=0),
+                   np.arange(j - r, j + r + 1) % nx, axis=1)
+
+
+@pytest.mark.parametrize("n,L,npix", [(2048, 65, 8), (4096, 129, 4)])
+def test_paper_scale_sampled_bf16(P, orc, n, L, npix):
+    """The paper's sizes (2048^2 with 65^2, 4096^2 with 129^2 motion blur),
+    BF16 denoiser, direct layout: x+ at sampled pixels from wrapped crops
+    (blur and adjoint need radius 2r) and the denoiser on unwrapped crops."""
+    prob = synth.make_problem(n, n, synth.motion_kernel(L, 0.9), 25.0, 4000 + L)
+    dw = synth.workload_denoiser(2)
+    net = orc.Net.from_weights(dw)
+    gp = P.Problem(prob.y, prob.h, prob.sigma, P.Denoiser.from_weights(dw), seed=prob.seed,
+                   precision="bf16")
+    prm = gp.params()
+    rng = np.random.default_rng(L)
+    pix = [(0, 0), (n - 1, n - 1), (n // 2, 3)][:npix] + \
+        [tuple(v) for v in rng.integers(0, n, size=(max(npix - 3, 1), 2))]
+    x0 = np.clip(prob.y + 0.05 * rng.standard_normal(prob.shape), -0.1, 1.1).astype(np.float32)
+    t = 17
+    gp.set_state(x0, t)
+    gp.step(1)
+    xn, _ = gp.state()
+    rr = L // 2
+    K = net.K
+    xi = orc.normals(prob.seed, t, 0, n * n).reshape(n, n)
+    gam, c_prior = prm["gamma"], prm["alpha"] * prm["gamma"] / prm["eps"] ** 2
+    got, ref, gmax = [], [], 0.0
+    x64 = x0.astype(np.float64)
+    for (i, j) in pix:
+        xc = _crop_wrap(x64, i, j, 2 * rr)
+        yc = _crop_wrap(prob.y, i, j, 2 * rr)
+        g = orc.blur_adj(orc.blur(xc, prob.h) - yc, prob.h)[2 * rr, 2 * rr] / prob.sigma ** 2
+        i0, i1, j0, j1 = max(0, i - K), min(n, i + K + 1), max(0, j - K), min(n, j + K + 1)
+        G = x64[i, j] - orc.denoise(x64[i0:i1, j0:j1], net)[i - i0, j - j0]
+        gmax = max(gmax, abs(G))
+        xv = x64[i, j]
+        v = xv - gam * g - c_prior * G + gam / prm["lam"] * (min(max(xv, 0.0), 1.0) - xv)
+        v += np.sqrt(2 * gam) * xi[i, j]
+        got.append(xn[0][i, j])
+        ref.append(v)
+    gcrop = np.abs(x64[:96, :96] - orc.denoise(x64[:96, :96], net)).max()
+    bound = c_prior * 3e-2 * max(gmax, gcrop) + 1e-5 * np.abs(xn[0]).max()
+    err = np.abs(np.array(got) - np.array(ref)).max()
+    assert err <= bound, (err, bound)
