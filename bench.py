@@ -659,15 +659,17 @@ def main():
                     kernel=ktag, peak_kind=f"{precs[0]} sustained ({peaks['src']}"
                                                   + (", bf16 x nominal ratio 2)" if precs[0] == "fp8" else ")"))
     elif ddfb:
-        # dual layers stream the P-channel dual variable: the first writes it
-        # (reads v), the others read and write it; bytes averaged over the
-        # K - 1 launches the timer covers
-        Kd, Pd = 4, 64
-        bpp = ((4 + 4 * Pd) + (Kd - 2) * (4 + 8 * Pd)) / (Kd - 1)
+        # a dual layer (the conv_fp32 timer; the first layer and the output run
+        # under conv_edge) streams the P-channel dual variable: read v and u,
+        # write u
+        Pd = 64
+        bpp = 4 + 8 * Pd
         gbs = bpp * pix_per_launch / (kern["avg_ms"] * 1e-3) / 1e9
         roof = dict(bound="hbm", achieved=round(gbs, 1), peak=peaks["hbm"], unit="GB/s",
-                    frac=round(gbs / peaks["hbm"], 4), traffic=None, kernel="k_ddfb<64,0|1>",
-                    bytes_per_pixel=round(bpp, 1), peak_kind=f"HBM copy ({peaks['src']})")
+                    frac=round(gbs / peaks["hbm"], 4),
+                    traffic=ncu_traffic("k_ddfb<64,0>", args.workload, "fp32"),
+                    kernel="k_ddfb<64,0>", bytes_per_pixel=bpp,
+                    peak_kind=f"HBM copy ({peaks['src']})")
     else:
         flop = 2.0 * F * F * 9 * pix_per_launch
         achieved = flop / (kern["avg_ms"] * 1e-3) / 1e12

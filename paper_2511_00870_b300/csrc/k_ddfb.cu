@@ -7,14 +7,17 @@
 // One launch per dual layer, one for the output. The work per pixel is small
 // (P x 9 multiply-adds per operator), so each launch streams the P-channel
 // dual variable once in and once out of HBM:
-//   * a block owns a 32 x 8 tile; the P channels are staged in shared memory
-//     16 at a time with a 2-pixel halo, and each thread accumulates W_k^* u at
-//     the tile + 1-pixel halo positions it owns (s needs one more ring than the
-//     tile for the following W_k);
+//   * a block owns a 32 x 8 tile; the P channels stream through shared
+//     memory 8 at a time with a 2-pixel halo, double buffered: 16-byte
+//     asynchronous copies of the next group (source offsets computed once per
+//     thread, the pattern repeats for every group) are in flight while the
+//     current one is reduced;
+//   * W_k^* u is accumulated for vertical pairs of positions over the tile +
+//     1-pixel ring (s needs one more ring than the tile for the following W_k):
+//     a 4 x 3 window of each channel gives both sums;
 //   * the update re-reads each pixel's own P dual values (just staged by the
-//     same block, so from L2) instead of holding them in registers: at about
-//     40 registers a thread, several blocks share an SM and hide each other's
-//     load latency;
+//     same block, so from L2) instead of holding them in registers, which
+//     keeps four blocks per SM;
 //   * the layer's filters are a by-value kernel parameter: every multiply-add
 //     takes its weight from the constant bank;
 //   * the first dual layer computes u_0 = W_K v from v on the fly (u_0 is never
@@ -26,11 +29,43 @@ namespace pnp {
 
 namespace {
 
-constexpr int DB_TW = 32, DB_TH = 8, DB_CH = 16;
+constexpr int DB_TW = 32, DB_TH = 8, DB_CH = 8;
 
 struct DdfbFilters {
     float w[64 * 9];    // W_k (or W_K for the output launch), [p][3][3]
     float wK[64 * 9];   // W_K, used by the first dual layer for u_0 = W_K v
+};
+
+// asynchronous global -> shared copies; src_bytes = 0 writes zeros
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <int MODE>
+struct DdfbGeom {
+    static constexpr int HALO = MODE == 2 ? 1 : 2;          // u ring around the tile
+    static constexpr int UH = DB_TH + 2 * HALO, UW = DB_TW + 2 * HALO;
+    // staged rows hold columns j0 - 4 .. j0 + 35 (a 16-byte aligned span that
+    // contains the UW columns j0 - HALO .. j0 + 31 + HALO, at offset CX)
+    static constexpr int UP = DB_TW + 8, CX = 4 - HALO;
+    static constexpr int SH = MODE == 2 ? DB_TH : DB_TH + 2;  // W^* u positions: tile (+1 ring)
+    static constexpr int SW = MODE == 2 ? DB_TW : DB_TW + 2;
+    static constexpr int NPAIR = SW * (SH / 2);               // vertical pairs of positions
+    static constexpr int VH = DB_TH + 6, VW = DB_TW + 6;      // v: tile + 3 rings (first layer)
+    static constexpr size_t SMEM =
+        sizeof(float) * (2 * DB_CH * UH * UP + (DB_TH + 2) * (DB_TW + 2) + (MODE == 1 ? VH * VW : 0));
 };
 
 // MODE 0: dual layer from u_in; MODE 1: first dual layer (u_in = W_K v);
@@ -40,14 +75,13 @@ __global__ void __launch_bounds__(256, 4) k_ddfb(const float* __restrict__ v,
                                               const float* __restrict__ uin,
                                               float* __restrict__ out, int ny, int nx, float gam,
                                               float ht, const __grid_constant__ DdfbFilters L) {
-    constexpr int HALO = MODE == 2 ? 1 : 2;            // u ring around the tile
-    constexpr int UH = DB_TH + 2 * HALO, UW = DB_TW + 2 * HALO;
-    constexpr int SH = DB_TH + 2, SW = DB_TW + 2;      // s: tile + 1 ring (dual layers)
-    constexpr int NPOS = MODE == 2 ? DB_TH * DB_TW : SH * SW;
-    constexpr int VH = DB_TH + 6, VW = DB_TW + 6;      // v: tile + 3 rings (first layer)
-    __shared__ float us[DB_CH][UH][UW];
-    __shared__ float ss[SH][SW];
-    __shared__ float vs[MODE == 1 ? VH : 1][MODE == 1 ? VW : 1];
+    using G = DdfbGeom<MODE>;
+    constexpr int UH = G::UH, UW = G::UW, HALO = G::HALO, UP = G::UP, CX = G::CX;
+    constexpr int NCH = P / DB_CH;
+    extern __shared__ float4 sm4[];
+    float* us = reinterpret_cast<float*>(sm4);                 // [2][DB_CH][UH][UP]
+    float* ss = us + 2 * DB_CH * UH * UP;                      // [DB_TH + 2][DB_TW + 2]
+    float* vs = ss + (DB_TH + 2) * (DB_TW + 2);                // [VH][VW] (first layer)
 
     const int tid = threadIdx.x;
     const int tx = tid & 31, ty = tid >> 5;
@@ -55,105 +89,174 @@ __global__ void __launch_bounds__(256, 4) k_ddfb(const float* __restrict__ v,
     const int64_t plane = (int64_t)ny * nx;
     const int i0 = blockIdx.y * DB_TH, j0 = blockIdx.x * DB_TW;
     const float* vi = v + img * plane;
-    const float* ui = uin ? uin + img * (int64_t)P * plane : nullptr;
+    const float* ui = uin ? uin + img * (int64_t)P * plane : vi;
     pdl_wait();
     pdl_launch_dependents();
 
-    if constexpr (MODE == 1) {
-        for (int it = tid; it < VH * VW; it += 256) {
-            const int r = it / VW, c = it - r * VW;
-            const int gi = i0 - 3 + r, gj = j0 - 3 + c;
-            vs[r][c] = (gi >= 0 && gi < ny && gj >= 0 && gj < nx) ? __ldg(vi + (int64_t)gi * nx + gj)
-                                                                 : 0.f;
-        }
-    }
-    // positions this thread accumulates W^* u at (at most two)
-    int pr[2], pc[2];
-    bool pv[2];
+    // A group's copies: with rows of whole float4s (nx % 4 == 0) 16-byte copies
+    // whose source offsets within a channel group are computed once (the
+    // pattern repeats for every group); otherwise 4-byte copies.
+    const bool vec = (nx & 3) == 0 && (reinterpret_cast<uintptr_t>(ui) & 15) == 0;
+    constexpr int NV = DB_CH * UH * (UP / 4);
+    constexpr int KV = (NV + 255) / 256;
+    int64_t voff[KV];
+    int vso[KV];
+    bool vin[KV], vok[KV];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int pos = tid + 256 * k;
-        pv[k] = pos < NPOS;
-        if (MODE == 2) {
-            pr[k] = ty;
-            pc[k] = tx;
-        } else {
-            pr[k] = pv[k] ? pos / SW : 0;
-            pc[k] = pv[k] ? pos - pr[k] * SW : 0;
-        }
+    for (int k = 0; k < KV; ++k) {
+        const int it = tid + 256 * k;
+        vok[k] = it < NV;
+        const int ch = it / (UH * (UP / 4));
+        const int rem = it - ch * (UH * (UP / 4));
+        const int r = rem / (UP / 4), c4 = rem - r * (UP / 4);
+        const int gi = i0 - HALO + r, gj = j0 - 4 + 4 * c4;
+        vin[k] = vok[k] && gi >= 0 && gi < ny && gj >= 0 && gj < nx;
+        voff[k] = vin[k] ? (int64_t)ch * plane + (int64_t)gi * nx + gj : 0;
+        vso[k] = (ch * UH + r) * UP + 4 * c4;
     }
-    float sacc[2] = {0.f, 0.f};
+    auto stage = [&](int buf, int c0) {
+        float* dst = us + buf * DB_CH * UH * UP;
+        if (vec) {
+            const float* base = ui + (int64_t)c0 * plane;
+#pragma unroll
+            for (int k = 0; k < KV; ++k)
+                if (vok[k]) cp_async16(dst + vso[k], vin[k] ? base + voff[k] : ui, vin[k] ? 16 : 0);
+        } else {
+            for (int it = tid; it < DB_CH * UH * UP; it += 256) {
+                const int ch = it / (UH * UP);
+                const int rem = it - ch * (UH * UP);
+                const int r = rem / UP, c = rem - r * UP;
+                const int gi = i0 - HALO + r, gj = j0 - 4 + c;
+                const bool inside = gi >= 0 && gi < ny && gj >= 0 && gj < nx;
+                const float* src = inside ? ui + (int64_t)(c0 + ch) * plane + (int64_t)gi * nx + gj : ui;
+                cp_async4(dst + it, src, inside ? 4 : 0);
+            }
+        }
+        cp_async_commit();
+    };
+
+    if constexpr (MODE == 1) {
+        for (int it = tid; it < G::VH * G::VW; it += 256) {
+            const int r = it / G::VW, c = it - r * G::VW;
+            const int gi = i0 - 3 + r, gj = j0 - 3 + c;
+            vs[it] = (gi >= 0 && gi < ny && gj >= 0 && gj < nx) ? __ldg(vi + (int64_t)gi * nx + gj) : 0.f;
+        }
+    } else {
+        stage(0, 0);
+    }
+    // the vertical pair of W^* u positions this thread accumulates
+    const bool act = tid < G::NPAIR;
+    const int pc = act ? tid % G::SW : 0, pr = act ? 2 * (tid / G::SW) : 0;
+    float acc0 = 0.f, acc1 = 0.f;
 
 #pragma unroll
-    for (int c0 = 0; c0 < P; c0 += DB_CH) {
-        __syncthreads();   // previous chunk consumed (and vs filled)
-        for (int it = tid; it < DB_CH * UH * UW; it += 256) {
-            const int ch = it / (UH * UW);
-            const int rem = it - ch * (UH * UW);
-            const int r = rem / UW, c = rem - r * UW;
-            const int gi = i0 - HALO + r, gj = j0 - HALO + c;
-            const bool inside = gi >= 0 && gi < ny && gj >= 0 && gj < nx;
-            float val = 0.f;
-            if (inside) {
-                if constexpr (MODE == 1) {
-                    // u_0 = W_K v: correlation of v with the channel's filter
+    for (int k = 0; k < NCH; ++k) {
+        const int c0 = k * DB_CH;
+        float* ub = us + (k & 1) * DB_CH * UH * UP;
+        if constexpr (MODE == 1) {
+            __syncthreads();   // v staged; the buffer's previous group consumed
+            // u_0 = W_K v for the group's channels at vertical pairs of the staged
+            // block: the 4 x 3 window of v serves both positions and all channels
+            constexpr int UPAIR = UW * (UH / 2);
+            for (int q = tid; q < UPAIR; q += 256) {
+                const int c = q % UW, r = 2 * (q / UW);
+                float vw[4][3];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) vw[a][b] = vs[(r + a) * G::VW + c + b];
+                const int gi = i0 - HALO + r, gj = j0 - HALO + c;
+                const bool in0 = gi >= 0 && gi < ny && gj >= 0 && gj < nx;
+                const bool in1 = gi + 1 >= 0 && gi + 1 < ny && gj >= 0 && gj < nx;
+#pragma unroll
+                for (int ch = 0; ch < DB_CH; ++ch) {
                     const float* wk = L.wK + (c0 + ch) * 9;
+                    float u0 = 0.f, u1 = 0.f;
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
 #pragma unroll
-                        for (int b = 0; b < 3; ++b) val = fmaf(wk[a * 3 + b], vs[r + a][c + b], val);
-                } else {
-                    val = __ldg(ui + (int64_t)(c0 + ch) * plane + (int64_t)gi * nx + gj);
+                        for (int b = 0; b < 3; ++b) {
+                            u0 = fmaf(wk[a * 3 + b], vw[a][b], u0);
+                            u1 = fmaf(wk[a * 3 + b], vw[a + 1][b], u1);
+                        }
+                    ub[(ch * UH + r) * UP + c + CX] = in0 ? u0 : 0.f;
+                    ub[(ch * UH + r + 1) * UP + c + CX] = in1 ? u1 : 0.f;
                 }
             }
-            us[ch][r][c] = val;
+            __syncthreads();
+        } else {
+            if (k + 1 < NCH) {
+                stage((k + 1) & 1, c0 + DB_CH);   // next group in flight
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        // W^* u at the owned positions: sum_p sum_ab w[p][a][b] u_p(q - a + 1, q - b + 1)
+        // W^* u at (q, q + one row): sum_p sum_ab w[p][a][b] u_p(q - a + 1, q - b + 1);
+        // the staged block starts one ring further out than the positions, so
+        // u(q - a + 1) is staged row pr + 2 - a
+        if (act) {
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            if (!pv[k]) continue;
-            float acc = sacc[k];
-            // the staged u block starts one ring further out than the positions
-            // (HALO vs HALO - 1 rings), so u(q - a + 1) is staged row pr + 2 - a
-            const int rb = pr[k] + 2, cb = pc[k] + 2;
+            for (int ch = 0; ch < DB_CH; ++ch) {
+                const float* uc = ub + ch * UH * UP + CX;
+                float uw[4][3];
 #pragma unroll
-            for (int ch = 0; ch < DB_CH; ++ch)
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) uw[a][b] = uc[(pr + a) * UP + pc + b];
+                const float* wk = L.w + (c0 + ch) * 9;
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
 #pragma unroll
-                    for (int b = 0; b < 3; ++b)
-                        acc = fmaf(L.w[(c0 + ch) * 9 + a * 3 + b], us[ch][rb - a][cb - b], acc);
-            sacc[k] = acc;
+                    for (int b = 0; b < 3; ++b) {
+                        acc0 = fmaf(wk[a * 3 + b], uw[2 - a][2 - b], acc0);
+                        acc1 = fmaf(wk[a * 3 + b], uw[3 - a][2 - b], acc1);
+                    }
+            }
         }
+        if constexpr (MODE != 1) __syncthreads();   // group consumed before its buffer refills
     }
 
-    const int i = i0 + ty, j = j0 + tx;
-    const bool own = i < ny && j < nx;
     if constexpr (MODE == 2) {
-        if (own) {
-            const float d = __ldg(vi + (int64_t)i * nx + j) - gam * sacc[0];
-            out[img * plane + (int64_t)i * nx + j] = fminf(fmaxf(d, 0.f), 1.f);
+        if (act) {
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int i = i0 + pr + t, j = j0 + pc;
+                if (i < ny && j < nx) {
+                    const float d = __ldg(vi + (int64_t)i * nx + j) - gam * (t ? acc1 : acc0);
+                    out[img * plane + (int64_t)i * nx + j] = fminf(fmaxf(d, 0.f), 1.f);
+                }
+            }
         }
         return;
     }
     // s = proj_[0,1](v - W_k^* u) on the tile + 1 ring, zero outside the image
+    if (act) {
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        if (!pv[k]) continue;
-        const int gi = i0 - 1 + pr[k], gj = j0 - 1 + pc[k];
-        float sv = 0.f;
-        if (gi >= 0 && gi < ny && gj >= 0 && gj < nx)
-            sv = fminf(fmaxf(__ldg(vi + (int64_t)gi * nx + gj) - sacc[k], 0.f), 1.f);
-        ss[pr[k]][pc[k]] = sv;
+        for (int t = 0; t < 2; ++t) {
+            const int gi = i0 - 1 + pr + t, gj = j0 - 1 + pc;
+            float sv = 0.f;
+            if (gi >= 0 && gi < ny && gj >= 0 && gj < nx)
+                sv = fminf(fmaxf(__ldg(vi + (int64_t)gi * nx + gj) - (t ? acc1 : acc0), 0.f), 1.f);
+            ss[(pr + t) * (DB_TW + 2) + pc] = sv;
+        }
     }
     __syncthreads();
-    if (!own) return;
+    const int i = i0 + ty, j = j0 + tx;
+    if (i >= ny || j >= nx) return;
     float sr[9];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) sr[a * 3 + b] = ss[ty + a][tx + b];
+        for (int b = 0; b < 3; ++b) sr[a * 3 + b] = ss[(ty + a) * (DB_TW + 2) + tx + b];
+    float vw[3][3];
+    if constexpr (MODE == 1) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) vw[a][b] = vs[(ty + 2 + a) * G::VW + tx + 2 + b];
+    }
     float* uo = out + img * (int64_t)P * plane + (int64_t)i * nx + j;
     const float* uc = ui + (int64_t)i * nx + j;
 #pragma unroll 4
@@ -164,18 +267,31 @@ __global__ void __launch_bounds__(256, 4) k_ddfb(const float* __restrict__ v,
         for (int q = 0; q < 9; ++q) t = fmaf(L.w[p * 9 + q], sr[q], t);
         float u;
         if constexpr (MODE == 1) {
-            // u_0 = W_K v at the pixel, from the staged v
-            u = 0.f;
+            u = 0.f;   // u_0 = W_K v at the pixel
 #pragma unroll
             for (int a = 0; a < 3; ++a)
 #pragma unroll
-                for (int b = 0; b < 3; ++b) u = fmaf(L.wK[p * 9 + a * 3 + b], vs[ty + 2 + a][tx + 2 + b], u);
+                for (int b = 0; b < 3; ++b) u = fmaf(L.wK[p * 9 + a * 3 + b], vw[a][b], u);
         } else {
             u = __ldg(uc + (int64_t)p * plane);
         }
         const float un = fmaf(gam, t, u);
         uo[(int64_t)p * plane] = fminf(fmaxf(un, -ht), ht);
     }
+}
+
+template <int P, int MODE>
+cudaError_t ddfb_launch(dim3 grid, cudaStream_t s, const float* x, const float* u, float* out,
+                        int ny, int nx, float gam, float ht, const DdfbFilters& F) {
+    const size_t smem = DdfbGeom<MODE>::SMEM;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_ddfb<P, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    return launch_pdl(k_ddfb<P, MODE>, grid, dim3(256), smem, s, x, u, out, ny, nx, gam, ht, F);
 }
 
 template <int P>
@@ -195,21 +311,20 @@ cudaError_t ddfb_forward_P(const DenoiserDev& D, const float* x, int ny, int nx,
         const float* Wk = D.ddfb_w + (size_t)k * P * 9;
         for (int q = 0; q < P * 9; ++q) F.w[q] = Wk[q];
         float* nxt = (k % 2 == 0) ? ua : ub;
-        timer_begin(T_CONV_FP32, s);
+        // dual layers under conv_fp32; the first layer and the output under conv_edge
+        const int tid = k == 0 ? T_CONV_EDGE : T_CONV_FP32;
+        timer_begin(tid, s);
         if (k == 0)
-            e = launch_pdl(k_ddfb<P, 1>, grid, dim3(256), 0, s, x, (const float*)nullptr, nxt, ny,
-                           nx, D.ddfb_gamma[k], D.ddfb_ht, F);
+            e = ddfb_launch<P, 1>(grid, s, x, nullptr, nxt, ny, nx, D.ddfb_gamma[k], D.ddfb_ht, F);
         else
-            e = launch_pdl(k_ddfb<P, 0>, grid, dim3(256), 0, s, x, cur, nxt, ny, nx,
-                           D.ddfb_gamma[k], D.ddfb_ht, F);
-        timer_end(T_CONV_FP32, s);
+            e = ddfb_launch<P, 0>(grid, s, x, cur, nxt, ny, nx, D.ddfb_gamma[k], D.ddfb_ht, F);
+        timer_end(tid, s);
         cur = nxt;
     }
     if (e != cudaSuccess) return e;
     for (int q = 0; q < P * 9; ++q) F.w[q] = WK[q];
     timer_begin(T_CONV_EDGE, s);
-    e = launch_pdl(k_ddfb<P, 2>, grid, dim3(256), 0, s, x, cur, d, ny, nx, D.ddfb_gamma[K - 1],
-                   D.ddfb_ht, F);
+    e = ddfb_launch<P, 2>(grid, s, x, cur, d, ny, nx, D.ddfb_gamma[K - 1], D.ddfb_ht, F);
     timer_end(T_CONV_EDGE, s);
     return e;
 }

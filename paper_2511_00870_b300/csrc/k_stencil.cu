@@ -706,6 +706,7 @@ __device__ __forceinline__ void wide_tile(const float* __restrict__ img, int ny,
         }
     };
     if (taps) {
+#pragma unroll 2
         for (int k = 0; k < ntaps; ++k) {
             const float4 w = __ldg(reinterpret_cast<const float4*>(taps[k].w));
             group(__ldg(&taps[k].off), w.x, w.y, w.z, w.w);
