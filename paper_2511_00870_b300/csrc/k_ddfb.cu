@@ -20,8 +20,9 @@
 //     keeps four blocks per SM;
 //   * the layer's filters are a by-value kernel parameter: every multiply-add
 //     takes its weight from the constant bank;
-//   * the first dual layer computes u_0 = W_K v from v on the fly (u_0 is never
-//     written), the output launch reads u_{K-1} once.
+//   * the first dual layer takes W_1^* W_K v as one 5 x 5 filter of v away from
+//     the image border and u_0 = W_K v per pixel for its update (u_0 is never
+//     written); the output launch reads u_{K-1} once.
 #include "pdl.cuh"
 #include "pnp_internal.h"
 
@@ -34,6 +35,8 @@ constexpr int DB_TW = 32, DB_TH = 8, DB_CH = 8;
 struct DdfbFilters {
     float w[64 * 9];    // W_k (or W_K for the output launch), [p][3][3]
     float wK[64 * 9];   // W_K, used by the first dual layer for u_0 = W_K v
+    float c5[25];       // first dual layer: the 5 x 5 filter of W_1^* W_K (see k_ddfb)
+    float m81[81];      // M[a b][c d] = sum_p w_1[p][a][b] w_K[p][c][d] (border pixels)
 };
 
 // asynchronous global -> shared copies; src_bytes = 0 writes zeros
@@ -56,31 +59,39 @@ __device__ __forceinline__ void cp_async_wait() {
 template <int MODE>
 struct DdfbGeom {
     static constexpr int HALO = MODE == 2 ? 1 : 2;          // u ring around the tile
-    static constexpr int UH = DB_TH + 2 * HALO, UW = DB_TW + 2 * HALO;
+    static constexpr int UH = DB_TH + 2 * HALO;
     // staged rows hold columns j0 - 4 .. j0 + 35 (a 16-byte aligned span that
-    // contains the UW columns j0 - HALO .. j0 + 31 + HALO, at offset CX)
+    // contains the columns j0 - HALO .. j0 + 31 + HALO, at offset CX)
     static constexpr int UP = DB_TW + 8, CX = 4 - HALO;
     static constexpr int SH = MODE == 2 ? DB_TH : DB_TH + 2;  // W^* u positions: tile (+1 ring)
     static constexpr int SW = MODE == 2 ? DB_TW : DB_TW + 2;
     static constexpr int NPAIR = SW * (SH / 2);               // vertical pairs of positions
     static constexpr int VH = DB_TH + 6, VW = DB_TW + 6;      // v: tile + 3 rings (first layer)
+    static constexpr int USTAGE = MODE == 1 ? 0 : 2 * DB_CH * UH * UP;   // channel groups
     static constexpr size_t SMEM =
-        sizeof(float) * (2 * DB_CH * UH * UP + (DB_TH + 2) * (DB_TW + 2) + (MODE == 1 ? VH * VW : 0));
+        sizeof(float) * (USTAGE + (DB_TH + 2) * (DB_TW + 2) + (MODE == 1 ? VH * VW : 0));
 };
 
 // MODE 0: dual layer from u_in; MODE 1: first dual layer (u_in = W_K v);
 // MODE 2: output D(v) = clip(v - gam W_K^* u_in).
+// The first dual layer needs W_1^* W_K v. Away from the image border (all nine
+// pixels q - a + 1 inside the image) that is one 5 x 5 correlation of v,
+// C[e][f] = sum_p sum_{c - a = e - 2, d - b = f - 2} w_1[p][a][b] w_K[p][c][d],
+// so the P-channel u_0 is never formed there. On the border rows and columns
+// u_0 is zero outside the image, so the terms whose pixel q - a + 1 falls
+// outside drop out: the sum runs over the (a, b) inside, with the channel sum
+// folded into M[a b][c d] = sum_p w_1[p][a][b] w_K[p][c][d].
 template <int P, int MODE>
 __global__ void __launch_bounds__(256, 4) k_ddfb(const float* __restrict__ v,
                                               const float* __restrict__ uin,
                                               float* __restrict__ out, int ny, int nx, float gam,
                                               float ht, const __grid_constant__ DdfbFilters L) {
     using G = DdfbGeom<MODE>;
-    constexpr int UH = G::UH, UW = G::UW, HALO = G::HALO, UP = G::UP, CX = G::CX;
+    constexpr int UH = G::UH, HALO = G::HALO, UP = G::UP, CX = G::CX;
     constexpr int NCH = P / DB_CH;
     extern __shared__ float4 sm4[];
     float* us = reinterpret_cast<float*>(sm4);                 // [2][DB_CH][UH][UP]
-    float* ss = us + 2 * DB_CH * UH * UP;                      // [DB_TH + 2][DB_TW + 2]
+    float* ss = us + G::USTAGE;                                // [DB_TH + 2][DB_TW + 2]
     float* vs = ss + (DB_TH + 2) * (DB_TW + 2);                // [VH][VW] (first layer)
 
     const int tid = threadIdx.x;
@@ -135,56 +146,64 @@ __global__ void __launch_bounds__(256, 4) k_ddfb(const float* __restrict__ v,
         cp_async_commit();
     };
 
+    // the vertical pair of W^* u positions this thread accumulates
+    const bool act = tid < G::NPAIR;
+    const int pc = act ? tid % G::SW : 0, pr = act ? 2 * (tid / G::SW) : 0;
+    float acc0 = 0.f, acc1 = 0.f;
+
     if constexpr (MODE == 1) {
         for (int it = tid; it < G::VH * G::VW; it += 256) {
             const int r = it / G::VW, c = it - r * G::VW;
             const int gi = i0 - 3 + r, gj = j0 - 3 + c;
             vs[it] = (gi >= 0 && gi < ny && gj >= 0 && gj < nx) ? __ldg(vi + (int64_t)gi * nx + gj) : 0.f;
         }
+        __syncthreads();
+        if (act) {
+            // position (pr + t, pc) is vs row pr + t + 2, column pc + 2; the 5 x 5
+            // filter reads vs rows pr + t .. pr + t + 4, columns pc .. pc + 4
+            float vw6[6][5];
+#pragma unroll
+            for (int e = 0; e < 6; ++e)
+#pragma unroll
+                for (int f = 0; f < 5; ++f) vw6[e][f] = vs[(pr + e) * G::VW + pc + f];
+#pragma unroll
+            for (int e = 0; e < 5; ++e)
+#pragma unroll
+                for (int f = 0; f < 5; ++f) {
+                    acc0 = fmaf(L.c5[e * 5 + f], vw6[e][f], acc0);
+                    acc1 = fmaf(L.c5[e * 5 + f], vw6[e + 1][f], acc1);
+                }
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int gi = i0 - 1 + pr + t, gj = j0 - 1 + pc;
+                const bool inside = gi >= 0 && gi < ny && gj >= 0 && gj < nx;
+                if (!inside || (gi >= 1 && gi <= ny - 2 && gj >= 1 && gj <= nx - 2)) continue;
+                // image border: u_0(r) = (W_K v)(r) only for r inside the image
+                const int lr = pr + t + 2, lc = pc + 2;
+                float acc = 0.f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        const int ri = gi - a + 1, rj = gj - b + 1;
+                        if (ri < 0 || ri >= ny || rj < 0 || rj >= nx) continue;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+#pragma unroll
+                            for (int d = 0; d < 3; ++d)
+                                acc = fmaf(L.m81[(a * 3 + b) * 9 + c * 3 + d],
+                                           vs[(lr - a + c) * G::VW + lc - b + d], acc);
+                    }
+                if (t) acc1 = acc;
+                else acc0 = acc;
+            }
+        }
     } else {
         stage(0, 0);
-    }
-    // the vertical pair of W^* u positions this thread accumulates
-    const bool act = tid < G::NPAIR;
-    const int pc = act ? tid % G::SW : 0, pr = act ? 2 * (tid / G::SW) : 0;
-    float acc0 = 0.f, acc1 = 0.f;
-
 #pragma unroll
-    for (int k = 0; k < NCH; ++k) {
-        const int c0 = k * DB_CH;
-        float* ub = us + (k & 1) * DB_CH * UH * UP;
-        if constexpr (MODE == 1) {
-            __syncthreads();   // v staged; the buffer's previous group consumed
-            // u_0 = W_K v for the group's channels at vertical pairs of the staged
-            // block: the 4 x 3 window of v serves both positions and all channels
-            constexpr int UPAIR = UW * (UH / 2);
-            for (int q = tid; q < UPAIR; q += 256) {
-                const int c = q % UW, r = 2 * (q / UW);
-                float vw[4][3];
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 3; ++b) vw[a][b] = vs[(r + a) * G::VW + c + b];
-                const int gi = i0 - HALO + r, gj = j0 - HALO + c;
-                const bool in0 = gi >= 0 && gi < ny && gj >= 0 && gj < nx;
-                const bool in1 = gi + 1 >= 0 && gi + 1 < ny && gj >= 0 && gj < nx;
-#pragma unroll
-                for (int ch = 0; ch < DB_CH; ++ch) {
-                    const float* wk = L.wK + (c0 + ch) * 9;
-                    float u0 = 0.f, u1 = 0.f;
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-#pragma unroll
-                        for (int b = 0; b < 3; ++b) {
-                            u0 = fmaf(wk[a * 3 + b], vw[a][b], u0);
-                            u1 = fmaf(wk[a * 3 + b], vw[a + 1][b], u1);
-                        }
-                    ub[(ch * UH + r) * UP + c + CX] = in0 ? u0 : 0.f;
-                    ub[(ch * UH + r + 1) * UP + c + CX] = in1 ? u1 : 0.f;
-                }
-            }
-            __syncthreads();
-        } else {
+        for (int k = 0; k < NCH; ++k) {
+            const int c0 = k * DB_CH;
+            float* ub = us + (k & 1) * DB_CH * UH * UP;
             if (k + 1 < NCH) {
                 stage((k + 1) & 1, c0 + DB_CH);   // next group in flight
                 cp_async_wait<1>();
@@ -192,30 +211,30 @@ __global__ void __launch_bounds__(256, 4) k_ddfb(const float* __restrict__ v,
                 cp_async_wait<0>();
             }
             __syncthreads();
-        }
-        // W^* u at (q, q + one row): sum_p sum_ab w[p][a][b] u_p(q - a + 1, q - b + 1);
-        // the staged block starts one ring further out than the positions, so
-        // u(q - a + 1) is staged row pr + 2 - a
-        if (act) {
+            // W^* u at (q, q + one row): sum_p sum_ab w[p][a][b] u_p(q - a + 1, q - b + 1);
+            // the staged block starts one ring further out than the positions, so
+            // u(q - a + 1) is staged row pr + 2 - a
+            if (act) {
 #pragma unroll
-            for (int ch = 0; ch < DB_CH; ++ch) {
-                const float* uc = ub + ch * UH * UP + CX;
-                float uw[4][3];
+                for (int ch = 0; ch < DB_CH; ++ch) {
+                    const float* uc = ub + ch * UH * UP + CX;
+                    float uw[4][3];
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                    for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int b = 0; b < 3; ++b) uw[a][b] = uc[(pr + a) * UP + pc + b];
-                const float* wk = L.w + (c0 + ch) * 9;
+                        for (int b = 0; b < 3; ++b) uw[a][b] = uc[(pr + a) * UP + pc + b];
+                    const float* wk = L.w + (c0 + ch) * 9;
 #pragma unroll
-                for (int a = 0; a < 3; ++a)
+                    for (int a = 0; a < 3; ++a)
 #pragma unroll
-                    for (int b = 0; b < 3; ++b) {
-                        acc0 = fmaf(wk[a * 3 + b], uw[2 - a][2 - b], acc0);
-                        acc1 = fmaf(wk[a * 3 + b], uw[3 - a][2 - b], acc1);
-                    }
+                        for (int b = 0; b < 3; ++b) {
+                            acc0 = fmaf(wk[a * 3 + b], uw[2 - a][2 - b], acc0);
+                            acc1 = fmaf(wk[a * 3 + b], uw[3 - a][2 - b], acc1);
+                        }
+                }
             }
+            __syncthreads();   // group consumed before its buffer refills
         }
-        if constexpr (MODE != 1) __syncthreads();   // group consumed before its buffer refills
     }
 
     if constexpr (MODE == 2) {
@@ -305,6 +324,21 @@ cudaError_t ddfb_forward_P(const DenoiserDev& D, const float* x, int ny, int nx,
     DdfbFilters F;
     const float* WK = D.ddfb_w + (size_t)(K - 1) * P * 9;
     for (int q = 0; q < P * 9; ++q) F.wK[q] = WK[q];
+    // first dual layer: M[a b][c d] = sum_p w_1[p][a][b] w_K[p][c][d] and the
+    // 5 x 5 filter of W_1^* W_K, C[e][f] = sum over c - a = e - 2, d - b = f - 2
+    // of M (interior pixels), both accumulated in FP64
+    const float* W1 = D.ddfb_w;
+    double M[81], C[25] = {0.0};
+    for (int ab = 0; ab < 9; ++ab)
+        for (int cd = 0; cd < 9; ++cd) {
+            double m = 0.0;
+            for (int p = 0; p < P; ++p) m += (double)W1[p * 9 + ab] * WK[p * 9 + cd];
+            M[ab * 9 + cd] = m;
+            F.m81[ab * 9 + cd] = (float)m;
+            const int e = cd / 3 - ab / 3 + 2, f = cd % 3 - ab % 3 + 2;
+            C[e * 5 + f] += m;
+        }
+    for (int q = 0; q < 25; ++q) F.c5[q] = (float)C[q];
     cudaError_t e = cudaSuccess;
     const float* cur = nullptr;
     for (int k = 0; k < K - 1 && e == cudaSuccess; ++k) {
