@@ -302,14 +302,8 @@ __global__ void __launch_bounds__(256, 4) k_ddfb(const float* __restrict__ v,
 template <int P, int MODE>
 cudaError_t ddfb_launch(dim3 grid, cudaStream_t s, const float* x, const float* u, float* out,
                         int ny, int nx, float gam, float ht, const DdfbFilters& F) {
-    const size_t smem = DdfbGeom<MODE>::SMEM;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_ddfb<P, MODE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    constexpr size_t smem = DdfbGeom<MODE>::SMEM;
+    static_assert(smem <= 48 * 1024, "dynamic shared memory above 48 KB needs an opt-in");
     return launch_pdl(k_ddfb<P, MODE>, grid, dim3(256), smem, s, x, u, out, ny, nx, gam, ht, F);
 }
 
