@@ -47,6 +47,8 @@ extern "C" pnp_status pnp_denoise_noalloc(const pnp_denoiser* den, pnp_precision
     if (!den || !x || !d) return fail(PNP_EINVAL, "pnp_denoise_noalloc: NULL argument");
     if (ny < 1 || nx < 1 || nimg < 1) return fail(PNP_EINVAL, "pnp_denoise_noalloc: empty image");
     const DenoiserDev& D = den->dev;
+    if (D.ddfb && prec != PNP_FP32)
+        return fail(PNP_ENOTSUP, "pnp_denoise_noalloc: the DDFB denoiser runs in FP32");
     size_t need = 0;
     if (prec == PNP_FP32) {
         need = denoise_fp32_scratch(D, ny, nx, nimg);

@@ -112,6 +112,11 @@ def test_problem_rejects_bad_descriptors_without_gpu(lib):
         Problem(y, h, 0.1, den, blocks=(2, 2), halo=8)  # DDFB uses the direct layout
     with pytest.raises(PnpError):
         Denoiser.ddfb(dw.filters, -dw.gammas, dw.ht)     # gamma_k <= 0
+    dw64 = synth.ddfb_weights(4, 64, 1)
+    den64 = Denoiser.ddfb(dw64.filters, dw64.gammas, dw64.ht)
+    import ctypes as C
+    st = lib.pnp_denoise_noalloc(den64.handle, 1, C.c_void_p(16), 8, 8, 1, C.c_void_p(16), None)
+    assert st == 7                                      # BF16 on a DDFB denoiser: refused
 
 
 def test_stencil_tile_override_is_validated_on_the_host(lib):
