@@ -645,22 +645,23 @@ __global__ void __launch_bounds__(256) k_update_mask(UpdateParams p) {
 }
 
 // ---------------------------------------------------------------------------
-// Wide stencil for large kernels (up to 129 x 129). A block of 32 x 8 threads
+// Wide stencil for large kernels (up to 129 x 129). A block of 32 x 16 threads
 // owns a 64-row x 128-column output tile; the window (64 + kh + 2) x (128 +
-// kw - 1) is filled once with circular wrap (195 KB at 129 x 129). Thread (tx,
-// ty) accumulates rows 8 ty .. 8 ty + 7 at columns tx + 32 q (q = 0..3): for a
+// kw - 1) is filled once with circular wrap (195 KB at 129 x 129, so one block
+// per SM there: 16 warps to hide the shared-memory latency). Thread (tx, ty)
+// accumulates rows 4 ty .. 4 ty + 3 at columns tx + 32 q (q = 0..3): for a
 // fixed offset the 32 lanes of a warp read 32 consecutive window words, so the
 // loads are free of bank conflicts for any pitch. Taps come in groups of four
-// on consecutive rows of one window column: a thread loads the 8 + 3 window
-// values of a column once and applies all four taps to its 8 rows (32
-// multiply-adds per 11 shared-memory loads instead of one per load, the
-// shared-memory pipe being the bound). Only groups holding a nonzero tap are
-// visited (a motion blur of length L has O(L) of its L^2 entries). Sums run
-// over window columns in order, rows ascending; the operator entry points pass
-// no group list and the kernel walks h in groups of four rows itself, in the
-// same order (zero taps add exactly nothing), so both give the same sums.
+// on consecutive rows of one window column: a thread loads the 4 + 3 window
+// values of a column once and applies all four taps to its 4 rows (16
+// multiply-adds per 7 shared-memory loads instead of one per load). Only
+// groups holding a nonzero tap are visited (a motion blur of length L has O(L)
+// of its L^2 entries). Sums run over window columns in order, rows ascending;
+// the operator entry points pass no group list and the kernel walks h in
+// groups of four rows itself, in the same order (zero taps add exactly
+// nothing), so both give the same sums.
 // ---------------------------------------------------------------------------
-constexpr int WD_TW = 128, WD_R = 8, WD_BY = 8, WD_TR = WD_R * WD_BY;
+constexpr int WD_TW = 128, WD_R = 4, WD_BY = 16, WD_TR = WD_R * WD_BY;
 
 static size_t wide_smem(int kh, int kw) {
     return sizeof(float) * (size_t)(WD_TR + kh + 2) * (WD_TW + kw - 1);
@@ -673,7 +674,7 @@ __device__ __forceinline__ void wide_tile(const float* __restrict__ img, int ny,
     const int ay = kh >> 1, ax = kw >> 1;
     const int wy = WD_TR + kh + 2, wp = WD_TW + kw - 1;   // + 3 rows read by the last group
     const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int it = tid; it < wy * wp; it += 256) {
+    for (int it = tid; it < wy * wp; it += 32 * WD_BY) {
         const int r = it / wp, c = it - r * wp;
         int gi = (i0 - ay + r) % ny;
         if (gi < 0) gi += ny;
@@ -730,7 +731,7 @@ __device__ __forceinline__ void wide_tile(const float* __restrict__ img, int ny,
 }
 
 // out = (a (h * x) - y) scale (forward) or scale (h^T x) (adjoint).
-__global__ void __launch_bounds__(256) k_blur_wide(const float* __restrict__ x,
+__global__ void __launch_bounds__(32 * WD_BY) k_blur_wide(const float* __restrict__ x,
                                                    const float* __restrict__ y,
                                                    const float* __restrict__ h,
                                                    const WTap* __restrict__ taps, int ntaps,
@@ -766,7 +767,7 @@ __global__ void __launch_bounds__(256) k_blur_wide(const float* __restrict__ x,
 // Fused x-update with g = H^T r from the wide stencil: the tile's gradient is
 // staged in shared memory, then each thread updates 4 consecutive pixels of a
 // row (the Philox group layout and 16-byte accesses of k_update).
-__global__ void __launch_bounds__(256) k_update_wide(UpdateParams p) {
+__global__ void __launch_bounds__(32 * WD_BY) k_update_wide(UpdateParams p) {
     extern __shared__ float4 sm4[];
     float* win = reinterpret_cast<float*>(sm4);
     const int ny = p.ny, nx = p.nx;
