@@ -79,6 +79,8 @@ def lib():
         _lib.ora_denoise_blockwise.restype = C.c_int
         _lib.ora_stepsizes.argtypes = [C.c_double] * 6 + [d, d]
         _lib.ora_langevin_step.argtypes = [C.POINTER(_Problem), d, u32, u32, d]
+        _lib.ora_langevin_step_window.argtypes = [C.POINTER(_Problem), d, u32, u32, i, i, i, i, d]
+        _lib.ora_langevin_step_window.restype = C.c_int
         _lib.ora_run_chain.argtypes = [C.POINTER(_Problem), d, i, i, i, u32, d, d,
                                        C.POINTER(C.c_int64), d]
         _lib.ora_moments_two_pass.argtypes = [d, i64, i64, d, d]
@@ -225,6 +227,17 @@ def langevin_step(p: Problem, x, t: int, chain: int = 0):
     x = _f64(x)
     out = np.empty_like(x)
     lib().ora_langevin_step(C.byref(p.s), _dp(x), t, chain, _dp(out))
+    return out
+
+
+def langevin_step_window(p: Problem, x, t: int, i0: int, j0: int, wy: int, wx: int,
+                         chain: int = 0):
+    """x^(t+1) of langevin_step at the pixels [i0, i0+wy) x [j0, j0+wx) only."""
+    x = _f64(x)
+    out = np.empty((wy, wx))
+    rc = lib().ora_langevin_step_window(C.byref(p.s), _dp(x), t, chain, i0, j0, wy, wx, _dp(out))
+    if rc != 0:
+        raise ValueError("window outside the image, or a DDFB denoiser")
     return out
 
 

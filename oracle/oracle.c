@@ -288,6 +288,109 @@ void ora_langevin_step(const ora_problem* p, const double* x, uint32_t t, uint32
     free(xi);
 }
 
+/* Standard normal xi[n] of ora_normals for one flat index n: Philox group
+ * floor(n/4), word n mod 4, Box-Muller on the word pair holding it. */
+static double normal_at(uint64_t seed, uint32_t t, uint32_t chain, int64_t n) {
+    const uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    const double two_pi = 6.283185307179586476925286766559;
+    uint32_t ctr[4] = {(uint32_t)(n / 4), t, chain, 0u};
+    uint32_t r[4];
+    ora_philox4x32_10(ctr, key, r);
+    const int k = (int)(n % 4), pair = k / 2;
+    double u0 = ((double)(r[2 * pair] >> 8) + 0.5) * (1.0 / 16777216.0);
+    double u1 = ((double)(r[2 * pair + 1] >> 8) + 0.5) * (1.0 / 16777216.0);
+    double rad = sqrt(-2.0 * log(u0));
+    double ang = two_pi * u1;
+    return (k % 2 == 0) ? rad * cos(ang) : rad * sin(ang);
+}
+
+/* ---------------------------------------------------------------------------
+ * The transition of ora_langevin_step evaluated only at the output pixels of
+ * the window [i0, i0 + wy) x [j0, j0 + wx) of the image (for images too large
+ * to step whole in FP64). Each term is its definition restricted to the
+ * window: the residual r = h * x - y on the window grown by the blur radius
+ * (circular indices into the whole x), g = H^T r on the window, the
+ * denoiser on the crop of x that extends the window by the network's
+ * receptive radius K (ks / 2) (clipped at the image border, where its zero
+ * padding is the image's own), and xi at the pixels' global flat indices.
+ * Sums run in the same order as the whole-image routines, so the window
+ * equals the corresponding part of ora_langevin_step exactly. out: [wy][wx].
+ * Returns 0, or -1 for a window outside the image or a DDFB denoiser.
+ * ------------------------------------------------------------------------- */
+int ora_langevin_step_window(const ora_problem* p, const double* x, uint32_t t, uint32_t chain,
+                             int i0, int j0, int wy, int wx, double* out) {
+    const int ny = p->ny, nx = p->nx;
+    if (wy < 1 || wx < 1 || i0 < 0 || j0 < 0 || i0 + wy > ny || j0 + wx > nx) return -1;
+    if (!p->net && p->ddfb) return -1;
+    const int ry = p->mask ? 0 : p->kh / 2, rx = p->mask ? 0 : p->kw / 2;
+    /* residual on the window grown by (ry, rx): rows i0 - ry .. i0 + wy - 1 + ry */
+    const int ey = wy + 2 * ry, ex = wx + 2 * rx;
+    double* r = (double*)malloc(sizeof(double) * (int64_t)ey * ex);
+    for (int u = 0; u < ey; ++u)
+        for (int v = 0; v < ex; ++v) {
+            const int qi = wrap(i0 - ry + u, ny), qj = wrap(j0 - rx + v, nx);
+            const int64_t q = (int64_t)qi * nx + qj;
+            double s;
+            if (p->mask) {
+                s = p->mask[q] * x[q];
+            } else {
+                s = 0.0;
+                for (int a = 0; a < p->kh; ++a)
+                    for (int b = 0; b < p->kw; ++b)
+                        s += p->h[a * p->kw + b] *
+                             x[(int64_t)wrap(qi - (a - ry), ny) * nx + wrap(qj - (b - rx), nx)];
+            }
+            r[(int64_t)u * ex + v] = s - p->y[q];
+        }
+    /* denoiser on the crop that covers the window's receptive field */
+    double* d = NULL;
+    int ci0 = 0, cj0 = 0, cy = 0, cx = 0;
+    if (p->net) {
+        const int R = p->net->K * (p->net->ks / 2);
+        ci0 = i0 - R < 0 ? 0 : i0 - R;
+        cj0 = j0 - R < 0 ? 0 : j0 - R;
+        const int ci1 = i0 + wy + R > ny ? ny : i0 + wy + R;
+        const int cj1 = j0 + wx + R > nx ? nx : j0 + wx + R;
+        cy = ci1 - ci0;
+        cx = cj1 - cj0;
+        double* crop = (double*)malloc(sizeof(double) * (int64_t)cy * cx);
+        d = (double*)malloc(sizeof(double) * (int64_t)cy * cx);
+        for (int u = 0; u < cy; ++u)
+            memcpy(crop + (int64_t)u * cx, x + (int64_t)(ci0 + u) * nx + cj0, sizeof(double) * cx);
+        ora_denoise(crop, cy, cx, p->net, d);
+        free(crop);
+    }
+    const double gam = p->gamma;
+    const double s2 = p->sigma * p->sigma;
+    const double cprior = p->alpha * gam / (p->eps * p->eps);
+    const double cproj = p->lambda > 0.0 ? gam / p->lambda : 0.0;
+    const double cnoise = sqrt(2.0 * gam);
+    for (int u = 0; u < wy; ++u)
+        for (int v = 0; v < wx; ++v) {
+            const int i = i0 + u, j = j0 + v;
+            const int64_t n = (int64_t)i * nx + j;
+            double g;
+            if (p->mask) {
+                g = p->mask[n] * r[(int64_t)u * ex + v];
+            } else {
+                g = 0.0;
+                for (int a = 0; a < p->kh; ++a)
+                    for (int b = 0; b < p->kw; ++b)
+                        g += p->h[a * p->kw + b] * r[(int64_t)(u + a) * ex + (v + b)];
+            }
+            const double xv = x[n];
+            double val = xv - gam * g / s2;
+            if (d) val += cprior * (d[(int64_t)(i - ci0) * cx + (j - cj0)] - xv);
+            const double pr = xv < 0.0 ? 0.0 : (xv > 1.0 ? 1.0 : xv);
+            val += cproj * (pr - xv);
+            val += cnoise * (p->noise ? normal_at(p->seed, t, chain, n) : 0.0);
+            out[(int64_t)u * wx + v] = val;
+        }
+    free(r);
+    free(d);
+    return 0;
+}
+
 void ora_run_chain(const ora_problem* p, double* x, int t0, int T, int burn_in,
                    uint32_t chain, double* mean, double* m2, int64_t* n_kept,
                    double* samples) {

@@ -26,6 +26,8 @@
  *   ora_denoise_blockwise  pinned (equals whole image iff halo >= K)
  *   ora_langevin_step      pinned (closed-form Gaussian recursion and stationary
  *                          law; projection and linear-prior fixed points)
+ *   ora_langevin_step_window pinned (equals ora_langevin_step bitwise on every
+ *                          window of small images: corners, edges, interior)
  *   ora_run_chain moments  pinned (two-pass vs Welford, stored samples)
  *   ora_stepsizes          pinned (Eq. 10 inequalities)
  *   mask operator (inpainting) pinned (per-pixel closed form and stationary law,
@@ -91,6 +93,12 @@ void ora_stepsizes(double hnorm, double sigma, double alpha, double eps, double 
 
 void ora_langevin_step(const ora_problem* p, const double* x, uint32_t t, uint32_t chain,
                        double* xnew);
+/* ora_langevin_step at the output pixels of the window [i0, i0+wy) x
+ * [j0, j0+wx) only (whole-image x in, out [wy][wx]); for images too large to
+ * step whole. Equal to the corresponding part of ora_langevin_step. Returns
+ * 0, or -1 for a window outside the image or a DDFB denoiser. */
+int ora_langevin_step_window(const ora_problem* p, const double* x, uint32_t t, uint32_t chain,
+                             int i0, int j0, int wy, int wx, double* out);
 /* Runs iterations t = t0 .. t0+T-1 from x (updated in place). Samples
  * x^(t+1) with t+1 > burn_in enter the FP64 Welford moments (mean, m2, *n).
  * samples (optional) receives every kept sample, [n_kept][ny*nx]. */
