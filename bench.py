@@ -1,18 +1,34 @@
 #!/usr/bin/env python3
-"""Throughput benchmark of the PnP-ULA Gaussian-deconvolution sampler on B300.
+"""Throughput benchmark of the PnP-ULA sampler on B300.
 
-A step is one full x-update of the chain (Eq. 8 / Algorithm 1 x-part): blur
-residual, block-wise DnCNN-form denoiser, fused Langevin update with Philox
-noise and Welford moments. Metric: Mpixel-iterations/s = pixels x iterations /
-time. Default workload: 1024 x 1024 Gaussian deconvolution, 9 x 9 uniform
-blur, 20 dB BSNR, 8-layer 64-channel seeded denoiser, 4 x 4 blocks; the
-headline value is the BF16 denoiser form, with the FP32 plain form and the
-MMSE PSNR of both reported beside it.
+Default (``--workload serve``, the headline): the serving form. A seeded
+Poisson stream of sampling jobs (20 jobs/s; sizes uniform over {512, 1024,
+2048, 4096}^2; blur and noise drawn as in the batched workload; 200 burn-in +
+800 kept iterations; MMSE and std returned) is continuously batched by the
+library's server with the BF16 denoiser. A step is one job of the stream:
+``--steps K`` jobs are timed (at most 64), after ``--warmup W`` iterations on
+every distinct job size. value = the stream's pixel-iterations / the server's
+device time (CUDA events around each round's launches); e2e = the same
+pixel-iterations / wall time from the first submission to the last completion
+(host inputs in, host MMSE/std out). Beside it: p50/p99 job latency, the FP32
+one-job-at-a-time baseline (FP32 iteration time measured per size over 50
+iterations, FIFO over the same arrivals: modelled), MMSE PSNR of a served BF16
+job against its FP32 plain chain, the tensor-core conv roofline from a timed
+batch pass over the stream's jobs, the FP64 oracle on the host cores, and the
+single-job 1024^2 and 8192^2 workloads nested as extra keys.
+
+A step of every other workload is one full x-update of the chain (Eq. 8 /
+Algorithm 1 x-part): blur residual, block-wise DnCNN-form denoiser, fused
+Langevin update with Philox noise and Welford moments. Metric:
+Mpixel-iterations/s = pixels x iterations / time.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload deconv1024|deconv8192|deconv128|motion2048|motion4096|
-                                   inpaint1024|poisson1024|batch48|serve]
-                       [--no-quality] [--jobs M]
+                       [--workload serve|deconv1024|deconv8192|deconv128|motion2048|motion4096|
+                                   inpaint1024|poisson1024|ddfb1024|batch48]
+                       [--no-quality] [--no-nested] [--jobs M]
+deconv1024: 1024 x 1024 Gaussian deconvolution, 9 x 9 uniform blur, 20 dB
+BSNR, 8-layer 64-channel seeded denoiser, 4 x 4 blocks (BF16, with the FP32
+plain form, the FP8 variant and the MMSE PSNR of each beside it).
 ddfb1024: the deconv1024 posterior with the DDFB denoiser (Sec. II-B, Example
 2: K = 4 unrolled dual forward-backward layers, P = 64 filters) in FP32.
 inpaint1024: Gaussian-noise inpainting (Sec. IV-A: H = diag(mask), 30 % of the
@@ -66,18 +82,6 @@ def poisson_problem(rank=0):
     w = synth.WORKLOADS[2]
     return synth.make_poisson_problem(w["ny"], w["nx"], synth.blur_from_spec(w["blur"]),
                                       POISSON["eta"], synth.gt_seed(2, rank) + 50)
-
-
-def ncu_traffic(kernel, workload, precision):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
-    if not os.path.exists(path):
-        return None
-    for line in open(path):
-        f = line.split()
-        if len(f) == 5 and not f[0].startswith("#") and f[:3] == [kernel, workload, precision]:
-            return int(f[3]) + int(f[4])
-    return None
 
 
 def load_peaks():
@@ -281,7 +285,6 @@ def run_reference(args):
     if rank != 0:
         return
     cfg_id = WORKLOADS[args.workload]
-    w = synth.WORKLOADS[cfg_id]
     steps = max(1, args.steps)
     n = args.warmup + steps
     crop = 128 if n <= 60 else (64 if n <= 250 else 32)
@@ -300,11 +303,18 @@ def run_reference(args):
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     sample = (f"each step one FP64 oracle iteration on a {crop}x{crop} crop of the "
               f"{prob.shape[0]}x{prob.shape[1]} workload (same blur, noise, network)")
+    if cfg_id == 5:
+        sample += "; the image is the first job of the serving stream"
+        wname = "serve"
+    elif cfg_id == 4:
+        wname = "batch48"
+    else:
+        wname = (args.workload if poisson or inpaint or args.workload == "ddfb1024"
+                 else synth.WORKLOADS[cfg_id]["name"])
     line = dict(metric=METRIC, value=val, unit=UNIT, n_gpus=args.gpus, steps=steps,
                 warmup=args.warmup, ms_per_step=1e3 * dt / steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload=f"{args.workload if poisson or inpaint or args.workload == 'ddfb1024' else w['name']} "
-                                     "(oracle, bounded crop sample)"),
+                config=dict(workload=f"{wname} (oracle, bounded crop sample)"),
                 cpu_baseline=dict(kind="oracle", cores=cores, sample=sample, value=val, unit=UNIT),
                 e2e=dict(value=val, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
@@ -319,11 +329,12 @@ def _percentile(v, q):
     return v[lo] + (v[hi] - v[lo]) * (k - lo)
 
 
-def _fp32_iter_time(P, torch, den, prob, stream, iters=5):
-    """Device time of one FP32 plain iteration (eager, CUDA events)."""
+def _fp32_iter_time(P, torch, den, prob, stream, iters=50):
+    """Device time of one FP32 plain iteration (graph replay, CUDA events on
+    the problem's stream, mean over `iters` iterations after 3 warm-up ones)."""
     gp = P.Problem(prob.y, prob.h, prob.sigma, den, seed=prob.seed, precision="fp32",
                    stream=stream.cuda_stream)
-    gp.step(2)
+    gp.step(3)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -332,6 +343,49 @@ def _fp32_iter_time(P, torch, den, prob, stream, iters=5):
     torch.cuda.synchronize()
     gp.close()
     return e0.elapsed_time(e1) / iters / 1e3
+
+
+KTIMERS = ("blur", "update", "conv_fp32", "conv_tc", "conv_edge", "conv_last", "zupdate")
+
+
+def _source_sha(kernel):
+    """Short hash of the CUDA source a kernel is built from (ties a committed
+    ncu traffic figure to the kernel version it was measured on)."""
+    import hashlib
+    name = ("k_conv_tc.cu" if kernel.startswith("k_conv_tc") or kernel.startswith("k_first_tc")
+            else "k_ddfb.cu" if kernel.startswith("k_ddfb") else "k_stencil.cu")
+    path = os.path.join(ROOT, "paper_2511_00870_b300", "csrc", name)
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:12]
+
+
+def ncu_traffic(kernel, workload, precision):
+    """(DRAM bytes per launch, note) of `kernel` from the committed ncu summary:
+    bytes only when the line was captured on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None, "no ncu capture committed"
+    cur = _source_sha(kernel)
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 5 and not f[0].startswith("#") and f[:3] == [kernel, workload, precision]:
+            if len(f) >= 6 and f[5] == cur:
+                return int(f[3]) + int(f[4]), f"profiles/ncu_traffic.txt, ncu capture of source {cur}"
+            return None, "kernel source changed since the committed ncu capture"
+    return None, "no ncu capture of this kernel and workload committed"
+
+
+def _tc_roofline(peaks, prec, flop, avg_ms, kernel, workload):
+    """Tensor-core conv roofline for a kernel timed alone by per-launch CUDA
+    events in a short eager pass: the burst peak (FP8: x nominal ratio 2)."""
+    achieved = flop / (avg_ms * 1e-3) / 1e12
+    pk = peaks["bf16"] * (2 if prec == "fp8" else 1)
+    traffic, tnote = ncu_traffic(kernel, workload, prec)
+    return dict(bound="tensor", achieved=round(achieved, 2), peak=pk, unit="TFLOP/s",
+                frac=round(achieved / pk, 4), traffic=traffic, traffic_source=tnote, kernel=kernel,
+                flop_per_launch=flop, avg_launch_ms=round(avg_ms, 5),
+                peak_kind=f"{prec} burst ({peaks['src']}"
+                          + (", bf16 x nominal ratio 2" if prec == "fp8" else "")
+                          + "): kernel timed alone by per-launch CUDA events in a short eager pass")
 
 
 def run_batch(args, P, torch, stream, ws, rank, local):
@@ -374,7 +428,8 @@ def run_batch(args, P, torch, stream, ws, rank, local):
         b.close()
     if rank != 0:
         return
-    achieved = 2.0 * 64 * 64 * 9 * npix / (out["bf16"]["conv_tc_avg_ms"] * 1e-3) / 1e12
+    roof = _tc_roofline(peaks, "bf16", 2.0 * 64 * 64 * 9 * npix, out["bf16"]["conv_tc_avg_ms"],
+                        "k_conv_tc<0,0> (48-job table)", "batch48")
     sizes = [p.y.shape[0] for p in probs]
     line = dict(
         metric=METRIC, value=round(out["bf16"]["value"], 3), unit=UNIT, n_gpus=ws,
@@ -385,9 +440,7 @@ def run_batch(args, P, torch, stream, ws, rank, local):
                              f"15-40 dB, K=8 F=64 BF16, one launch per layer over all jobs",
                     precision="bf16", graph="one CUDA graph per batch iteration",
                     l2="working set per step > 126 MB L2"),
-        roofline=dict(bound="tensor", achieved=round(achieved, 2), peak=peaks["bf16_sus"],
-                      unit="TFLOP/s", frac=round(achieved / peaks["bf16_sus"], 4), traffic=None,
-                      kernel="k_conv_tc (48-job table)", peak_kind=f"bf16 sustained ({peaks['src']})"),
+        roofline=roof,
         fp32_plain=dict(value=round(out["fp32"]["value"], 3), unit=UNIT, steps=out["fp32"]["steps"],
                         speedup_bf16=round(out["bf16"]["value"] / out["fp32"]["value"], 3)),
         gpu_launches=int(round(out["bf16"]["launches_per_iter"])) * args.steps,
@@ -397,22 +450,75 @@ def run_batch(args, P, torch, stream, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def _stencil_roofline(peaks, kern, npix, poisson=False, wide_h=None, iters=None):
+    """Stencils against HBM from the eager per-kernel timing: algorithmic bytes
+    per pixel (r = Hx - y: read x, y, write r: 12 B; update while sampling:
+    read r, x, d, mean, m2, write x, mean, m2: 32 B, Poisson + z2: 36 B;
+    Poisson z-update: read x, z1, z2, y, write z1, z2: 24 B) x the pixels of
+    one iteration (npix, all jobs) x iterations / the kernel's total time
+    (iters = None: one launch per iteration). Large (wide) kernels add their
+    FMA rate against the FP32 FFMA peak."""
+    out = {}
+    for kname, bpp in (("blur", 12), ("update", 36 if poisson else 32), ("zupdate", 24)):
+        n = kern["counts"].get(kname, 0)
+        if not n:
+            continue
+        avg = kern["breakdown"][kname] / n
+        it = n if iters is None else iters
+        gbs = bpp * npix * it / (kern["breakdown"][kname] * 1e-3) / 1e9
+        out[kname] = dict(avg_us=round(avg * 1e3, 2), bytes_per_pixel=bpp,
+                          achieved_gbs=round(gbs, 1), frac=round(gbs / peaks["hbm"], 4))
+        if wide_h is not None and kname != "zupdate":
+            nnz = int(np.count_nonzero(wide_h.astype(np.float32)))
+            tf = 2.0 * nnz * npix * it / (kern["breakdown"][kname] * 1e-3) / 1e12
+            alu = 148 * 128 * 2 * peaks["sm_max"] / 1e6
+            out[kname].update(nonzero_taps=nnz, achieved_tflops=round(tf, 2),
+                              alu_frac=round(tf / alu, 4), alu_peak_tflops=round(alu, 1))
+    if out:
+        out["peak_gbs"] = peaks["hbm"]
+        out["peak_kind"] = f"HBM copy ({peaks['src']})"
+    return out
+
+
+def _timed_kernels(P, torch, run, n_timed):
+    """Per-kernel device time of `n_timed` eager iterations (CUDA events
+    around every launch): {name: ms}, {name: launches}."""
+    P.pnp_kernel_timer(True)
+    run(n_timed)
+    torch.cuda.synchronize()
+    tot = {k: P.pnp_kernel_timer_read(k) for k in KTIMERS}
+    P.pnp_kernel_timer(False)
+    return ({k: v[0] for k, v in tot.items()}, {k: v[1] for k, v in tot.items()})
+
+
 def run_serve(args, P, torch, stream, ws, rank, local):
-    """Serving form: a seeded Poisson stream of sampling jobs (20 jobs/s), each
-    200 burn-in + 800 kept iterations, continuously batched by the server; a
-    bounded run of the first --jobs arrivals. The FP32 one-job-at-a-time
-    baseline is measured per image size and applied to the same arrivals."""
+    """Serving form (the headline): a seeded Poisson stream of sampling jobs
+    (20 jobs/s), each 200 burn-in + 800 kept iterations, continuously batched
+    by the server; a bounded run of the first K arrivals (K = --steps, at most
+    64). The FP32 one-job-at-a-time baseline is modelled from FP32 iteration
+    times measured per image size on the same GPU."""
     import threading as th
     peaks = load_peaks()
-    n = args.jobs
+    n = max(1, min(args.jobs if args.jobs else args.steps, 64))
     specs = synth.serving_jobs(n, seed=5000 + 31 * rank)
     arrivals = synth.poisson_arrivals(n, 20.0, seed=5000 + 31 * rank)
-    probs = []
-    for sp in specs:
-        probs.append(synth.make_problem(sp["size"], sp["size"], sp["h"], sp["bsnr"], sp["gt_seed"]))
+    probs = [synth.make_problem(sp["size"], sp["size"], sp["h"], sp["bsnr"], sp["gt_seed"])
+             for sp in specs]
     den = P.Denoiser.from_weights(synth.workload_denoiser(2))
     T, TB = 1000, 200
-    free, total = torch.cuda.mem_get_info()
+    # warm-up: every distinct (size, blur size) runs W iterations once, so the
+    # per-size one-time work (stencil tile timing, lazy kernel setup) is done
+    warm = {}
+    for p in probs:
+        warm.setdefault((p.y.shape, p.h.shape), p)
+    for p in warm.values():
+        gw = P.Problem(p.y, p.h, p.sigma, den, seed=p.seed, precision="bf16",
+                       stream=stream.cuda_stream)
+        gw.step(args.warmup)
+        gw.sync()
+        gw.close()
+    torch.cuda.synchronize()
+    free, _ = torch.cuda.mem_get_info()
     srv = P.Server(den, precision="bf16", hbm_budget_bytes=int(0.8 * free), round_iters=8)
     ids = [None] * n
     t_start = 0.0
@@ -426,23 +532,29 @@ def run_serve(args, P, torch, stream, ws, rank, local):
             ids[k] = srv.submit(p.y, p.h, p.sigma, T, TB, seed=p.seed)
 
     rank_barrier(ws)
-    t_start = time.perf_counter()
+    launches0 = P.pnp_launch_count()
     sampler = ClockSampler(local)
     sampler.start()
+    t_start = time.perf_counter()
     thr = th.Thread(target=submitter)
     thr.start()
     thr.join()
     for jid in ids:
         srv.wait(jid, 3600)
+    t_end = time.perf_counter()
     ck = sampler.stop()
+    launches = P.pnp_launch_count() - launches0
+    dev_s = srv.device_seconds()
     times = [srv.times(j) for j in ids]
     lat = [t["done"] - t["submit"] for t in times]
     span = max(t["done"] for t in times) - min(t["submit"] for t in times)
     pix_iters = sum(p.y.size for p in probs) * T
-    value, _ = replica_rate(pix_iters, span, ws)
-    # quality at equal PSNR on the first (smallest-index) job: BF16 served vs FP32 plain chain
-    q = probs[0]
-    _, mm16, _ = srv.poll(ids[0])
+    value, _ = replica_rate(pix_iters, dev_s, ws)
+    e2e_value, _ = replica_rate(pix_iters, span, ws)
+    # quality at equal PSNR on the smallest job: BF16 served vs its FP32 plain chain
+    kq = min(range(n), key=lambda k: probs[k].y.size)
+    q = probs[kq]
+    _, mm16, _ = srv.poll(ids[kq])
     srv.close()
     g32 = P.Problem(q.y, q.h, q.sigma, den, seed=q.seed, burn_in=TB, precision="fp32",
                     stream=stream.cuda_stream)
@@ -450,61 +562,274 @@ def run_serve(args, P, torch, stream, ws, rank, local):
     mm32, _, _ = g32.moments()
     g32.close()
     psnr = lambda m: 10 * math.log10(1.0 / float(np.mean((m - q.xbar) ** 2)))
+    # roofline: the tensor-core conv over a table of the stream's jobs (one
+    # launch per layer over all of them, as in the server's rounds), timed alone
+    sub = probs[:min(n, 8)]
+    b = P.Batch([dict(y=p.y, h=p.h, sigma=p.sigma, seed=p.seed, burn_in=TB) for p in sub], den,
+                precision="bf16", stream=stream.cuda_stream)
+    b.step(3)
+    kb, kc = _timed_kernels(P, torch, b.step, 10)
+    b.close()
+    npix_b = sum(p.y.size for p in sub)
+    roof = _tc_roofline(peaks, "bf16", 2.0 * 64 * 64 * 9 * npix_b, kb["conv_tc"] / max(kc["conv_tc"], 1),
+                        "k_conv_tc<0,0>", "serve")
+    roof["units_per_launch"] = f"{npix_b} pixels of {len(sub)} served jobs x 73728 FLOP"
     # FP32 one-job-at-a-time: measured per-size iteration time, FIFO over the same arrivals
     per_size = {}
     for p in probs:
-        s = p.y.shape[0]
-        if s not in per_size:
-            per_size[s] = _fp32_iter_time(P, torch, den, p, stream)
+        key = (p.y.shape[0], p.h.shape)
+        if key not in per_size:
+            per_size[key] = _fp32_iter_time(P, torch, den, p, stream, iters=50)
     finish, lat32 = 0.0, []
     for k, p in enumerate(probs):
         start = max(arrivals[k], finish)
-        finish = start + T * per_size[p.y.shape[0]]
+        finish = start + T * per_size[(p.y.shape[0], p.h.shape)]
         lat32.append(finish - arrivals[k])
     value32 = pix_iters / (finish - arrivals[0]) / 1e6
     if rank != 0:
-        return
+        return None
     sizes = [p.y.shape[0] for p in probs]
     h2d = sum(p.y.size * 4 + p.h.size * 4 for p in probs)
     d2h = sum(2 * p.y.size * 8 for p in probs)
-    iters = n * T
     line = dict(
-        metric=METRIC, value=round(value, 3), unit=UNIT, n_gpus=ws, steps=T, warmup=0,
-        ms_per_step=None, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="bf16",
-        data="synthetic",
-        config=dict(workload=f"serve: first {n} jobs of a Poisson stream at 20 jobs/s, sizes "
-                             f"{sorted(set(sizes))}, 200 burn-in + 800 kept iterations, MMSE + std, "
-                             f"K=8 F=64 BF16; continuous batching, HBM-budget admission",
-                    precision="bf16", l2="working set > 126 MB L2"),
+        metric=METRIC, value=round(value, 3), unit=UNIT, n_gpus=ws, steps=n, warmup=args.warmup,
+        ms_per_step=round(1e3 * span / n, 3), higher_is_better=True, scaling="weak",
+        vs_baseline=None, dtype="bf16", data="synthetic",
+        config=dict(workload=f"serve: the first {n} jobs of a seeded Poisson stream at 20 jobs/s, "
+                             f"sizes {sorted(set(sizes))} (uniform over 512..4096 squared), blur and "
+                             "BSNR drawn as in the batched workload, 200 burn-in + 800 kept "
+                             "iterations, MMSE + std maps; K=8 F=64 DnCNN-form denoiser in BF16; "
+                             "continuous batching with HBM-budget admission",
+                    step="one job of the stream (1000 iterations)",
+                    value="stream pixel-iterations / server device time (CUDA events around every "
+                          "round's launches)",
+                    precision="bf16", l2="working set per round > 126 MB L2"),
+        roofline=roof,
+        e2e=dict(value=round(e2e_value, 3), unit=UNIT, h2d_bytes_per_step=h2d / n,
+                 d2h_bytes_per_step=d2h / n,
+                 note="wall time from the first submission to the last completion: host y and h "
+                      "copied in at admission, FP64 MMSE and std maps copied out at retirement"),
         latency=dict(p50_s=round(_percentile(lat, 50), 3), p99_s=round(_percentile(lat, 99), 3),
-                     unit="s", definition="completion - submission"),
+                     unit="s", definition="completion - submission", jobs=n),
         fp32_plain=dict(value=round(value32, 3), unit=UNIT,
                         p50_s=round(_percentile(lat32, 50), 3), p99_s=round(_percentile(lat32, 99), 3),
-                        note="one job at a time, FIFO; per-size FP32 iteration time measured here "
-                             "(5 iterations each) times T"),
+                        kind="modelled",
+                        note="one job at a time, FIFO over the same arrivals; FP32 plain iteration "
+                             "time measured on this GPU per image and blur size (50 iterations, "
+                             "graph replay) times T = 1000",
+                        per_size_ms={f"{k[0]}x{k[0]} h{k[1][0]}": round(1e3 * v, 4)
+                                     for k, v in per_size.items()}),
         speedup_bf16=round(value / value32, 3),
+        e2e_speedup_bf16=round(e2e_value / value32, 3),
         quality=dict(job=f"{q.y.shape[0]}x{q.y.shape[1]}", psnr_bf16_served_db=round(psnr(mm16), 4),
                      psnr_fp32_plain_db=round(psnr(mm32), 4),
                      delta_db=round(psnr(mm16) - psnr(mm32), 4)),
-        e2e=dict(value=round(value, 3), unit=UNIT, h2d_bytes_per_step=h2d / iters,
-                 d2h_bytes_per_step=d2h / iters,
-                 note="the served path is end to end: host inputs in, host MMSE/std out"),
+        gpu_launches=int(launches),
         clocks=ck,
+        kernel_breakdown_ms=dict(batch_pass=kb, launches=kc, iterations=10, jobs=len(sub)),
+        stencil_roofline=_stencil_roofline(peaks, dict(breakdown=kb, counts=kc), npix_b, iters=10),
+        server=dict(device_s=round(dev_s, 3), wall_s=round(span, 3), timed_region_s=round(t_end - t_start, 3)),
     )
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def measure_single(args, P, torch, stream, ws, rank, local, workload, precs, steps, warmup,
+                   quality=True, cpu_baseline=True):
+    """One workload's single-job line: device-timed graph replay (value), the
+    same K iterations end to end through the public API with host buffers
+    (e2e), per-kernel eager timing (roofline, stencils), MMSE PSNR per
+    precision and the FP64 oracle on the host cores. Returns the line (rank 0)
+    or None."""
+    cfg_id = WORKLOADS[workload]
+    w = synth.WORKLOADS[cfg_id]
+    poisson = workload == "poisson1024"
+    inpaint = workload == "inpaint1024"
+    ddfb = workload == "ddfb1024"
+    prob = (poisson_problem(rank) if poisson else inpainting_problem(rank) if inpaint
+            else synth.workload_problem(cfg_id, job=rank))
+    dw = synth.workload_denoiser(cfg_id)
+    if ddfb:
+        dd = ddfb_net()
+        den = P.Denoiser.ddfb(dd.filters, dd.gammas, dd.ht)
+    else:
+        den = P.Denoiser.from_weights(dw)
+    ny, nx = prob.shape
+    npix = ny * nx
+    peaks = load_peaks()
+    precs = list(precs)
+    if w["F"] != 64 or ddfb:
+        precs = ["fp32"]
+
+    def make_problem(prec, burn_in):
+        kw = dict(blocks=w["blocks"], halo=0, seed=prob.seed, burn_in=burn_in, precision=prec,
+                  stream=stream.cuda_stream)
+        if poisson:
+            return P.Problem(prob.y, prob.h, 0.0, den, noise_model="poisson", eta=prob.eta,
+                             rho1=POISSON["rho1"], rho2=POISSON["rho2"], **kw)
+        if inpaint:
+            return P.Problem(prob.y, None, prob.sigma, den, mask=prob.mask, x0=prob.x0, **kw)
+        return P.Problem(prob.y, prob.h, prob.sigma, den, **kw)
+
+    results = {}
+    clocks = None
+    for prec in precs:
+        gp = make_problem(prec, w["burn_in"])
+        st = steps if prec == precs[0] else min(steps, 200)
+        gp.step(warmup)
+        torch.cuda.synchronize()
+        rank_barrier(ws)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gp.step(st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rank_barrier(ws)
+        ck = sampler.stop()
+        rate, slow = replica_rate(npix * st, e0.elapsed_time(e1) / 1e3, ws)
+        results[prec] = dict(ms=slow * 1e3, steps=st, value=rate)
+        if prec == precs[0]:
+            clocks = ck
+        # per-kernel timing: the same iterations launched eagerly with CUDA events
+        n_timed = max(5, min(steps, 20))
+        kb, kc = _timed_kernels(P, torch, gp.step, n_timed)
+        name = "conv_fp32" if prec == "fp32" else "conv_tc"
+        results[prec]["kernel"] = dict(name=name, avg_ms=kb[name] / max(kc[name], 1),
+                                       launches=kc[name], breakdown=kb, counts=kc,
+                                       launches_per_iter=sum(kc.values()) / n_timed)
+        gp.close()
+
+    # end-to-end through the public API with host buffers: create (H2D of y, h),
+    # run K iterations, read MMSE + std back (D2H)
+    prec0 = precs[0]
+    torch.cuda.synchronize()
+    rank_barrier(ws)
+    t0 = time.perf_counter()
+    gp = make_problem(prec0, 0)
+    gp.run_chain(steps, 0)
+    mm, sd, _ = gp.moments()
+    e2e_rate, _ = replica_rate(npix * steps, time.perf_counter() - t0, ws)
+    gp.close()
+    e2e = dict(value=e2e_rate, unit=UNIT,
+               h2d_bytes_per_step=(prob.y.size * 4 + (prob.mask.size * 4 + prob.x0.size * 4 if inpaint
+                                                       else prob.h.size * 4)) / steps,
+               d2h_bytes_per_step=2 * npix * 8 / steps)
+
+    # quality at equal PSNR: the full chain of the workload for each precision
+    qual = None
+    if quality and rank == 0 and cfg_id in (1, 2):
+        qual = {}
+        for prec in precs:
+            gq = make_problem(prec, w["burn_in"])
+            gq.run_chain(w["T"], w["burn_in"])
+            mq, _, _ = gq.moments()
+            qual[f"psnr_{prec}_db"] = round(10 * math.log10(1.0 / float(np.mean((mq - prob.xbar) ** 2))), 4)
+            gq.close()
+        if "bf16" in precs and "fp32" in precs:
+            qual["delta_db"] = round(qual["psnr_bf16_db"] - qual["psnr_fp32_db"], 4)
+        if "fp8" in precs and "fp32" in precs:
+            qual["delta_fp8_db"] = round(qual["psnr_fp8_db"] - qual["psnr_fp32_db"], 4)
+        qual["chain"] = f"{w['T']} iterations, {w['burn_in']} burn-in"
+    if rank != 0:
+        return None
+
+    head = results[precs[0]]
+    kern = head["kernel"]
+    K, F = w["K"], w["F"]
+    if kern["name"] == "conv_tc":
+        ktag = "k_conv_tc<0,1>" if precs[0] == "fp8" else "k_conv_tc<0,0>"
+        roof = _tc_roofline(peaks, precs[0], 2.0 * F * F * 9 * npix, kern["avg_ms"], ktag, workload)
+    elif ddfb:
+        # a dual layer (the conv_fp32 timer; the first layer and the output run
+        # under conv_edge) streams the P-channel dual variable: read v and u, write u
+        bpp = 4 + 8 * 64
+        gbs = bpp * npix / (kern["avg_ms"] * 1e-3) / 1e9
+        traffic, tnote = ncu_traffic("k_ddfb<64,0>", workload, "fp32")
+        roof = dict(bound="hbm", achieved=round(gbs, 1), peak=peaks["hbm"], unit="GB/s",
+                    frac=round(gbs / peaks["hbm"], 4), traffic=traffic, traffic_source=tnote,
+                    kernel="k_ddfb<64,0>", bytes_per_pixel=bpp, peak_kind=f"HBM copy ({peaks['src']})")
+    else:
+        flop = 2.0 * F * F * 9 * npix
+        achieved = flop / (kern["avg_ms"] * 1e-3) / 1e12
+        alu_peak = 148 * 128 * 2 * peaks["sm_max"] / 1e6
+        roof = dict(bound="alu", achieved=round(achieved, 2), peak=round(alu_peak, 2),
+                    unit="TFLOP/s", frac=round(achieved / alu_peak, 4), traffic=None,
+                    kernel="k_conv3x3<64,64>", peak_kind="FP32 FFMA: 148 SM x 128 lanes x 2 x max clock")
+    wide = prob.h if (not poisson and not inpaint and max(prob.h.shape) > 31) else None
+    stencils = _stencil_roofline(peaks, kern, npix, poisson=poisson, wide_h=wide)
+    cpu = None
+    if cpu_baseline:
+        try:
+            cpu = oracle_baseline(cfg_id, budget_s=15.0, poisson=poisson, inpaint=inpaint, ddfb=ddfb)
+        except Exception as ex:  # report, never fake
+            cpu = dict(value=None, unit=UNIT, cores=None, kind="oracle", sample=f"failed: {ex}")
+    if poisson:
+        wl = (f"poisson1024: {ny}x{nx} Poisson counts, peak eta={prob.eta:g}, rho1={POISSON['rho1']:g}, "
+              f"rho2={POISSON['rho2']:g}, AXDA + PSGLA, blur {w['blur'][0]} {w['blur'][1]}x{w['blur'][1]}, ")
+    elif inpaint:
+        wl = (f"inpaint1024: {ny}x{nx} grayscale, 30 % of the pixels observed, 15 dB input SNR, "
+              "cubic-interpolant start, ")
+    elif ddfb:
+        wl = (f"ddfb1024: {ny}x{nx} grayscale, {w['bsnr']} dB BSNR, DDFB prior K=4 P=64 (FP32), "
+              f"blur {w['blur'][0]} {w['blur'][1]}x{w['blur'][1]}, ")
+    else:
+        wl = (f"{w['name']}: {ny}x{nx} grayscale, {w['bsnr']} dB BSNR, "
+              f"blur {w['blur'][0]} {w['blur'][1]}x{w['blur'][1]}, ")
+    wl += ("" if ddfb else f"DnCNN-form K={K} F={F}, ") + \
+        f"{w['blocks'][0]}x{w['blocks'][1]} blocks (halo-exchange-free), 1 chain per GPU"
+    line = dict(
+        metric=METRIC, value=round(head["value"], 3), unit=UNIT, n_gpus=ws, steps=steps,
+        warmup=warmup, ms_per_step=round(head["ms"] / steps, 4), higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype=("bf16" if precs[0] == "bf16" else
+                                                 "fp8" if precs[0] == "fp8" else "f32"),
+        data="synthetic",
+        config=dict(workload=wl, precision=precs[0],
+                    l2="working set per step > 126 MB L2 (activation planes)",
+                    graph="one CUDA graph per iteration"),
+        roofline=roof,
+        cpu_baseline=cpu,
+        e2e=e2e,
+        gpu_launches=int(round(kern["launches_per_iter"])) * steps,
+        clocks=clocks,
+        kernel_breakdown_ms={p: results[p]["kernel"]["breakdown"] for p in results},
+        stencil_roofline=stencils,
+    )
+    if "fp32" in results and precs[0] != "fp32":
+        line["fp32_plain"] = dict(value=round(results["fp32"]["value"], 3), unit=UNIT,
+                                  ms_per_step=round(results["fp32"]["ms"] / results["fp32"]["steps"], 4),
+                                  steps=results["fp32"]["steps"],
+                                  speedup_bf16=round(head["value"] / results["fp32"]["value"], 3))
+    if "fp8" in results and precs[0] != "fp8":
+        r8 = results["fp8"]
+        r8roof = _tc_roofline(peaks, "fp8", 2.0 * F * F * 9 * npix, r8["kernel"]["avg_ms"],
+                              "k_conv_tc<0,1>", workload)
+        line["fp8_variant"] = dict(
+            value=round(r8["value"], 3), unit=UNIT, ms_per_step=round(r8["ms"] / r8["steps"], 4),
+            steps=r8["steps"], speedup_vs_bf16=round(r8["value"] / head["value"], 3),
+            conv_tc_tflops=r8roof["achieved"], conv_tc_frac=r8roof["frac"],
+            peak_kind=r8roof["peak_kind"],
+            note="E4M3 weights (per-output-channel scales) and activations (per-layer static scales)")
+    if qual:
+        line["quality"] = qual
+    line["latency"] = dict(p50_s=None, p99_s=None, note="single-job workload")
+    return line
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="deconv1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="serve", choices=sorted(WORKLOADS))
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-nested", action="store_true",
+                    help="serve: skip the nested single-job deconv1024 / deconv8192 lines")
     ap.add_argument("--precisions", default="bf16,fp32,fp8")
-    ap.add_argument("--jobs", type=int, default=16, help="serve: number of arrivals")
+    ap.add_argument("--jobs", type=int, default=0, help="serve: number of arrivals (default: --steps)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -523,240 +848,41 @@ def main():
         build.build()
     if ws > 1:
         torch.distributed.barrier()
-
-    if args.workload in ("batch48", "serve"):
-        stream = torch.cuda.Stream()
-        torch.cuda.set_stream(stream)
-        fn = run_batch if args.workload == "batch48" else run_serve
-        fn(args, P, torch, stream, ws, rank, local)
-        if ws > 1:
-            torch.distributed.destroy_process_group()
-        return
-
-    cfg_id = WORKLOADS[args.workload]
-    w = synth.WORKLOADS[cfg_id]
-    poisson = args.workload == "poisson1024"
-    inpaint = args.workload == "inpaint1024"
-    prob = (poisson_problem(rank) if poisson else inpainting_problem(rank) if inpaint
-            else synth.workload_problem(cfg_id, job=rank))
-    dw = synth.workload_denoiser(cfg_id)
-    ddfb = args.workload == "ddfb1024"
-    if ddfb:
-        dd = ddfb_net()
-        den = P.Denoiser.ddfb(dd.filters, dd.gammas, dd.ht)
-    else:
-        den = P.Denoiser.from_weights(dw)
-    ny, nx = prob.shape
-    npix = ny * nx
     # a dedicated stream: the problems enqueue on it and the events are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    peaks = load_peaks()
-    precs = [p for p in args.precisions.split(",") if p]
-    if w["F"] != 64 or ddfb:
-        precs = ["fp32"]
 
-    def barrier():
-        rank_barrier(ws)
-
-    def make_problem(prec, burn_in):
-        kw = dict(blocks=w["blocks"], halo=0, seed=prob.seed, burn_in=burn_in, precision=prec,
-                  stream=stream.cuda_stream)
-        if poisson:
-            return P.Problem(prob.y, prob.h, 0.0, den, noise_model="poisson", eta=prob.eta,
-                             rho1=POISSON["rho1"], rho2=POISSON["rho2"], **kw)
-        if inpaint:
-            return P.Problem(prob.y, None, prob.sigma, den, mask=prob.mask, x0=prob.x0, **kw)
-        return P.Problem(prob.y, prob.h, prob.sigma, den, **kw)
-
-    results = {}
-    clocks = None
-    for prec in precs:
-        gp = make_problem(prec, w["burn_in"])
-        steps = args.steps if prec == precs[0] else min(args.steps, 200)
-        gp.step(args.warmup)
-        torch.cuda.synchronize()
-        barrier()
-        torch.cuda.synchronize()
-        sampler = ClockSampler(local)
-        sampler.start()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        gp.step(steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        ck = sampler.stop()
-        rate, slow = replica_rate(npix * steps, e0.elapsed_time(e1) / 1e3, ws)
-        results[prec] = dict(ms=slow * 1e3, steps=steps, value=rate)
-        if prec == precs[0]:
-            clocks = ck
-        # dominant-kernel timing: same iterations launched eagerly with CUDA events
-        P.pnp_kernel_timer(True)
-        n_timed = max(5, min(args.steps, 20))
-        gp.step(n_timed)
-        torch.cuda.synchronize()
-        name = "conv_fp32" if prec == "fp32" else "conv_tc"
-        kms, kn = P.pnp_kernel_timer_read(name)
-        tot = {k: P.pnp_kernel_timer_read(k) for k in ("blur", "update", "conv_fp32", "conv_tc",
-                                                        "conv_edge", "conv_last", "zupdate")}
-        P.pnp_kernel_timer(False)
-        results[prec]["kernel"] = dict(name=name, avg_ms=kms / max(kn, 1), launches=kn,
-                                       breakdown={k: v[0] for k, v in tot.items()},
-                                       counts={k: v[1] for k, v in tot.items()},
-                                       launches_per_iter=sum(v[1] for v in tot.values()) / n_timed)
-        gp.close()
-
-    # end-to-end through the public API with host buffers: create (H2D of y, h),
-    # run K iterations, read MMSE + std back (D2H)
-    prec0 = precs[0]
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    gp = make_problem(prec0, 0)
-    gp.run_chain(args.steps, 0)
-    mm, sd, _ = gp.moments()
-    e2e_rate, t_e2e = replica_rate(npix * args.steps, time.perf_counter() - t0, ws)
-    gp.close()
-    e2e = dict(value=e2e_rate, unit=UNIT,
-               h2d_bytes_per_step=(prob.y.size * 4 + (prob.mask.size * 4 + prob.x0.size * 4 if inpaint
-                                                       else prob.h.size * 4)) / args.steps,
-               d2h_bytes_per_step=2 * npix * 8 / args.steps)
-
-    # quality at equal PSNR: the full chain of the workload for each precision
-    quality = None
-    if not args.no_quality and rank == 0 and cfg_id in (1, 2):
-        quality = {}
-        for prec in precs:
-            gq = make_problem(prec, w["burn_in"])
-            gq.run_chain(w["T"], w["burn_in"])
-            mq, _, _ = gq.moments()
-            quality[f"psnr_{prec}_db"] = round(10 * math.log10(1.0 / float(np.mean((mq - prob.xbar) ** 2))), 4)
-            gq.close()
-        if "bf16" in precs and "fp32" in precs:
-            quality["delta_db"] = round(quality["psnr_bf16_db"] - quality["psnr_fp32_db"], 4)
-        if "fp8" in precs and "fp32" in precs:
-            quality["delta_fp8_db"] = round(quality["psnr_fp8_db"] - quality["psnr_fp32_db"], 4)
-        quality["chain"] = f"{w['T']} iterations, {w['burn_in']} burn-in"
-
-    if rank != 0:
-        if ws > 1:
-            torch.distributed.destroy_process_group()
-        return
-
-    head = results[precs[0]]
-    kern = head["kernel"]
-    K, F = w["K"], w["F"]
-    pix_per_launch = npix  # one image per replica
-    if kern["name"] == "conv_tc":
-        flop = 2.0 * F * F * 9 * pix_per_launch
-        achieved = flop / (kern["avg_ms"] * 1e-3) / 1e12
-        pk = peaks["bf16_sus"] * (2 if precs[0] == "fp8" else 1)
-        ktag = "k_conv_tc<0,1>" if precs[0] == "fp8" else "k_conv_tc<0,0>"
-        roof = dict(bound="tensor", achieved=round(achieved, 2),
-                    peak=pk, unit="TFLOP/s",
-                    frac=round(achieved / pk, 4), traffic=ncu_traffic(ktag, args.workload, precs[0]),
-                    kernel=ktag, peak_kind=f"{precs[0]} sustained ({peaks['src']}"
-                                                  + (", bf16 x nominal ratio 2)" if precs[0] == "fp8" else ")"))
-    elif ddfb:
-        # a dual layer (the conv_fp32 timer; the first layer and the output run
-        # under conv_edge) streams the P-channel dual variable: read v and u,
-        # write u
-        Pd = 64
-        bpp = 4 + 8 * Pd
-        gbs = bpp * pix_per_launch / (kern["avg_ms"] * 1e-3) / 1e9
-        roof = dict(bound="hbm", achieved=round(gbs, 1), peak=peaks["hbm"], unit="GB/s",
-                    frac=round(gbs / peaks["hbm"], 4),
-                    traffic=ncu_traffic("k_ddfb<64,0>", args.workload, "fp32"),
-                    kernel="k_ddfb<64,0>", bytes_per_pixel=bpp,
-                    peak_kind=f"HBM copy ({peaks['src']})")
+    if args.workload == "batch48":
+        run_batch(args, P, torch, stream, ws, rank, local)
+    elif args.workload == "serve":
+        line = run_serve(args, P, torch, stream, ws, rank, local)
+        cpu = None
+        if rank == 0 and not args.no_cpu_baseline:
+            try:
+                cpu = oracle_baseline(5, budget_s=15.0)
+            except Exception as ex:  # report, never fake
+                cpu = dict(value=None, unit=UNIT, cores=None, kind="oracle", sample=f"failed: {ex}")
+        nested = {}
+        if not args.no_nested:
+            for wl, precs, q in (("deconv1024", ("bf16", "fp32", "fp8"), not args.no_quality),
+                                 ("deconv8192", ("bf16",), False)):
+                nested[wl] = measure_single(args, P, torch, stream, ws, rank, local, wl, precs,
+                                            args.steps, args.warmup, quality=q, cpu_baseline=False)
+        if rank == 0:
+            line["cpu_baseline"] = cpu
+            for wl, sub in nested.items():
+                line[f"single_job_{wl}"] = {k: sub[k] for k in (
+                    "value", "unit", "ms_per_step", "steps", "dtype", "config", "roofline", "e2e",
+                    "gpu_launches", "clocks", "kernel_breakdown_ms", "stencil_roofline",
+                    "fp32_plain", "fp8_variant", "quality") if k in sub}
+            print(json.dumps(line), flush=True)
     else:
-        flop = 2.0 * F * F * 9 * pix_per_launch
-        achieved = flop / (kern["avg_ms"] * 1e-3) / 1e12
-        alu_peak = 148 * 128 * 2 * peaks["sm_max"] / 1e6
-        roof = dict(bound="alu", achieved=round(achieved, 2), peak=round(alu_peak, 2),
-                    unit="TFLOP/s", frac=round(achieved / alu_peak, 4), traffic=None,
-                    kernel="k_conv3x3<64,64>", peak_kind="FP32 FFMA: 148 SM x 128 lanes x 2 x max clock")
-    # stencils against HBM: algorithmic bytes per pixel = r = Hx - y: read x, y,
-    # write r (12 B); update while sampling: read r, x, d, mean, m2, write x,
-    # mean, m2 (32 B; Poisson also reads z2: 36 B); Poisson z-update: read x,
-    # z1, z2, y, write z1, z2 (24 B)
-    stencils = {}
-    for kname, bpp in (("blur", 12), ("update", 36 if poisson else 32), ("zupdate", 24)):
-        n = kern["counts"].get(kname, 0)
-        if n:
-            avg = kern["breakdown"][kname] / n
-            gbs = bpp * npix / (avg * 1e-3) / 1e9
-            stencils[kname] = dict(avg_us=round(avg * 1e3, 2), bytes_per_pixel=bpp,
-                                   achieved_gbs=round(gbs, 1), frac=round(gbs / peaks["hbm"], 4))
-            if not poisson and not inpaint and max(prob.h.shape) > 31 and kname != "zupdate":
-                # wide stencil: 2 FLOP per nonzero tap and pixel against the FFMA peak
-                nnz = int(np.count_nonzero(prob.h.astype(np.float32)))
-                tf = 2.0 * nnz * npix / (avg * 1e-3) / 1e12
-                alu = 148 * 128 * 2 * peaks["sm_max"] / 1e6
-                stencils[kname].update(nonzero_taps=nnz, achieved_tflops=round(tf, 2),
-                                       alu_frac=round(tf / alu, 4), alu_peak_tflops=round(alu, 1))
-    if stencils:
-        stencils["peak_gbs"] = peaks["hbm"]
-        stencils["peak_kind"] = f"HBM copy ({peaks['src']})"
-    # every kernel of an iteration is timed in the eager pass: blur, the denoiser's
-    # layers (the BF16 form folds the last layer into the last F -> F layer and
-    # the update), update (whose last block advances the step counter)
-    launches_per_step = int(round(kern["launches_per_iter"]))
-    cpu = None
-    if not args.no_cpu_baseline:
-        try:
-            cpu = oracle_baseline(cfg_id, budget_s=15.0, poisson=poisson, inpaint=inpaint, ddfb=ddfb)
-        except Exception as ex:  # report, never fake
-            cpu = dict(value=None, unit=UNIT, cores=None, kind="oracle", sample=f"failed: {ex}")
-    line = dict(
-        metric=METRIC, value=round(head["value"], 3), unit=UNIT, n_gpus=ws, steps=args.steps,
-        warmup=args.warmup, ms_per_step=round(head["ms"] / args.steps, 4), higher_is_better=True,
-        scaling="weak", vs_baseline=None, dtype=("bf16" if precs[0] == "bf16" else "f32"),
-        data="synthetic",
-        config=dict(workload=(f"poisson1024: {ny}x{nx} Poisson counts, peak eta={prob.eta:g}, "
-                              f"rho1={POISSON['rho1']:g}, rho2={POISSON['rho2']:g}, AXDA + PSGLA, "
-                              f"blur {w['blur'][0]} {w['blur'][1]}x{w['blur'][1]}, "
-                              if poisson else
-                              f"inpaint1024: {ny}x{nx} grayscale, 30 % of the pixels observed, "
-                              "15 dB input SNR, cubic-interpolant start, "
-                              if inpaint else
-                              f"ddfb1024: {ny}x{nx} grayscale, {w['bsnr']} dB BSNR, DDFB prior "
-                              f"K=4 P=64 (FP32), blur {w['blur'][0]} {w['blur'][1]}x{w['blur'][1]}, "
-                              if ddfb else
-                              f"{w['name']}: {ny}x{nx} grayscale, {w['bsnr']} dB BSNR, "
-                              f"blur {w['blur'][0]} {w['blur'][1]}x{w['blur'][1]}, ")
-                             + ("" if ddfb else f"DnCNN-form K={K} F={F}, ")
-                             + f"{w['blocks'][0]}x{w['blocks'][1]} blocks "
-                             f"(halo-exchange-free), 1 chain per GPU",
-                    precision=precs[0], l2="working set per step > 126 MB L2 (activation planes)",
-                    graph="one CUDA graph per iteration"),
-        roofline=roof,
-        cpu_baseline=cpu,
-        e2e=e2e,
-        gpu_launches=launches_per_step * args.steps,
-        clocks=clocks,
-        kernel_breakdown_ms={p: results[p]["kernel"]["breakdown"] for p in results},
-        stencil_roofline=stencils,
-    )
-    if "fp32" in results and precs[0] != "fp32":
-        line["fp32_plain"] = dict(value=round(results["fp32"]["value"], 3), unit=UNIT,
-                                  ms_per_step=round(results["fp32"]["ms"] / results["fp32"]["steps"], 4),
-                                  steps=results["fp32"]["steps"],
-                                  speedup_bf16=round(head["value"] / results["fp32"]["value"], 3))
-    if "fp8" in results and precs[0] != "fp8":
-        r8 = results["fp8"]
-        a8 = 2.0 * F * F * 9 * npix / (r8["kernel"]["avg_ms"] * 1e-3) / 1e12
-        line["fp8_variant"] = dict(
-            value=round(r8["value"], 3), unit=UNIT, ms_per_step=round(r8["ms"] / r8["steps"], 4),
-            steps=r8["steps"], speedup_vs_bf16=round(r8["value"] / head["value"], 3),
-            conv_tc_tflops=round(a8, 2), conv_tc_frac=round(a8 / (2 * peaks["bf16_sus"]), 4),
-            peak_kind="fp8 = measured bf16 sustained x nominal ratio 2",
-            note="E4M3 weights (per-output-channel scales) and activations (per-layer static scales)")
-    if quality:
-        line["quality"] = quality
-    line["latency"] = dict(p50_s=None, p99_s=None, note="single-job workload; see --workload serve")
-    print(json.dumps(line), flush=True)
+        line = measure_single(args, P, torch, stream, ws, rank, local, args.workload,
+                              [p for p in args.precisions.split(",") if p], args.steps,
+                              args.warmup, quality=not args.no_quality,
+                              cpu_baseline=not args.no_cpu_baseline)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
 

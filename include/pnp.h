@@ -140,20 +140,42 @@ pnp_status pnp_denoise(const pnp_denoiser* D, pnp_precision prec, const float* x
  * (a raw cudaMalloc would fail there) or a latency-bound loop that cannot
  * afford cudaMalloc/cudaFree synchronizing the device.
  * Same arguments and result as pnp_denoise with halo = 0 (whole-image
- * layers). Scratch is a fixed area inside the library (a file-scope
- * __device__ array of PNP_NOALLOC_SCRATCH_BYTES), reserved on every GPU that
- * loads the library until the process exits. It needs
+ * layers) for PNP_FP32 and PNP_BF16; PNP_FP8 returns PNP_ENOTSUP. Scratch is
+ * a fixed area inside the library (a file-scope __device__ array of
+ * PNP_NOALLOC_SCRATCH_BYTES), held on a GPU until the process exits. It needs
  *   FP32: 8 * F * nimg * ny * nx bytes,  BF16: 256 * nimg * ny * ceil8(nx) + 256 bytes
  * (BF16 fits a 512 x 512 image; FP32 with F = 64 fits about 362 x 362);
  * larger requests return PNP_EINVAL with the needed size and launch nothing.
- * The first call on a device looks up the area's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The area is reserved, and its device address looked up
+ * (cudaGetSymbolAddress), by pnp_create_denoiser on the device current at
+ * creation: create the denoiser before another allocator takes the device's
+ * memory. On any other device the first call does the lookup (and
+ * reservation); make that first call before any stream capture.
  * All calls on a device share its one area and it keeps the previous call's
  * contents, so calls that can overlap on the GPU (for example on two streams
  * of the same device) race: serialize them on one stream. Calls no
- * cudaMalloc, cudaFree or other allocating routine. */
+ * cudaMalloc, cudaFree or other allocating routine. A tensor-core wait that
+ * ran out is reported by pnp_denoise_status. */
 pnp_status pnp_denoise_noalloc(const pnp_denoiser* D, pnp_precision prec, const float* x,
                                int ny, int nx, int nimg, float* d, void* stream);
+
+/* Waits for `stream`, then reports whether a bounded device-side wait ran out
+ * in a tensor-core layer of an earlier pnp_denoise or pnp_denoise_noalloc
+ * call with D since the last report: PNP_ETIMEOUT (the flag is then cleared;
+ * the outputs of the affected call are incomplete) or PNP_OK. The paper has
+ * no counterpart: this is the library's error channel for its bounded waits
+ * (each wait gives up after about two seconds instead of hanging the GPU). */
+pnp_status pnp_denoise_status(const pnp_denoiser* D, void* stream);
+
+/* Test hook (no counterpart in the paper): arms a one-shot fault for the next
+ * F -> F tensor-core layer launched outside stream capture, on any thread:
+ * CTA `cta` of that launch skips issuing its TMA load number `load_index`
+ * (nothing is in flight for it), and every wait of that launch gives up
+ * after budget_cycles SM clock cycles (>= 1000) instead of the default. The
+ * CTA waiting for the missing row then aborts, waits for its own copies and
+ * MMAs already in flight, releases its tensor memory and sets the caller's
+ * timeout flag, which the next synchronising call reports as PNP_ETIMEOUT. */
+pnp_status pnp_debug_inject_tc_timeout(int cta, int load_index, long long budget_cycles);
 
 /* One fused PnP-ULA x-update (Eq. 8) for nchain chains sharing y and h:
  *   g = H^T r / sigma^2 (r = H x - y from pnp_blur, device [nchain][ny][nx]),
@@ -263,7 +285,11 @@ pnp_status pnp_problem_params(const pnp_problem* p, double* lambda, double* gamm
 pnp_status pnp_step(pnp_problem* p, int n_iters);
 /* Run T iterations with the given burn-in (resets nothing) and wait. */
 pnp_status pnp_run_chain(pnp_problem* p, int T, int burn_in);
-/* Wait for the problem's stream. */
+/* Wait for the problem's stream. PNP_ETIMEOUT if a bounded device-side wait
+ * of a tensor-core denoiser layer ran out since the last synchronising call
+ * (pnp_sync, pnp_run_chain, pnp_get_state, pnp_get_moments report it once and
+ * clear it; the chain state is then not trustworthy: reset it with
+ * pnp_set_state). */
 pnp_status pnp_sync(pnp_problem* p);
 /* FP64 MMSE and std (want_var = 0) or variance for chain `chain`; host
  * buffers [ny*nx]; n_kept may be NULL. Synchronous. */
@@ -276,7 +302,11 @@ pnp_status pnp_set_state(pnp_problem* p, const float* x, int64_t t);
  * may be NULL). PNP_EINVAL for a Gaussian problem. Synchronous. */
 pnp_status pnp_get_aux_state(pnp_problem* p, float* z1, float* z2);
 pnp_status pnp_set_aux_state(pnp_problem* p, const float* z1, const float* z2);
-/* Device pointer of the chain state x [nchain][ny][nx] (valid until destroy). */
+/* Device pointer of the chain state x [nchain][ny][nx] after the iterations
+ * enqueued so far (valid until destroy). With a separable blur under Gaussian
+ * noise the state alternates between two buffers from one iteration to the
+ * next (the fused update reads the current state with a halo while writing the
+ * new one), so the pointer changes with every step; call again after stepping. */
 float* pnp_problem_x_device(pnp_problem* p);
 /* Replay captured CUDA graphs (one of 8 iterations, plus a one-iteration graph
  * for remainders; default on) or launch every kernel eagerly. */
@@ -321,6 +351,7 @@ void pnp_batch_destroy(pnp_batch* b);
 pnp_status pnp_batch_step(pnp_batch* b, int n_iters);
 /* Set every job's burn-in, run T iterations and wait. */
 pnp_status pnp_batch_run(pnp_batch* b, int T, int burn_in);
+/* Wait for the batch's stream; PNP_ETIMEOUT as for pnp_sync (any job's flag). */
 pnp_status pnp_batch_sync(pnp_batch* b);
 /* Borrowed handle of job `job` (for pnp_get_moments / pnp_get_state); owned by the batch. */
 pnp_status pnp_batch_job(pnp_batch* b, int job, pnp_problem** p);
@@ -344,7 +375,9 @@ pnp_status pnp_server_create(const pnp_denoiser* D, pnp_precision prec, size_t h
 /* Copies the job's inputs. PNP_EBUSY if the job alone exceeds the budget. */
 pnp_status pnp_server_submit(pnp_server* s, const pnp_problem_desc* desc, int T, int burn_in,
                              int64_t* job_id);
-/* State of a job; when done, copies MMSE / std (host [ny*nx], either may be NULL). */
+/* State of a job; when done, copies MMSE / std (host [ny*nx], either may be NULL).
+ * A round in which a bounded device-side wait ran out fails its jobs (state 3,
+ * error PNP_ETIMEOUT). */
 pnp_status pnp_server_poll(pnp_server* s, int64_t job_id, double* mmse, double* std, int* state);
 /* Wait up to timeout_s seconds for the job to end; PNP_ETIMEOUT if it did not. */
 pnp_status pnp_server_wait(pnp_server* s, int64_t job_id, double timeout_s, int* state);
@@ -355,6 +388,10 @@ pnp_status pnp_server_job_times(pnp_server* s, int64_t job_id, double* t_submit,
                                 double* t_done);
 pnp_status pnp_server_stats(pnp_server* s, int64_t* pixel_iters, int* active, int* queued,
                             size_t* used_bytes);
+/* Device time (seconds) of the work of all rounds so far, measured with CUDA
+ * events around each round's launches: the sampling itself, without the
+ * admission copies, the retirement read-backs or idle time between arrivals. */
+pnp_status pnp_server_device_seconds(pnp_server* s, double* seconds);
 /* Scheduling: in each round (between retire/admit points) a job runs
  * iters x min(max_boost, largest active job's pixels / its pixels) iterations
  * (never past its T), so small jobs finish early while large ones keep the
@@ -371,6 +408,10 @@ void pnp_server_destroy(pnp_server* s);
  * synchronizes the device and returns the summed device time and launches.
  * ------------------------------------------------------------------------ */
 pnp_status pnp_kernel_timer(int enable);
+/* Number of kernel launches the library has enqueued eagerly since it was
+ * loaded (any thread); kernels replayed from a captured CUDA graph are not
+ * counted again. */
+int64_t pnp_launch_count(void);
 pnp_status pnp_kernel_timer_read(const char* name, double* total_ms, int64_t* launches);
 
 #ifdef __cplusplus

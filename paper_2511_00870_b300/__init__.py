@@ -106,6 +106,12 @@ def pnp_stepsizes_poisson(hnorm, eta, rho1, rho2, alpha, eps, lip_eps, c=0.99):
     return tuple(o.value for o in out)
 
 
+def pnp_debug_inject_tc_timeout(cta: int, load_index: int, budget_cycles: int):
+    """Test hook: one-shot skipped load and short wait budget for the next
+    eager F -> F tensor-core layer (see include/pnp.h)."""
+    check(load().pnp_debug_inject_tc_timeout(int(cta), int(load_index), int(budget_cycles)))
+
+
 def pnp_set_graph_mode(enable: bool):
     check(load().pnp_set_graph_mode(int(bool(enable))))
 
@@ -122,6 +128,11 @@ def pnp_stencil_tile_count() -> int:
 def pnp_set_stencil_tile(tile: int):
     """Force stencil tile shape `tile` for every later launch (-1: per-problem choice)."""
     check(load().pnp_set_stencil_tile(int(tile)))
+
+
+def pnp_launch_count() -> int:
+    """Kernel launches the library has enqueued eagerly so far (graph replays excluded)."""
+    return int(load().pnp_launch_count())
 
 
 def pnp_kernel_timer(enable: bool):
@@ -185,11 +196,28 @@ class Denoiser:
 
     def denoise_noalloc(self, x, out, precision="fp32", stream=None):
         """pnp_denoise_noalloc: same result as denoise() with halo = 0, computed in
-        the library's fixed scratch area instead of allocating; `out` is caller-owned."""
+        the library's fixed scratch area instead of allocating; `out` is caller-owned.
+        x and out must be float32 tensors of one shape on the current CUDA device
+        (the fixed area is looked up for that device)."""
+        import torch
+        dev = torch.cuda.current_device()
+        for name, t in (("x", x), ("out", out)):
+            if t.dtype != torch.float32:
+                raise ValueError(f"denoise_noalloc: {name} must be float32, not {t.dtype}")
+            if not t.is_cuda or t.device.index != dev:
+                raise ValueError(f"denoise_noalloc: {name} must be on the current CUDA device "
+                                 f"cuda:{dev}, not {t.device}")
+        if tuple(out.shape) != tuple(x.shape):
+            raise ValueError("denoise_noalloc: out must have the shape of x")
         n, ny, nx = x.shape
         check(load().pnp_denoise_noalloc(self.handle, _prec(precision), _ptr(x), ny, nx, n,
                                          _ptr(out), _stream(stream)))
         return out
+
+    def status(self, stream=None):
+        """pnp_denoise_status: waits for the stream, raises PnpError (PNP_ETIMEOUT)
+        if a bounded device-side wait of an earlier denoise call ran out."""
+        check(load().pnp_denoise_status(self.handle, _stream(stream)))
 
     def close(self):
         if getattr(self, "handle", None):
@@ -445,6 +473,12 @@ class Server:
         px, act, q, used = C.c_int64(), C.c_int(), C.c_int(), C.c_size_t()
         check(load().pnp_server_stats(self.handle, C.byref(px), C.byref(act), C.byref(q), C.byref(used)))
         return dict(pixel_iters=px.value, active=act.value, queued=q.value, used_bytes=used.value)
+
+    def device_seconds(self):
+        """Device time of all rounds so far (pnp_server_device_seconds)."""
+        v = C.c_double()
+        check(load().pnp_server_device_seconds(self.handle, C.byref(v)))
+        return v.value
 
     def close(self):
         if getattr(self, "handle", None):

@@ -58,6 +58,8 @@ SIGNATURES = {
     "pnp_blur_adjoint": ([vp, vp, i32, i32, i32, i32, i32, f32, vp, vp], i32),
     "pnp_denoise": ([vp, i32, vp, i32, i32, i32, i32, i32, i32, vp, vp], i32),
     "pnp_denoise_noalloc": ([vp, i32, vp, i32, i32, i32, vp, vp], i32),
+    "pnp_denoise_status": ([vp, vp], i32),
+    "pnp_debug_inject_tc_timeout": ([i32, i32, C.c_longlong], i32),
     "pnp_langevin_update": ([vp, vp, vp, vp, i32, i32, i32, i32, i32, f64, f64, f64, f64, f64,
                              u64, u32, i32, vp, vp, i64, vp], i32),
     "pnp_inpaint_update": ([vp, vp, vp, i32, i32, i32, f64, f64, f64, f64, f64, u64, u32, i32,
@@ -99,6 +101,8 @@ SIGNATURES = {
     "pnp_server_set_round": ([vp, i32, i32], i32),
     "pnp_server_destroy": ([vp], None),
     "pnp_kernel_timer": ([i32], i32),
+    "pnp_launch_count": ([], i64),
+    "pnp_server_device_seconds": ([vp, dp], i32),
     "pnp_kernel_timer_read": ([C.c_char_p, dp, C.POINTER(i64)], i32),
 }
 

@@ -2,6 +2,7 @@
 // CUDA-graph replay around the kernels of k_stencil.cu, k_conv_simt.cu and
 // k_conv_tc.cu. Every compute step runs on the GPU; the host only validates,
 // allocates, derives the step sizes (Eq. 10) and enqueues work.
+#include <atomic>
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -26,6 +27,19 @@ pnp_status cuda_fail(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? PNP_ENOMEM : PNP_ECUDA;
 }
 
+pnp_status take_timeout(int* flag, cudaStream_t s, const char* who) {
+    if (!flag) return PNP_OK;
+    int h = 0;
+    PNP_CUDA_TRY(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PNP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h == 0) return PNP_OK;
+    PNP_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    PNP_CUDA_TRY(cudaStreamSynchronize(s));
+    return fail(PNP_ETIMEOUT, std::string(who) +
+                                  ": a bounded wait in a tensor-core denoiser layer ran out; the "
+                                  "affected results are incomplete");
+}
+
 int num_sms() {
     static int cached[64] = {0};
     int dev = 0;
@@ -48,6 +62,8 @@ static TimerSlot g_timers[T_COUNT];
 static bool g_timing = false;
 static bool g_pdl = true;
 bool pdl_enabled() { return g_pdl; }
+static std::atomic<int64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 static const char* g_timer_names[T_COUNT] = {"blur", "update", "conv_fp32", "conv_tc", "conv_edge", "conv_last",
                                               "zupdate"};
 
@@ -174,6 +190,20 @@ extern "C" pnp_status pnp_create_denoiser(int K, int F, const float* weights, co
     D.F = F;
     D.lip = lipschitz_eps;
     cudaGetDevice(&den->device);
+    {
+        pnp_status fs = dalloc(&den->err, 1);
+        if (fs != PNP_OK) {
+            pnp_destroy_denoiser(den);
+            return fs;
+        }
+        cudaMemset(den->err, 0, sizeof(int));
+        // the allocation-free entry point's fixed area is reserved now, while
+        // device memory is still available, rather than at its first call
+        if (noalloc_reserve() != PNP_OK) {
+            cudaGetLastError();
+            set_error("");
+        }
+    }
     std::vector<int> cin(K), cout(K);
     for (int k = 0; k < K; ++k) {
         cin[k] = k == 0 ? 1 : F;
@@ -340,7 +370,7 @@ extern "C" pnp_status pnp_create_ddfb(int K, int P, const float* filters, const 
             return fail(PNP_EINVAL, "pnp_create_ddfb: gammas must be > 0");
     pnp_denoiser* den = new pnp_denoiser();
     DenoiserDev& D = den->dev;
-    cudaGetDevice(&den->device);
+    cudaGetDevice(&den->device);   // host-only: the DDFB kernels have no bounded waits
     D.K = K;
     D.F = P;
     D.lip = 1.0;   // D is a (relaxed) proximity operator: Id - D is nonexpansive
@@ -366,6 +396,7 @@ extern "C" void pnp_destroy_denoiser(pnp_denoiser* den) {
     dfree(D.wtc8_last);
     delete[] D.w8_scale;
     dfree(den->scratch);
+    dfree(den->err);
     delete[] D.w32_off;
     delete[] D.b_off;
     delete[] D.hw;
@@ -430,10 +461,10 @@ static size_t denoise_scratch_bytes(const DenoiserDev& D, pnp_precision prec, in
 
 static cudaError_t run_denoise(const DenoiserDev& D, pnp_precision prec, bool residual, const float* x, int ny,
                                int nx, int nimg, const Rect* rects, float* d, void* scratch,
-                               cudaStream_t s) {
+                               cudaStream_t s, int* err) {
     if (prec == PNP_FP32) return denoise_fp32(D, x, ny, nx, nimg, rects, d, (float*)scratch, s);
-    if (prec == PNP_FP8) return denoise_fp8(D, x, ny, nx, nimg, rects, d, scratch, s, residual);
-    return denoise_bf16(D, x, ny, nx, nimg, rects, d, scratch, s, residual);
+    if (prec == PNP_FP8) return denoise_fp8(D, x, ny, nx, nimg, rects, d, scratch, s, residual, err);
+    return denoise_bf16(D, x, ny, nx, nimg, rects, d, scratch, s, residual, err);
 }
 
 static pnp_status check_denoise_args(const pnp_denoiser* den, pnp_precision prec, int ny, int nx,
@@ -510,7 +541,7 @@ extern "C" pnp_status pnp_denoise(const pnp_denoiser* den, pnp_precision prec, c
             PNP_CUDA_TRY(cudaMemset(dn->scratch, 0, need));
             dn->scratch_bytes = need;
         }
-        PNP_CUDA_TRY(run_denoise(D, prec, false, x, ny, nx, nimg, nullptr, d, dn->scratch, s));
+        PNP_CUDA_TRY(run_denoise(D, prec, false, x, ny, nx, nimg, nullptr, d, dn->scratch, s, dn->err));
         return PNP_OK;
     }
     // block + halo: gather extended blocks, run the network per tile, scatter interiors
@@ -541,9 +572,23 @@ extern "C" pnp_status pnp_denoise(const pnp_denoiser* den, pnp_precision prec, c
     BlockDesc* blocks = (BlockDesc*)p;
     PNP_CUDA_TRY(cudaMemcpyAsync(blocks, bl.data(), nb * sizeof(BlockDesc), cudaMemcpyHostToDevice, s));
     PNP_CUDA_TRY(launch_gather_blocks(x, ny, nx, blocks, nb, halo, ty, tx, tiles, rects, s));
-    PNP_CUDA_TRY(run_denoise(D, prec, false, tiles, ty, tx, nb, rects, dtiles, net_scratch, s));
+    PNP_CUDA_TRY(run_denoise(D, prec, false, tiles, ty, tx, nb, rects, dtiles, net_scratch, s, dn->err));
     PNP_CUDA_TRY(launch_scatter_blocks(dtiles, ny, nx, blocks, nb, halo, ty, tx, d, s));
     PNP_CUDA_TRY(cudaStreamSynchronize(s));   // the host block table must outlive the copy
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_denoise_status(const pnp_denoiser* den, void* stream) {
+    if (!den) return fail(PNP_EINVAL, "pnp_denoise_status: denoiser is NULL");
+    return take_timeout(den->err, (cudaStream_t)stream, "pnp_denoise");
+}
+
+extern "C" pnp_status pnp_debug_inject_tc_timeout(int cta, int load_index,
+                                                  long long budget_cycles) {
+    if (cta < 0 || load_index < 0 || budget_cycles < 1000)
+        return fail(PNP_EINVAL, "pnp_debug_inject_tc_timeout: need cta >= 0, load_index >= 0 and "
+                                "budget_cycles >= 1000");
+    tc_inject_timeout(cta, load_index, budget_cycles);
     return PNP_OK;
 }
 
@@ -583,6 +628,8 @@ static pnp_status fill_update_params(UpdateParams& u, float* x, const float* r, 
     u.c_z2 = 0.f;
     u.wtaps = nullptr;
     u.nwtaps = 0;
+    u.qb = nullptr;
+    u.x_out = nullptr;
     return PNP_OK;
 }
 
@@ -638,13 +685,17 @@ extern "C" pnp_status pnp_finalize_moments(const float* mean, const float* m2, i
 extern "C" void pnp_destroy_problem(pnp_problem* p) {
     if (!p) return;
     if (p->stream) cudaStreamSynchronize(p->stream);
-    if (p->graph) cudaGraphExecDestroy(p->graph);
-    if (p->graph_batch) cudaGraphExecDestroy(p->graph_batch);
-    for (void* q : {(void*)p->y, (void*)p->h, (void*)p->x, (void*)p->r, (void*)p->d,
+    for (int k = 0; k < 2; ++k) {
+        if (p->graph[k]) cudaGraphExecDestroy(p->graph[k]);
+        if (p->graph_batch[k]) cudaGraphExecDestroy(p->graph_batch[k]);
+    }
+    // the state buffers are xb[0] and, for the one-pass gradient, the residual
+    // plane r; x points at one of them
+    for (void* q : {(void*)p->y, (void*)p->h, (void*)p->xb[0], (void*)p->r, (void*)p->d,
                     (void*)p->mean, (void*)p->m2, (void*)p->blocks, (void*)p->tiles,
                     (void*)p->dtiles, (void*)p->rects, p->scratch, (void*)p->st,
                     (void*)p->hsep, (void*)p->z1, (void*)p->z2, (void*)p->wt_fwd,
-                    (void*)p->wt_adj})
+                    (void*)p->wt_adj, (void*)p->err, (void*)p->qb, (void*)p->qsep})
         dfree(q);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
     delete p;
@@ -664,6 +715,7 @@ static pnp_status poisson_refresh_r(pnp_problem* p) {
 
 pnp_status problem_pre(pnp_problem* p, cudaStream_t s) {
     if (p->inpaint) return PNP_OK;   // H = diag(mask): the update forms x - y itself
+    if (p->fused) return PNP_OK;     // the update forms (H^T H) x - H^T y from x itself
     if (p->poisson) {
         return PNP_OK;               // r = eta H x - z1 was written by the last z-update
     } else {
@@ -693,6 +745,16 @@ static pnp_status problem_update_params(const pnp_problem* p, UpdateParams& u) {
     u.hsep = p->hsep;
     u.wtaps = p->wt_adj;
     u.nwtaps = p->nwt;
+    if (p->fused) {
+        // one pass over the current state with the taps of H^T H, x+ to the other buffer
+        u.r = p->x;
+        u.x_out = p->xb[p->par ^ 1];
+        u.qb = p->qb;
+        u.hsep = p->qsep;
+        u.h = nullptr;
+        u.kh = 2 * p->kh - 1;
+        u.kw = 2 * p->kw - 1;
+    }
     if (p->poisson) {
         u.inv_s2 = (float)(p->eta / p->rho1);
         u.z2 = p->z2;
@@ -738,6 +800,7 @@ pnp_status problem_post(pnp_problem* p, cudaStream_t s) {
     if (p->inpaint) PNP_CUDA_TRY(launch_update_mask(u, s));
     else PNP_CUDA_TRY(launch_langevin_update(u, s));
     if (p->poisson) PNP_CUDA_TRY(launch_zupdate(problem_z_params(p), s));
+    problem_flip(p);
     return PNP_OK;
 }
 
@@ -751,12 +814,12 @@ static pnp_status enqueue_iteration(pnp_problem* p) {
         const DenoiserDev& D = p->D->dev;
         if (p->halo == 0) {
             PNP_CUDA_TRY(run_denoise(D, p->prec, p->prec != PNP_FP32, p->x, p->ny, p->nx, p->nchain, nullptr, p->d,
-                                     p->scratch, s));
+                                     p->scratch, s, p->err));
         } else {
             PNP_CUDA_TRY(launch_gather_blocks(p->x, p->ny, p->nx, p->blocks, p->nblocks, p->halo,
                                               p->ty, p->tx, p->tiles, p->rects, s));
             PNP_CUDA_TRY(run_denoise(D, p->prec, p->prec != PNP_FP32, p->tiles, p->ty, p->tx, p->nblocks, p->rects,
-                                     p->dtiles, p->scratch, s));
+                                     p->dtiles, p->scratch, s, p->err));
             PNP_CUDA_TRY(launch_scatter_blocks(p->dtiles, p->ny, p->nx, p->blocks, p->nblocks,
                                                p->halo, p->ty, p->tx, p->d, s));
         }
@@ -945,11 +1008,14 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
     ALLOC(p->y, N);
     ALLOC(p->h, (size_t)q.kh * q.kw);
     ALLOC(p->x, NC);
+    p->xb[0] = p->xb[1] = p->x;
     ALLOC(p->r, NC);
     ALLOC(p->d, NC);
     ALLOC(p->mean, NC);
     ALLOC(p->m2, NC);
     ALLOC(p->st, 1);
+    ALLOC(p->err, 1);
+    cudaMemset(p->err, 0, sizeof(int));
     if (poisson) {
         ALLOC(p->z1, NC);
         ALLOC(p->z2, NC);
@@ -1019,6 +1085,47 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
                 return st;
             }
             cudaMemcpy(p->hsep, sep.data(), sep.size() * 4, cudaMemcpyHostToDevice);
+            // One-pass gradient for a separable blur under Gaussian noise:
+            // H^T (H x - y) = (H^T H) x - H^T y. H^T H is the correlation with
+            // the autocorrelation q of h (symmetric, 2 L - 1 taps per axis),
+            // separable as qu qv^T when h = u v^T.
+            if (!poisson && !inpaint && 2 * q.kh - 1 <= STENCIL_MAXK && 2 * q.kw - 1 <= STENCIL_MAXK) {
+                const int qh = 2 * q.kh - 1, qw = 2 * q.kw - 1;
+                auto autocorr = [](const float* v, int L, std::vector<double>& out) {
+                    out.assign(2 * L - 1, 0.0);
+                    for (int k = -(L - 1); k <= L - 1; ++k)
+                        for (int a = 0; a < L; ++a)
+                            if (a + k >= 0 && a + k < L) out[k + L - 1] += (double)v[a + k] * v[a];
+                };
+                std::vector<double> qu, qv;
+                autocorr(sep.data(), q.kh, qu);
+                autocorr(sep.data() + q.kh, q.kw, qv);
+                std::vector<float> qs(2 * (qh + qw));
+                for (int a = 0; a < qh; ++a) {
+                    qs[a] = (float)qu[a];
+                    qs[qh + qw + a] = (float)qu[qh - 1 - a];
+                }
+                for (int b = 0; b < qw; ++b) {
+                    qs[qh + b] = (float)qv[b];
+                    qs[2 * qh + qw + b] = (float)qv[qw - 1 - b];
+                }
+                if ((st = dalloc(&p->qsep, qs.size())) != PNP_OK ||
+                    (st = dalloc(&p->qb, (size_t)N)) != PNP_OK) {
+                    pnp_destroy_problem(p);
+                    return st;
+                }
+                cudaMemcpy(p->qsep, qs.data(), qs.size() * 4, cudaMemcpyHostToDevice);
+                // H^T y, formed once for the whole chain
+                cudaError_t e = launch_blur_adjoint(p->y, p->h, q.kh, q.kw, q.ny, q.nx, 1, 1.0f,
+                                                    p->qb, p->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+                if (e != cudaSuccess) {
+                    pnp_destroy_problem(p);
+                    return cuda_fail(e, "pnp_create_problem: H^T y");
+                }
+                p->fused = true;
+                p->xb[1] = p->r;   // the residual plane is not needed: second state buffer
+            }
         }
     }
     {
@@ -1035,9 +1142,13 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
             u.burn_dev = nullptr;
             u.arrive = nullptr;
             u.inv_n = 1.0f;   // time the sampling form (Welford traffic included)
-            cudaError_t e = stencil_autotune(p->x, p->y, p->h, p->hsep, p->kh, p->kw, p->ny,
-                                             p->nx, p->nchain, p->r, u, p->stream,
-                                             &p->blur_tile, &p->update_tile);
+            cudaError_t e = p->fused
+                ? stencil_autotune(p->x, p->y, p->h, p->qsep, 2 * p->kh - 1, 2 * p->kw - 1, p->ny,
+                                   p->nx, p->nchain, p->r, u, p->stream, &p->blur_tile,
+                                   &p->update_tile)
+                : stencil_autotune(p->x, p->y, p->h, p->hsep, p->kh, p->kw, p->ny,
+                                   p->nx, p->nchain, p->r, u, p->stream,
+                                   &p->blur_tile, &p->update_tile);
             if (e != cudaSuccess) us = cuda_fail(e, "stencil autotune");
         }
         if (us != PNP_OK) {
@@ -1103,13 +1214,18 @@ extern "C" pnp_status pnp_problem_params(const pnp_problem* p, double* lambda, d
     return PNP_OK;
 }
 
-// Captures `iters` iterations of the problem into one executable graph.
+// Captures `iters` iterations of the problem, starting from its current state
+// buffer, into one executable graph. Capturing executes nothing, so the
+// host-side state buffer is restored afterwards.
 static pnp_status capture_graph(pnp_problem* p, int iters, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
+    const int par0 = p->par;
     PNP_CUDA_TRY(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
     pnp_status st = PNP_OK;
     for (int i = 0; i < iters && st == PNP_OK; ++i) st = enqueue_iteration(p);
     cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+    p->par = par0;
+    p->x = p->xb[par0];
     if (st != PNP_OK) {
         if (g) cudaGraphDestroy(g);
         return st;
@@ -1151,6 +1267,8 @@ extern "C" pnp_status pnp_kernel_timer_read(const char* name, double* total_ms, 
     return fail(PNP_EINVAL, std::string("unknown kernel timer ") + name);
 }
 
+extern "C" int64_t pnp_launch_count(void) { return g_launches.load(); }
+
 extern "C" pnp_status pnp_set_graph_mode(int enable) {
     g_use_graph = enable != 0;
     return PNP_OK;
@@ -1182,20 +1300,32 @@ extern "C" pnp_status pnp_step(pnp_problem* p, int n_iters) {
     if (!p || n_iters < 0) return fail(PNP_EINVAL, "pnp_step: bad arguments");
     if (n_iters == 0) return PNP_OK;
     if (g_use_graph && !g_timing) {
-        if (!p->graph) {
+        if (!p->eager_done) {
             // one eager iteration first performs the lazy per-kernel setup
             PNP_TRY(enqueue_iteration(p));
+            p->eager_done = true;
             p->t += 1;
             --n_iters;
             if (n_iters == 0) return PNP_OK;
-            PNP_TRY(capture_graph(p, 1, &p->graph));
         }
-        if (n_iters >= kGraphBatch && !p->graph_batch)
-            PNP_TRY(capture_graph(p, kGraphBatch, &p->graph_batch));
+        // graphs per start parity of the state buffers (one pair when the
+        // state is updated in place); a kGraphBatch-iteration graph ends on
+        // the parity it started from
         int left = n_iters;
-        for (; left >= kGraphBatch; left -= kGraphBatch)
-            PNP_CUDA_TRY(cudaGraphLaunch(p->graph_batch, p->stream));
-        for (; left > 0; --left) PNP_CUDA_TRY(cudaGraphLaunch(p->graph, p->stream));
+        while (left > 0) {
+            const int gi = p->xb[0] == p->xb[1] ? 0 : p->par;
+            if (left >= kGraphBatch) {
+                if (!p->graph_batch[gi]) PNP_TRY(capture_graph(p, kGraphBatch, &p->graph_batch[gi]));
+                PNP_CUDA_TRY(cudaGraphLaunch(p->graph_batch[gi], p->stream));
+                left -= kGraphBatch;
+                if (kGraphBatch % 2) problem_flip(p);
+            } else {
+                if (!p->graph[gi]) PNP_TRY(capture_graph(p, 1, &p->graph[gi]));
+                PNP_CUDA_TRY(cudaGraphLaunch(p->graph[gi], p->stream));
+                left -= 1;
+                problem_flip(p);
+            }
+        }
     } else {
         for (int i = 0; i < n_iters; ++i) PNP_TRY(enqueue_iteration(p));
     }
@@ -1206,7 +1336,7 @@ extern "C" pnp_status pnp_step(pnp_problem* p, int n_iters) {
 extern "C" pnp_status pnp_sync(pnp_problem* p) {
     if (!p) return fail(PNP_EINVAL, "problem is NULL");
     PNP_CUDA_TRY(cudaStreamSynchronize(p->stream));
-    return PNP_OK;
+    return take_timeout(p->err, p->stream, "pnp_sync");
 }
 
 extern "C" pnp_status pnp_run_chain(pnp_problem* p, int T, int burn_in) {
@@ -1224,6 +1354,7 @@ extern "C" pnp_status pnp_get_moments(pnp_problem* p, int chain, double* mmse, d
                                       int64_t* n_kept, int want_var) {
     if (!p || !mmse || !std_or_var || chain < 0 || chain >= p->nchain)
         return fail(PNP_EINVAL, "pnp_get_moments: bad arguments");
+    PNP_TRY(take_timeout(p->err, p->stream, "pnp_get_moments"));
     const int64_t n = std::max<int64_t>(0, p->t - p->burn_in);
     double* dm = nullptr;
     PNP_TRY(dalloc(&dm, (size_t)2 * p->N));
@@ -1240,6 +1371,7 @@ extern "C" pnp_status pnp_get_moments(pnp_problem* p, int chain, double* mmse, d
 
 extern "C" pnp_status pnp_get_state(pnp_problem* p, float* x, int64_t* t) {
     if (!p) return fail(PNP_EINVAL, "problem is NULL");
+    PNP_TRY(take_timeout(p->err, p->stream, "pnp_get_state"));
     if (x) {
         PNP_CUDA_TRY(cudaMemcpyAsync(x, p->x, (size_t)p->N * p->nchain * 4, cudaMemcpyDeviceToHost, p->stream));
     }

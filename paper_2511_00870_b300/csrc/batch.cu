@@ -1,9 +1,10 @@
 // Batched sampling: many independent posteriors (jobs) of different image
-// sizes stepped together. One iteration of the batch runs, for every job,
-// r = H x - y and the BF16 first layer, then ONE tensor-core launch per F -> F
-// layer and one for the last layer over the rows of all jobs (a device table
-// of per-job tensor maps, balanced across the SMs to within a row), then every
-// job's fused Langevin update. The whole iteration is captured once as a CUDA
+// sizes stepped together. One iteration of the batch runs, for every job that
+// needs it, r = H x - y; then ONE first-layer launch over every job's state (a
+// by-value job table), ONE tensor-core launch per F -> F layer and one for the
+// last layer over the rows of all jobs (a device table of per-job tensor maps,
+// balanced across the SMs to within a row), then every job's fused Langevin
+// update. The whole iteration is captured once as a CUDA
 // graph and replayed. Jobs never interact: each one's result is the same as
 // when it runs alone (same kernels, same per-pixel summation order, its own
 // Philox stream and step counter).
@@ -17,12 +18,13 @@ namespace pnp {
 
 size_t BatchPlan::table_bytes(int n) { return (size_t)3 * n * sizeof(TcJob); }
 
-// Activation planes of a BF16 problem (layout of denoise_bf16's scratch).
+// Activation planes of a BF16 problem (layout of denoise_bf16's scratch) and
+// its timeout flag.
 static void bf16_planes(const pnp_problem* p, __nv_bfloat16** A, __nv_bfloat16** B, int** err) {
     const size_t act = (size_t)p->nchain * p->ny * bf16_pad_width(p->nx) * 64;
     *A = (__nv_bfloat16*)p->scratch;
     *B = *A + act;
-    *err = (int*)(*B + act);
+    *err = p->err;
 }
 
 pnp_status plan_build(BatchPlan& plan, const std::vector<pnp_problem*>& jobs, cudaStream_t s) {
@@ -81,12 +83,21 @@ pnp_status plan_enqueue_step(const BatchPlan& plan, const std::vector<pnp_proble
     if (p0->D && p0->alpha != 0.0) {
         const DenoiserDev& D = p0->D->dev;
         if (plan.bf16) {
-            for (pnp_problem* p : jobs) {
+            // the first layer of every job in one launch (each job's current state)
+            std::vector<FirstJob> fj(jobs.size());
+            for (size_t k = 0; k < jobs.size(); ++k) {
+                const pnp_problem* p = jobs[k];
                 __nv_bfloat16 *A, *B;
                 int* err;
                 bf16_planes(p, &A, &B, &err);
-                PNP_CUDA_TRY(first_layer_bf16(D, p->x, p->ny, p->nx, p->nchain, nullptr, A, err, s));
+                memset(&fj[k], 0, sizeof(FirstJob));
+                fj[k].x = p->x;
+                fj[k].out = A;
+                fj[k].ny = p->ny;
+                fj[k].nx = p->nx;
+                fj[k].nimg = p->nchain;
             }
+            PNP_CUDA_TRY(first_layer_bf16_jobs(D, fj.data(), (int)fj.size(), plan.err, s));
             TcJob dummy;
             memset(&dummy, 0, sizeof(dummy));
             for (int k = 1; k < D.K - 1; ++k) {
@@ -116,14 +127,18 @@ struct pnp_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     BatchPlan plan;
-    cudaGraphExec_t graph = nullptr;
+    // one graph per phase: every job steps each iteration, so the jobs' state
+    // buffers alternate together (phase = iterations since creation mod 2)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int phase = 0;
     bool eager_done = false;
 };
 
 extern "C" void pnp_batch_destroy(pnp_batch* b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
-    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (int k = 0; k < 2; ++k)
+        if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
     for (pnp_problem* p : b->jobs) pnp_destroy_problem(p);
     plan_free(b->plan);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -184,25 +199,35 @@ extern "C" pnp_status pnp_batch_step(pnp_batch* b, int n_iters) {
             PNP_TRY(plan_enqueue_step(b->plan, b->jobs, b->stream));
             b->eager_done = true;
         } else {
-            if (!b->graph) {
+            cudaGraphExec_t& ge = b->graph[b->phase];
+            if (!ge) {
+                // capturing executes nothing: the jobs' state buffers are restored
+                std::vector<int> par0;
+                for (pnp_problem* p : b->jobs) par0.push_back(p->par);
                 cudaGraph_t g = nullptr;
                 PNP_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
                 pnp_status st = plan_enqueue_step(b->plan, b->jobs, b->stream);
                 cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+                for (size_t k = 0; k < b->jobs.size(); ++k) {
+                    b->jobs[k]->par = par0[k];
+                    b->jobs[k]->x = b->jobs[k]->xb[par0[k]];
+                }
                 if (st != PNP_OK) {
                     if (g) cudaGraphDestroy(g);
                     return st;
                 }
                 if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-                e = cudaGraphInstantiate(&b->graph, g, 0);
+                e = cudaGraphInstantiate(&ge, g, 0);
                 cudaGraphDestroy(g);
                 if (e != cudaSuccess) {
-                    b->graph = nullptr;
+                    ge = nullptr;
                     return cuda_fail(e, "cudaGraphInstantiate");
                 }
             }
-            PNP_CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
+            PNP_CUDA_TRY(cudaGraphLaunch(ge, b->stream));
+            for (pnp_problem* p : b->jobs) problem_flip(p);
         }
+        b->phase ^= 1;
         for (pnp_problem* p : b->jobs) p->t += 1;
     }
     return PNP_OK;
@@ -211,7 +236,13 @@ extern "C" pnp_status pnp_batch_step(pnp_batch* b, int n_iters) {
 extern "C" pnp_status pnp_batch_sync(pnp_batch* b) {
     if (!b) return fail(PNP_EINVAL, "batch is NULL");
     PNP_CUDA_TRY(cudaStreamSynchronize(b->stream));
-    return PNP_OK;
+    // the layers shared by all jobs report into the first job's flag
+    pnp_status st = PNP_OK;
+    for (pnp_problem* p : b->jobs) {
+        pnp_status sj = take_timeout(p->err, b->stream, "pnp_batch_sync");
+        if (st == PNP_OK) st = sj;
+    }
+    return st;
 }
 
 extern "C" pnp_status pnp_batch_run(pnp_batch* b, int T, int burn_in) {

@@ -214,6 +214,7 @@ static cudaError_t launch_layer(const float* in, const float* w, const float* b,
     dim3 grid(ceil_div(nx, CV_TX), ceil_div(ny, CV_TY), nimg);
     const int tid = CIN == COUT ? T_CONV_FP32 : T_CONV_EDGE;
     timer_begin(tid, s);
+    note_launch();
     kern<<<grid, CV_THREADS, C::SMEM, s>>>(in, w, b, ny, nx, rects, out);
     timer_end(tid, s);
     return cudaGetLastError();
@@ -237,6 +238,7 @@ static cudaError_t denoise_fp32_F(const DenoiserDev& D, const float* x, int ny, 
     const int L = D.K - 1;
     dim3 grid(ceil_div(nx, CV_TX), ceil_div(ny, CV_TY), nimg);
     timer_begin(T_CONV_EDGE, s);
+    note_launch();
     k_conv3x3_last<F><<<grid, CV_THREADS, 0, s>>>(A, D.w32 + D.w32_off[L], D.b32 + D.b_off[L], x,
                                                   ny, nx, d);
     timer_end(T_CONV_EDGE, s);
@@ -266,16 +268,19 @@ static cudaError_t denoise_fp32_amax_F(const DenoiserDev& D, const float* x, int
         e = launch_layer<1, F, true>(x, D.w32 + D.w32_off[0], D.b32 + D.b_off[0], ny, nx, nimg,
                                      nullptr, A, s);
     if (e != cudaSuccess) return e;
+    note_launch();
     k_amax<<<grid, 256, 0, s>>>(A, act, amax + 0);
     for (int k = 1; k < D.K - 1; ++k) {
         e = launch_layer<F, F, true>(A, D.w32 + D.w32_off[k], D.b32 + D.b_off[k], ny, nx, nimg,
                                      nullptr, B, s);
         if (e != cudaSuccess) return e;
+        note_launch();
         k_amax<<<grid, 256, 0, s>>>(B, act, amax + k);
         float* t = A; A = B; B = t;
     }
     const int L = D.K - 1;
     dim3 g(ceil_div(nx, CV_TX), ceil_div(ny, CV_TY), nimg);
+    note_launch();
     k_conv3x3_last<F><<<g, CV_THREADS, 0, s>>>(A, D.w32 + D.w32_off[L], D.b32 + D.b_off[L], x, ny,
                                                nx, d);
     return cudaGetLastError();
@@ -350,6 +355,7 @@ cudaError_t launch_gather_blocks(const float* x, int ny, int nx, const BlockDesc
                                  int nblocks, int halo, int ty, int tx, float* tiles, Rect* rects,
                                  cudaStream_t s) {
     dim3 blk(32, 8), grid(ceil_div(tx, 32), ceil_div(ty, 8), nblocks);
+    note_launch();
     k_gather<<<grid, blk, 0, s>>>(x, ny, nx, blocks, halo, ty, tx, tiles, rects);
     return cudaGetLastError();
 }
@@ -358,6 +364,7 @@ cudaError_t launch_scatter_blocks(const float* dtiles, int ny, int nx, const Blo
                                   int nblocks, int halo, int ty, int tx, float* d,
                                   cudaStream_t s) {
     dim3 blk(32, 8), grid(ceil_div(tx, 32), ceil_div(ty, 8), nblocks);
+    note_launch();
     k_scatter<<<grid, blk, 0, s>>>(dtiles, ny, nx, blocks, halo, ty, tx, d);
     return cudaGetLastError();
 }

@@ -39,6 +39,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include <cuda_fp8.h>
 
@@ -119,6 +120,9 @@ struct TcCommon {
     const TcJob* jobs;            // device table, or nullptr: the single job parameter
     int njobs;
     int64_t total_rows;
+    long long budget;             // clock cycles a wait may last before the CTA gives up
+    int skip_cta, skip_load;      // fault injection: CTA skip_cta never issues its load
+                                  // number skip_load (skip_cta < 0: off)
 };
 
 // Position in the concatenated row stream of a launch.
@@ -247,6 +251,10 @@ __global__ void __launch_bounds__(TcMode<LAST, FP8>::THREADS, 1)
     // this CTA's share of the concatenated row stream
     const int64_t g_begin = c.total_rows * blockIdx.x / gridDim.x;
     const int64_t g_end = c.total_rows * (blockIdx.x + 1) / gridDim.x;
+    const long long budget = c.budget;
+    // loads issued by the producer and the one it skipped (fault injection),
+    // read again when unwinding after an abort
+    uint32_t loads = 0, skipped = 0xffffffffu;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -254,27 +262,30 @@ __global__ void __launch_bounds__(TcMode<LAST, FP8>::THREADS, 1)
             uint32_t L = 0;
             bool ok = true;
             int j = 0;
+            const uint32_t skip_at =
+                (int)blockIdx.x == c.skip_cta ? (uint32_t)c.skip_load : 0xffffffffu;
             for (int64_t g = g_begin; g < g_end && ok;) {
                 const RowPos p = locate(job0, c, j, g, g_end);
                 for (int r = p.y - 1; r <= p.y + p.len && ok; ++r, ++L) {
                     const uint32_t slot = L % NS, u = L / NS;
-                    if (!ptx::mbar_wait(&empty[slot], (u & 1) ^ 1, abort_flag, BUDGET)) { ok = false; break; }
+                    if (!ptx::mbar_wait(&empty[slot], (u & 1) ^ 1, abort_flag, budget)) { ok = false; break; }
+                    if (L == skip_at) {   // nothing is issued or expected for this row
+                        skipped = L;
+                        continue;
+                    }
                     ptx::mbar_arrive_expect_tx(&full[slot], Mode::ROWB);
                     ptx::tma_load_5d(ring + slot * ROW_BYTES, &p.J->tin, &full[slot], 0,
                                      p.strip * (SEG / 8) - HALO_PX / 8, 0, r, p.img);
                 }
                 g += p.len;
             }
-            // wait for this thread's copies still in flight (only after an abort)
-            if (!ok) {
-                for (uint32_t k = (L > NS ? L - NS : 0); k < L; ++k)
-                    ptx::mbar_wait(&full[k % NS], (k / NS) & 1, abort_flag, BUDGET / 8);
-            }
+            loads = L;
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer: 12 MMAs (N = 192) per input row
-            bool ok = ptx::mbar_wait(wbar, 0, abort_flag, BUDGET);
+            bool ok = ptx::mbar_wait(wbar, 0, abort_flag, budget);
+            const bool w_landed = ok;
             const uint32_t ring_lo = (ptx::smem_u32(ring) >> 4) | A_LBO_FIELD;
             const uint32_t w_lo = (ptx::smem_u32(wsm) >> 4) | Mode::B_LBO;
             uint32_t L = 0;
@@ -284,8 +295,8 @@ __global__ void __launch_bounds__(TcMode<LAST, FP8>::THREADS, 1)
                 const RowPos p = locate(job0, c, j, g, g_end);
                 for (int ri = -1; ri <= p.len && ok; ++ri, ++L) {
                     const uint32_t reg = L % NACC, u = L / NACC;
-                    ok = ptx::mbar_wait(&full[L % NS], (L / NS) & 1, abort_flag, BUDGET);
-                    if (ok) ok = ptx::mbar_wait(&tempty[reg], (u & 1) ^ 1, abort_flag, BUDGET);
+                    ok = ptx::mbar_wait(&full[L % NS], (L / NS) & 1, abort_flag, budget);
+                    if (ok) ok = ptx::mbar_wait(&tempty[reg], (u & 1) ^ 1, abort_flag, budget);
                     if (!ok) break;
                     ptx::tc_fence_after();
                     const uint32_t a_row = ring_lo + (L % NS) * (ROW_BYTES >> 4);
@@ -303,10 +314,13 @@ __global__ void __launch_bounds__(TcMode<LAST, FP8>::THREADS, 1)
                 }
                 g += p.len;
             }
+            // every MMA of this thread completes before TMEM is released, and the
+            // weight copy lands before the CTA exits, also after an abort
             if (issued) {
                 ptx::mma_commit(drain);
-                ptx::mbar_wait(drain, 0, abort_flag, BUDGET);
+                ptx::mbar_wait_drain(drain, 0, budget);
             }
+            if (!w_landed) ptx::mbar_wait_drain(wbar, 0, budget);
         }
     } else if constexpr (LAST) {
         // ---------------- epilogue of the last layer: warps 2..5 own TMEM lane
@@ -352,7 +366,7 @@ __global__ void __launch_bounds__(TcMode<LAST, FP8>::THREADS, 1)
                 bool w = true;
                 for (int k = 0; k < nb && w; ++k) {
                     const uint32_t Lk = L + k;
-                    w = ptx::mbar_wait(&tfull[Lk % NACC], (Lk / NACC) & 1, abort_flag, BUDGET);
+                    w = ptx::mbar_wait(&tfull[Lk % NACC], (Lk / NACC) & 1, abort_flag, budget);
                 }
                 if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
                 ptx::tc_fence_after();
@@ -479,7 +493,7 @@ __global__ void __launch_bounds__(TcMode<LAST, FP8>::THREADS, 1)
             };
             for (int ri = -1; ri <= p.len; ++ri, ++L) {
                 const uint32_t reg = L % NACC, u = L / NACC;
-                if (!__all_sync(0xffffffffu, ptx::mbar_wait(&tfull[reg], u & 1, abort_flag, BUDGET))) { ok = false; break; }
+                if (!__all_sync(0xffffffffu, ptx::mbar_wait(&tfull[reg], u & 1, abort_flag, budget))) { ok = false; break; }
                 ptx::tc_fence_after();
                 const uint32_t taddr = lane_base + reg * Mode::RSTRIDE;
                 // output row q lives in X[q & 1]: prev = X[(ri-1) & 1], cur = X[ri & 1]
@@ -495,6 +509,12 @@ __global__ void __launch_bounds__(TcMode<LAST, FP8>::THREADS, 1)
 
     ptx::tc_fence_before();
     __syncthreads();
+    // after an abort the producer waits for its loads still in flight (the
+    // last NS issued; older ones were consumed before their slot was reused)
+    if (warp == 0 && lane == 0 && *abort_flag) {
+        for (uint32_t k = loads > (uint32_t)NS ? loads - NS : 0; k < loads; ++k)
+            if (k != skipped) ptx::mbar_wait_drain(&full[k % NS], (k / NS) & 1, budget);
+    }
     if (warp == 2) {
         ptx::tc_fence_after();
         ptx::tmem_dealloc(tmem_base, TMEM_COLS);
@@ -544,10 +564,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 template <bool FP8>
-__global__ void __launch_bounds__(128) k_first_tc(const float* __restrict__ x,
-                                                  const uint4* __restrict__ wb, int ny, int nx,
-                                                  int nxp, int nimg, const Rect* __restrict__ rects,
-                                                  void* __restrict__ out_, float inv_out,
+__global__ void __launch_bounds__(128) k_first_tc(const __grid_constant__ FirstTable T,
+                                                  const uint4* __restrict__ wb, float inv_out,
                                                   int* __restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -557,9 +575,7 @@ __global__ void __launch_bounds__(128) k_first_tc(const float* __restrict__ x,
     volatile int* abort_flag = (volatile int*)(smem + ftc::OFF_MISC + 4);
     const int warp = threadIdx.x / 32;
     const int p = threadIdx.x;
-    const uint32_t nsx = (uint32_t)(nxp + 127) / 128;
-    const uint32_t nseg = (uint32_t)nimg * (uint32_t)ny * nsx;   // < 2^31 (checked by the host)
-    const int64_t plane = (int64_t)ny * nx;
+    const uint32_t nseg = T.nseg;   // all jobs' segments, < 2^31 (checked by the host)
 
     if (threadIdx.x == 0) {
         ptx::mbar_init(&bar[0], 1);
@@ -582,27 +598,35 @@ __global__ void __launch_bounds__(128) k_first_tc(const float* __restrict__ x,
     pdl_launch_dependents();
     pdl_wait();
 
-    // segment -> (image, row, 128-pixel column block)
+    // segment -> (job, image, row, 128-pixel column block). A CTA's segments
+    // increase, so its job index only moves forward.
     struct Seg {
-        int img, yy, bx;
+        int job, img, yy, bx;
     };
+    int jcur = 0;
     auto decompose = [&](uint32_t seg) {
-        const uint32_t r = seg / nsx;
+        while (jcur + 1 < T.n && seg >= T.j[jcur + 1].seg_begin) ++jcur;
+        const FirstJob& J = T.j[jcur];
+        const uint32_t local = seg - J.seg_begin;
+        const uint32_t r = local / J.nsx;
         Seg q;
-        q.bx = (int)(seg - r * nsx);
-        q.img = (int)(r / (uint32_t)ny);
-        q.yy = (int)(r - (uint32_t)q.img * (uint32_t)ny);
+        q.job = jcur;
+        q.bx = (int)(local - r * J.nsx);
+        q.img = (int)(r / (uint32_t)J.ny);
+        q.yy = (int)(r - (uint32_t)q.img * (uint32_t)J.ny);
         return q;
     };
     // taps of one pixel of segment q (zero outside the image)
     auto load_taps = [&](const Seg& q, float v[9]) {
-        const int yy = q.yy, img = q.img;
+        const FirstJob& J = T.j[q.job];
+        const int yy = q.yy, img = q.img, ny = J.ny, nx = J.nx;
         const int xx = q.bx * 128 + p;
+        const float* x = J.x + (int64_t)img * ny * nx;
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
             const int sy = yy + t / 3 - 1, sx = xx + t % 3 - 1;
             v[t] = (sy >= 0 && sy < ny && sx >= 0 && sx < nx)
-                       ? __ldg(x + img * plane + (int64_t)sy * nx + sx)
+                       ? __ldg(x + (int64_t)sy * nx + sx)
                        : 0.f;
         }
     };
@@ -631,13 +655,14 @@ __global__ void __launch_bounds__(128) k_first_tc(const float* __restrict__ x,
         uint32_t acc[64];
         ptx::tmem_ld_32x32b_x64(tmem_base + ((uint32_t)(warp * 32) << 16) + buf * 64, acc);
         ptx::tmem_ld_wait();
-        const int yy = q.yy, img = q.img;
+        const FirstJob& J = T.j[q.job];
+        const int yy = q.yy, img = q.img, ny = J.ny, nx = J.nx, nxp = J.nxp;
         const int xx = q.bx * 128 + p;
         if (xx >= nxp) return;   // past the padded width: nothing to store
-        const Rect rc = rects ? rects[img] : Rect{0, ny, 0, nx};
+        const Rect rc = J.rects ? J.rects[img] : Rect{0, ny, 0, nx};
         const bool valid = xx < nx && yy >= rc.y0 && yy < rc.y1 && xx >= rc.x0 && xx < rc.x1;
         if constexpr (FP8) {
-            uint8_t* o = reinterpret_cast<uint8_t*>(out_) + (((int64_t)img * ny + yy) * 4 * nxp + xx) * 16;
+            uint8_t* o = reinterpret_cast<uint8_t*>(J.out) + (((int64_t)img * ny + yy) * 4 * nxp + xx) * 16;
 #pragma unroll
             for (int cg = 0; cg < 4; ++cg) {
                 uint32_t pk[4];
@@ -656,7 +681,7 @@ __global__ void __launch_bounds__(128) k_first_tc(const float* __restrict__ x,
                 *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
         } else {
-            __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(out_) + ((((int64_t)img * ny + yy) * 8) * nxp + xx) * 8;
+            __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(J.out) + ((((int64_t)img * ny + yy) * 8) * nxp + xx) * 8;
 #pragma unroll
             for (int cg = 0; cg < 8; ++cg) {
                 uint32_t pk[4];
@@ -788,6 +813,22 @@ cudaError_t tc_make_job(TcJob* J, const void* in, void* out, int ny, int nx, int
     return cudaSuccess;
 }
 
+// One-shot fault injection for the F -> F layers (pnp_debug_inject_tc_timeout):
+// armed by the host, consumed by the next such launch that is not being
+// captured into a graph.
+static std::mutex g_inject_mu;
+static bool g_inject_armed = false;
+static int g_inject_cta = -1, g_inject_load = 0;
+static long long g_inject_budget = 0;
+
+void tc_inject_timeout(int cta, int load_index, long long budget_cycles) {
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    g_inject_armed = true;
+    g_inject_cta = cta;
+    g_inject_load = load_index;
+    g_inject_budget = budget_cycles;
+}
+
 cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64_t total_rows,
                       const void* wblob, const float* bias_host, int* err, bool last,
                       cudaStream_t s, bool fp8, const float* scale_host, float inv_out) {
@@ -818,6 +859,20 @@ cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64
     c.jobs = jobs_dev;
     c.njobs = jobs_dev ? njobs : 1;
     c.total_rows = total_rows;
+    c.budget = tc::BUDGET;
+    c.skip_cta = -1;
+    c.skip_load = 0;
+    if (!last) {
+        std::lock_guard<std::mutex> lk(g_inject_mu);
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (g_inject_armed && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
+            cs == cudaStreamCaptureStatusNone) {
+            g_inject_armed = false;
+            c.skip_cta = g_inject_cta;
+            c.skip_load = g_inject_load;
+            c.budget = g_inject_budget;
+        }
+    }
     const int grid = (int)std::min<int64_t>(num_sms(), total_rows);
     timer_begin(last ? T_CONV_LAST : T_CONV_TC, s);
     cudaError_t e;
@@ -841,10 +896,11 @@ cudaError_t conv_tc_layer(const __nv_bfloat16* in, const __nv_bfloat16* wblob, c
     return tc_launch(J, nullptr, 1, J.rows, wblob, bias_host, err, false, s, false, nullptr, 1.f);
 }
 
+// One launch over up to FIRST_MAXJ image stacks (jobs); more jobs take
+// several launches. Jobs with no pixels are skipped.
 template <bool FP8>
-static cudaError_t launch_first_tc(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
-                                   const Rect* rects, void* out, float inv_out, int* err,
-                                   cudaStream_t s) {
+static cudaError_t launch_first_tc(const DenoiserDev& D, const FirstJob* jobs, int njobs,
+                                   float inv_out, int* err, cudaStream_t s) {
     static bool attr_done[2] = {false, false};
     if (!attr_done[FP8]) {
         cudaError_t e = cudaFuncSetAttribute(k_first_tc<FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -855,21 +911,55 @@ static cudaError_t launch_first_tc(const DenoiserDev& D, const float* x, int ny,
         if (e != cudaSuccess) return e;
         attr_done[FP8] = true;
     }
-    const int nxp = bf16_pad_width(nx);
-    const int64_t nseg = (int64_t)nimg * ny * ceil_div(nxp, 128);
-    if (nseg + (int64_t)num_sms() * ftc::CTAS_PER_SM >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
-    const int grid = (int)std::min<int64_t>(nseg, (int64_t)num_sms() * ftc::CTAS_PER_SM);
-    timer_begin(T_CONV_EDGE, s);
-    cudaError_t e = launch_pdl(k_first_tc<FP8>, dim3(grid), dim3(128), ftc::SMEM, s, x,
-                               reinterpret_cast<const uint4*>(D.wtc_first), ny, nx, nxp, nimg,
-                               rects, out, inv_out, err);
-    timer_end(T_CONV_EDGE, s);
-    return e;
+    for (int j0 = 0; j0 < njobs; j0 += FIRST_MAXJ) {
+        FirstTable T;
+        memset(&T, 0, sizeof(T));
+        int64_t nseg = 0;
+        for (int k = j0; k < std::min(njobs, j0 + FIRST_MAXJ); ++k) {
+            FirstJob J = jobs[k];
+            J.nxp = bf16_pad_width(J.nx);
+            J.nsx = (uint32_t)ceil_div(J.nxp, 128);
+            J.seg_begin = (uint32_t)nseg;
+            nseg += (int64_t)J.nimg * J.ny * J.nsx;
+            if (nseg + (int64_t)num_sms() * ftc::CTAS_PER_SM >= ((int64_t)1 << 31))
+                return cudaErrorInvalidValue;
+            T.j[T.n++] = J;
+        }
+        if (nseg == 0) continue;
+        T.nseg = (uint32_t)nseg;
+        const int grid = (int)std::min<int64_t>(nseg, (int64_t)num_sms() * ftc::CTAS_PER_SM);
+        timer_begin(T_CONV_EDGE, s);
+        cudaError_t e = launch_pdl(k_first_tc<FP8>, dim3(grid), dim3(128), ftc::SMEM, s, T,
+                                   reinterpret_cast<const uint4*>(D.wtc_first), inv_out, err);
+        timer_end(T_CONV_EDGE, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <bool FP8>
+static cudaError_t launch_first_tc(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
+                                   const Rect* rects, void* out, float inv_out, int* err,
+                                   cudaStream_t s) {
+    FirstJob J;
+    memset(&J, 0, sizeof(J));
+    J.x = x;
+    J.out = out;
+    J.rects = rects;
+    J.ny = ny;
+    J.nx = nx;
+    J.nimg = nimg;
+    return launch_first_tc<FP8>(D, &J, 1, inv_out, err, s);
 }
 
 cudaError_t first_layer_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
                              const Rect* rects, __nv_bfloat16* out, int* err, cudaStream_t s) {
     return launch_first_tc<false>(D, x, ny, nx, nimg, rects, out, 1.f, err, s);
+}
+
+cudaError_t first_layer_bf16_jobs(const DenoiserDev& D, const FirstJob* jobs, int njobs, int* err,
+                                  cudaStream_t s) {
+    return launch_first_tc<false>(D, jobs, njobs, 1.f, err, s);
 }
 
 cudaError_t last_layer_bf16(const DenoiserDev& D, const __nv_bfloat16* act, const float* x,
@@ -884,13 +974,14 @@ cudaError_t last_layer_bf16(const DenoiserDev& D, const __nv_bfloat16* act, cons
 }
 
 cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
-                         const Rect* rects, float* d, void* scratch, cudaStream_t s, bool residual) {
+                         const Rect* rects, float* d, void* scratch, cudaStream_t s, bool residual,
+                         int* err) {
     if (D.F != 64 || !D.wtc || !D.wtc_last || !D.wtc_first || D.K < 2) return cudaErrorInvalidValue;
     const int nxp = bf16_pad_width(nx);
     const size_t act = (size_t)nimg * ny * nxp * 64;
     __nv_bfloat16* A = (__nv_bfloat16*)scratch;
     __nv_bfloat16* B = A + act;
-    int* err = (int*)(B + act);
+    if (!err) err = (int*)(B + act);
     cudaError_t e = first_layer_bf16(D, x, ny, nx, nimg, rects, A, err, s);
     if (e != cudaSuccess) return e;
     for (int k = 1; k < D.K - 1; ++k) {
@@ -909,6 +1000,7 @@ __global__ void k_to_e4m3(const float* __restrict__ src, uint8_t* __restrict__ d
 }
 
 cudaError_t convert_e4m3(const float* src, uint8_t* dst, size_t n, cudaStream_t s) {
+    note_launch();
     k_to_e4m3<<<ceil_div((int64_t)n, 256), 256, 0, s>>>(src, dst, n);
     return cudaGetLastError();
 }
@@ -921,14 +1013,15 @@ size_t denoise_fp8_scratch(const DenoiserDev& D, int ny, int nx, int nimg) {
 // E4M3 denoiser: activations quantised with the per-layer static scales
 // D.a8_scale (input of layer k), weights with per-output-channel scales.
 cudaError_t denoise_fp8(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
-                        const Rect* rects, float* d, void* scratch, cudaStream_t s, bool residual) {
+                        const Rect* rects, float* d, void* scratch, cudaStream_t s, bool residual,
+                        int* err) {
     if (D.F != 64 || !D.wtc8 || !D.wtc8_last || !D.wtc_first || !D.fp8_calibrated)
         return cudaErrorInvalidValue;
     const int nxp = bf16_pad_width(nx);
     const size_t act = (size_t)nimg * ny * nxp * 64;
     uint8_t* A = (uint8_t*)scratch;
     uint8_t* B = A + act;
-    int* err = (int*)(B + act);
+    if (!err) err = (int*)(B + act);
     cudaError_t e = launch_first_tc<true>(D, x, ny, nx, nimg, rects, A, 1.f / D.a8_scale[1], err, s);
     if (e != cudaSuccess) return e;
     const size_t blob = 3 * 4 * 192 * 16;   // bytes of one F -> F layer

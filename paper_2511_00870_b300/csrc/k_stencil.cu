@@ -416,14 +416,22 @@ __global__ void __launch_bounds__(256) k_update(UpdateParams p) {
             const int64_t n = (int64_t)t + 1 - *p.burn_dev;
             inv_n = n > 0 ? 1.0f / (float)n : 0.0f;
         }
+        // one-pass gradient: the stencil ran over the current state x itself,
+        // so x at this thread's outputs is in the window (rows from i0 - kh/2,
+        // columns from j0 - AL), and x+ goes to the other state buffer
+        const bool fused = p.qb != nullptr;
+        const float* xwin = reinterpret_cast<const float*>(sm4) +
+                            (ty * R + kh / 2) * Geom<KW>::WP + 4 * tx + Geom<KW>::AL;
         float* xc = p.x + chain * plane;
+        float* xo = fused ? p.x_out + chain * plane : xc;
         const float* dc = p.d ? p.d + chain * plane : nullptr;
         float* mc = p.mean ? p.mean + chain * plane : nullptr;
         float* qc = p.m2 ? p.m2 + chain * plane : nullptr;
         const bool vec = (nx & 3) == 0 &&
                          ((reinterpret_cast<uintptr_t>(p.x) | reinterpret_cast<uintptr_t>(p.d) |
                            reinterpret_cast<uintptr_t>(p.mean) | reinterpret_cast<uintptr_t>(p.m2) |
-                           reinterpret_cast<uintptr_t>(p.z2)) & 15) == 0;
+                           reinterpret_cast<uintptr_t>(p.z2) | reinterpret_cast<uintptr_t>(p.qb) |
+                           reinterpret_cast<uintptr_t>(p.x_out)) & 15) == 0;
 #pragma unroll
         for (int o = 0; o < R; ++o) {
             const int i = i0 + ty * R + o;
@@ -431,8 +439,23 @@ __global__ void __launch_bounds__(256) k_update(UpdateParams p) {
             const int64_t n0 = (int64_t)i * nx + j;
             float z[4] = {0.f, 0.f, 0.f, 0.f};
             if (p.c_noise != 0.f) normals4(p.key0, p.key1, n0, t, (uint32_t)chain, z);
+            if (fused) {
+                // g = (H^T H) x - H^T y
+                if (vec) {
+                    const float4 bv = __ldg(reinterpret_cast<const float4*>(p.qb + n0));
+                    g[o][0] -= bv.x;
+                    g[o][1] -= bv.y;
+                    g[o][2] -= bv.z;
+                    g[o][3] -= bv.w;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (j + q < nx) g[o][q] -= __ldg(p.qb + n0 + q);
+                }
+            }
             if (vec) {
-                float4 xv = *reinterpret_cast<const float4*>(xc + n0);
+                float4 xv = fused ? *reinterpret_cast<const float4*>(xwin + o * Geom<KW>::WP)
+                                  : *reinterpret_cast<const float4*>(xc + n0);
                 float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (dc) dv = __ldg(reinterpret_cast<const float4*>(dc + n0));
                 float4 z2v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -442,7 +465,7 @@ __global__ void __launch_bounds__(256) k_update(UpdateParams p) {
                 v.y = update1(p, xv.y, g[o][1], dv.y, z[1], z2v.y);
                 v.z = update1(p, xv.z, g[o][2], dv.z, z[2], z2v.z);
                 v.w = update1(p, xv.w, g[o][3], dv.w, z[3], z2v.w);
-                *reinterpret_cast<float4*>(xc + n0) = v;
+                *reinterpret_cast<float4*>(xo + n0) = v;
                 if (inv_n > 0.f) {
                     float4 mo = *reinterpret_cast<const float4*>(mc + n0);
                     float4 qo = *reinterpret_cast<const float4*>(qc + n0);
@@ -458,9 +481,10 @@ __global__ void __launch_bounds__(256) k_update(UpdateParams p) {
                 for (int q = 0; q < 4; ++q) {
                     if (j + q >= nx) break;
                     const int64_t n = n0 + q;
-                    const float v = update1(p, xc[n], g[o][q], dc ? __ldg(dc + n) : 0.f, z[q],
+                    const float xv = fused ? xwin[o * Geom<KW>::WP + q] : xc[n];
+                    const float v = update1(p, xv, g[o][q], dc ? __ldg(dc + n) : 0.f, z[q],
                                             p.z2 ? __ldg(p.z2 + chain * plane + n) : 0.f);
-                    xc[n] = v;
+                    xo[n] = v;
                     if (inv_n > 0.f) {
                         float mo = mc[n], qo = qc[n];
                         welford1(v, inv_n, mo, qo);
@@ -1074,10 +1098,10 @@ cudaError_t stencil_autotune(const float* x, const float* y, const float* h, con
                              int kh, int kw, int ny, int nx, int nimg, float* r,
                              const UpdateParams& u, cudaStream_t s, int* blur_tile,
                              int* update_tile) {
-    using Key = std::tuple<int, int, int, int, int, bool>;
+    using Key = std::tuple<int, int, int, int, int, bool, bool>;
     static std::mutex mu;
     static std::map<Key, std::pair<int, int>> cache;
-    const Key key{ny, nx, kh, kw, nimg, hsep != nullptr};
+    const Key key{ny, nx, kh, kw, nimg, hsep != nullptr, u.qb != nullptr};
     {
         std::lock_guard<std::mutex> lk(mu);
         auto it = cache.find(key);
@@ -1149,6 +1173,7 @@ __global__ void k_finalize(const float* __restrict__ mean, const float* __restri
 cudaError_t launch_finalize_moments(const float* mean, const float* m2, int64_t npix,
                                     int64_t n_kept, int want_var, double* mmse, double* out2,
                                     cudaStream_t s) {
+    note_launch();
     k_finalize<<<ceil_div(npix, 256), 256, 0, s>>>(mean, m2, npix, n_kept, want_var, mmse, out2);
     return cudaGetLastError();
 }

@@ -7,8 +7,11 @@
 // latency-bound loop that must never stall, where cudaMalloc/cudaFree can
 // synchronize the device. This entry point runs the same kernels on a fixed
 // scratch area that lives in the library itself: a file-scope __device__
-// array, reserved by the CUDA loader when the library's module is loaded on
-// a GPU and held until the process exits.
+// array, held on a GPU from the moment its module is loaded there until the
+// process exits. With CUDA's lazy module loading that moment is the first
+// lookup of the array's address; pnp_create_denoiser does that lookup on the
+// current device (noalloc_reserve), so the area is reserved while device
+// memory is still free rather than at the first allocation-free call.
 #include "pnp_internal.h"
 
 namespace pnp {
@@ -35,6 +38,11 @@ static pnp_status noalloc_scratch(void** out) {
     }
     *out = g_noalloc_ptr[dev];
     return PNP_OK;
+}
+
+pnp_status noalloc_reserve() {
+    void* p = nullptr;
+    return noalloc_scratch(&p);
 }
 
 }  // namespace pnp
@@ -70,12 +78,10 @@ extern "C" pnp_status pnp_denoise_noalloc(const pnp_denoiser* den, pnp_precision
         // every activation plane is fully written before it is read
         PNP_CUDA_TRY(denoise_fp32(D, x, ny, nx, nimg, nullptr, d, (float*)scratch, s));
     } else {
-        // the tensor-core kernel's timeout flag sits after the two activation
-        // planes and must start at zero; the planes themselves (padding columns
-        // included) are fully rewritten by every layer
-        const size_t planes = need - 256;
-        PNP_CUDA_TRY(cudaMemsetAsync((unsigned char*)scratch + planes, 0, 256, s));
-        PNP_CUDA_TRY(denoise_bf16(D, x, ny, nx, nimg, nullptr, d, scratch, s));
+        // the activation planes (padding columns included) are fully rewritten
+        // by every layer; a tensor-core wait that runs out is reported in the
+        // denoiser's own flag (pnp_denoise_status)
+        PNP_CUDA_TRY(denoise_bf16(D, x, ny, nx, nimg, nullptr, d, scratch, s, false, den->err));
     }
     return PNP_OK;
 }

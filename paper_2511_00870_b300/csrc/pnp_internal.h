@@ -65,9 +65,13 @@ enum TimerId { T_BLUR = 0, T_UPDATE = 1, T_CONV_FP32 = 2, T_CONV_TC = 3, T_CONV_
 // such kernel signals griddepcontrol.launch_dependents only after its own TMEM
 // allocation, so a dependent that holds TMEM can never block a predecessor.
 bool pdl_enabled();
+// Counts kernel launches the library enqueues eagerly (pnp_launch_count);
+// launches replayed from a captured graph are not counted again.
+void note_launch();
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
                               cudaStream_t s, Args&&... args) {
+    note_launch();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -139,6 +143,9 @@ struct StepState {
 
 struct pnp_denoiser {
     pnp::DenoiserDev dev;
+    // device flag set to PNP_ETIMEOUT by a tensor-core layer of pnp_denoise or
+    // pnp_denoise_noalloc whose bounded wait ran out (read by pnp_denoise_status)
+    int* err = nullptr;
     // cached scratch (activation ping-pong), grown on demand
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -194,6 +201,13 @@ struct UpdateParams {
     float c_z2;                // gamma / rho2
     const WTap* wtaps;         // large kernels: adjoint taps (NULL: read h)
     int nwtaps;
+    // One-pass gradient (qb != NULL): g = (H^T H) r - qb with r the current
+    // state x (read through the stencil window, halo 2 r_h), the separable taps
+    // of H^T H in hsep and its size in kh, kw (2 kh_h - 1, 2 kw_h - 1), qb =
+    // H^T y [ny][nx]; x+ is written to x_out (not r: neighbouring tiles still
+    // read the current state).
+    const float* qb;
+    float* x_out;
 };
 
 // Auxiliary-variable update of the Poisson sampler (k_zupdate).
@@ -269,19 +283,49 @@ cudaError_t tc_launch(const TcJob& job0, const TcJob* jobs_dev, int njobs, int64
                       float inv_out = 1.f);
 cudaError_t first_layer_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
                              const Rect* rects, __nv_bfloat16* out, int* err, cudaStream_t s);
+// First layer over several image stacks in one launch (a by-value table of up
+// to FIRST_MAXJ jobs per launch): x, out, rects, ny, nx, nimg set by the
+// caller; nxp, nsx and seg_begin are filled by the launcher.
+struct FirstJob {
+    const float* x;
+    void* out;
+    const Rect* rects;
+    int ny, nx, nxp, nimg;
+    uint32_t seg_begin, nsx;
+};
+constexpr int FIRST_MAXJ = 64;
+struct FirstTable {
+    FirstJob j[FIRST_MAXJ];
+    int n;
+    uint32_t nseg;
+};
+cudaError_t first_layer_bf16_jobs(const DenoiserDev& D, const FirstJob* jobs, int njobs, int* err,
+                                  cudaStream_t s);
 cudaError_t last_layer_bf16(const DenoiserDev& D, const __nv_bfloat16* act, const float* x,
                             int ny, int nx, int nimg, float* d, int* err, cudaStream_t s);
 
 // BF16 tcgen05 denoiser (F = 64). scratch must hold denoise_bf16_scratch() bytes.
 // residual = true: write G = x - D(x) instead of d = D(x) (the chain's update
 // takes either; the tensor-core last layer then reads no x).
+// err: device flag that a layer whose bounded wait ran out sets to PNP_ETIMEOUT
+// (nullptr: an int right after the two activation planes in scratch).
 cudaError_t denoise_bf16(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
                          const Rect* rects, float* d, void* scratch, cudaStream_t s,
-                         bool residual = false);
+                         bool residual = false, int* err = nullptr);
 size_t denoise_bf16_scratch(const DenoiserDev& D, int ny, int nx, int nimg);
 cudaError_t denoise_fp8(const DenoiserDev& D, const float* x, int ny, int nx, int nimg,
                         const Rect* rects, float* d, void* scratch, cudaStream_t s,
-                        bool residual = false);
+                        bool residual = false, int* err = nullptr);
+// Arms a one-shot fault for the next F -> F tensor-core launch that is not
+// being captured: CTA `cta` skips its load number `load_index`, and every wait
+// of that launch gives up after budget_cycles (pnp_debug_inject_tc_timeout).
+void tc_inject_timeout(int cta, int load_index, long long budget_cycles);
+// Reads the device timeout flag (after waiting for stream s) and clears it:
+// PNP_ETIMEOUT with a message naming `who` if it was set, else PNP_OK.
+pnp_status take_timeout(int* flag, cudaStream_t s, const char* who);
+// Resolves the allocation-free entry point's fixed scratch area on the
+// current device (which reserves it); idempotent.
+pnp_status noalloc_reserve();
 size_t denoise_fp8_scratch(const DenoiserDev& D, int ny, int nx, int nimg);
 // FP32 denoiser that also records the largest activation of every layer's
 // output (amax_dev[k], k < K-1; activations are >= 0 after ReLU).
@@ -314,7 +358,12 @@ struct pnp_problem {
     int64_t N = 0;
     float* y = nullptr;
     float* h = nullptr;
+    // current chain state; with the one-pass gradient the state alternates
+    // between xb[0] and xb[1] (x = xb[par] at the point of the stream where the
+    // next enqueued iteration starts), otherwise xb[0] = xb[1] = x
     float* x = nullptr;
+    float* xb[2] = {nullptr, nullptr};
+    int par = 0;
     float* r = nullptr;
     float* d = nullptr;
     float* mean = nullptr;
@@ -347,8 +396,16 @@ struct pnp_problem {
     pnp::WTap* wt_fwd = nullptr;            // large kernels: forward / adjoint taps
     pnp::WTap* wt_adj = nullptr;
     int nwt = 0;
-    cudaGraphExec_t graph = nullptr;         // one iteration
-    cudaGraphExec_t graph_batch = nullptr;   // kGraphBatch iterations
+    // one-pass gradient g = (H^T H) x - H^T y of a separable blur (Gaussian
+    // noise, 2 kh - 1 and 2 kw - 1 <= 31): qb = H^T y, qsep = the separable
+    // taps of H^T H; the residual r is then not formed and xb[1] reuses its plane
+    bool fused = false;
+    float* qb = nullptr;
+    float* qsep = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};         // one iteration, per start parity
+    cudaGraphExec_t graph_batch[2] = {nullptr, nullptr};   // kGraphBatch iterations
+    bool eager_done = false;                 // one eager iteration ran (lazy kernel setup)
+    int* err = nullptr;                      // device timeout flag of the tensor-core layers
 };
 
 namespace pnp {
@@ -357,6 +414,12 @@ constexpr int kGraphBatch = 8;   // iterations per replayed graph
 // fused update (+ step counter advance).
 pnp_status problem_pre(pnp_problem* p, cudaStream_t s);
 pnp_status problem_post(pnp_problem* p, cudaStream_t s);
+// Advances the host-side state buffer after an iteration has been enqueued
+// (problem_post does it; graph replays do it for the iterations they hold).
+inline void problem_flip(pnp_problem* p) {
+    p->par ^= 1;
+    p->x = p->xb[p->par];
+}
 }  // namespace pnp
 
 namespace pnp {

@@ -68,6 +68,7 @@ struct pnp_server {
     bool stop = false;
     int64_t next_id = 1;
     int64_t pixel_iters = 0;
+    double device_s = 0.0;      // device time of the rounds' work (CUDA events)
 };
 
 // Device bytes a job needs: chain state, observation, kernel and denoiser scratch.
@@ -102,6 +103,11 @@ static void retire(pnp_server* s, ServerJob* j) {
 static void worker_loop(pnp_server* s) {
     cudaSetDevice(s->device);
     bool changed = true;
+    // events around each round's device work (admission copies and retirement
+    // read-backs fall outside them)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
     while (true) {
         std::vector<ServerJob*> admit;
         {
@@ -203,6 +209,7 @@ static void worker_loop(pnp_server* s) {
         std::vector<int64_t> prev_key;
         const BatchPlan* cur = nullptr;
         std::vector<pnp_problem*> sub;
+        const bool timed = ev0 && ev1 && cudaEventRecord(ev0, s->stream) == cudaSuccess;
         for (int64_t i = 0; i < kmax && st == PNP_OK; ++i) {
             std::vector<int64_t> key;
             std::vector<pnp_problem*> members;
@@ -227,7 +234,15 @@ static void worker_loop(pnp_server* s) {
             }
             if (st == PNP_OK) st = plan_enqueue_step(*cur, sub, s->stream);
         }
+        if (timed) cudaEventRecord(ev1, s->stream);
         cudaError_t e = cudaStreamSynchronize(s->stream);
+        float round_ms = 0.f;
+        if (timed && e == cudaSuccess && cudaEventElapsedTime(&round_ms, ev0, ev1) != cudaSuccess)
+            round_ms = 0.f;
+        // a tensor-core layer whose bounded wait ran out (flags of the round's
+        // jobs; the shared layers report into the first job's) fails the round
+        for (size_t q = 0; q < s->active.size() && st == PNP_OK && e == cudaSuccess; ++q)
+            st = take_timeout(s->active[q]->p->err, s->stream, "pnp_server");
         int64_t pix = 0;
         for (size_t q = 0; q < s->active.size(); ++q) {
             ServerJob* j = s->active[q];
@@ -237,6 +252,7 @@ static void worker_loop(pnp_server* s) {
         {
             std::lock_guard<std::mutex> g(s->mu);
             s->pixel_iters += pix;
+            s->device_s += 1e-3 * round_ms;
         }
         if (st != PNP_OK || e != cudaSuccess) {
             for (ServerJob* j : s->active) {
@@ -266,6 +282,8 @@ static void worker_loop(pnp_server* s) {
     }
     // shutdown: release whatever is still on the device
     cudaStreamSynchronize(s->stream);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
     for (ServerJob* j : s->active) {
         pnp_destroy_problem(j->p);
         j->p = nullptr;
@@ -410,6 +428,13 @@ extern "C" pnp_status pnp_server_stats(pnp_server* s, int64_t* pixel_iters, int*
     if (active) *active = (int)s->active.size();
     if (queued) *queued = (int)s->queue.size();
     if (used_bytes) *used_bytes = s->used;
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_server_device_seconds(pnp_server* s, double* seconds) {
+    if (!s || !seconds) return fail(PNP_EINVAL, "pnp_server_device_seconds: bad arguments");
+    std::lock_guard<std::mutex> g(s->mu);
+    *seconds = s->device_s;
     return PNP_OK;
 }
 

@@ -59,6 +59,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     }
 }
 
+// Bounded wait that ignores the abort flag, for unwinding: after an abort a
+// thread still waits (up to the budget) for the asynchronous copies and MMAs it
+// issued itself, so that none of them lands in shared memory or TMEM that the
+// CTA has already released. Returns false if the budget ran out.
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity,
+                                                long long budget_cycles) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (clock64() - t0 <= budget_cycles) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+    }
+    return false;
+}
+
 // TMA tiled load of a 5-D box into shared memory, completion on `bar`.
 __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
                                             int c1, int c2, int c3, int c4) {

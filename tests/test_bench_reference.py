@@ -1,6 +1,6 @@
 """The benchmark's reference arm (the FP64 oracle on a bounded crop) prints one
-JSON line with the contract's keys, for the default workload and for the
-DDFB and Poisson workloads (CPU only, a few seconds each)."""
+JSON line with the contract's keys, for the default (serving) workload, the
+1024^2 deconvolution and the DDFB and Poisson workloads (CPU only, a few seconds each)."""
 import json
 import os
 import subprocess
@@ -13,7 +13,7 @@ KEYS = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "
         "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"}
 
 
-@pytest.mark.parametrize("workload", ["deconv1024", "ddfb1024", "poisson1024"])
+@pytest.mark.parametrize("workload", ["serve", "deconv1024", "ddfb1024", "poisson1024"])
 def test_reference_arm_line(workload):
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
                           "--workload", workload, "--steps", "1", "--warmup", "3"],

@@ -103,20 +103,24 @@ def test_chain_same_for_every_tile(P, prec):
         np.testing.assert_array_equal(m, res[0][1])
 
 
-@pytest.mark.parametrize("kind", ["gaussian", "uniform", "motion"])
+@pytest.mark.parametrize("kind", ["gaussian", "uniform", "motion", "uniform15", "gaussian17"])
 def test_separable_and_direct_one_step_match_oracle(P, orc, kind):
-    """Rank-one kernels take the two-pass separable path, others the 2-D one;
-    either way one FP32 step (no prior) is within 1e-5 of the oracle's, on a
-    ragged 77 x 133 image."""
+    """Rank-one kernels of up to 15 taps take the one-pass gradient
+    (H^T H) x - H^T y over separable taps of H^T H (up to 29 taps), larger
+    rank-one kernels the two-pass separable residual and adjoint, others the
+    2-D stencils; every way one FP32 step (no prior) is within 1e-5 of the
+    oracle's H^T (H x - y) form, on a ragged 77 x 133 image, from states at two
+    step parities (the one-pass form alternates two state buffers)."""
     h = {"gaussian": synth.gaussian_kernel(9, 2.0), "uniform": synth.uniform_kernel(7),
-         "motion": synth.motion_kernel(11, 0.7)}[kind]
+         "motion": synth.motion_kernel(11, 0.7), "uniform15": synth.uniform_kernel(15),
+         "gaussian17": synth.gaussian_kernel(17, 3.0)}[kind]
     prob = synth.make_problem(77, 133, h, 25.0, 321)
     gp = P.Problem(prob.y, prob.h, prob.sigma, None, seed=prob.seed, burn_in=0)
     assert gp.stencil_tiles()[2] == (kind != "motion")
     prm = gp.params()
     rng = np.random.default_rng(5)
     x0 = rng.random(prob.shape).astype(np.float32)
-    for t in (0, 3):
+    for t in (0, 3, 4):
         gp.set_state(x0, t)
         gp.step(1)
         x1, _ = gp.state()
