@@ -394,7 +394,8 @@ def run_batch(args, P, torch, stream, ws, rank, local):
     peaks = load_peaks()
     probs = synth.batched_problems(48, seed=4000 + 17 * rank)
     den = P.Denoiser.from_weights(synth.workload_denoiser(2))
-    jobs = [dict(y=p.y, h=p.h, sigma=p.sigma, seed=p.seed, burn_in=200) for p in probs]
+    # timed in the sampling regime (burn-in 0: the Welford accumulation runs)
+    jobs = [dict(y=p.y, h=p.h, sigma=p.sigma, seed=p.seed, burn_in=0) for p in probs]
     npix = sum(p.y.size for p in probs)
     out = {}
     for prec in ("bf16", "fp32"):
@@ -416,15 +417,10 @@ def run_batch(args, P, torch, stream, ws, rank, local):
         rate, slow = replica_rate(npix * steps, e0.elapsed_time(e1) / 1e3, ws)
         out[prec] = dict(ms=slow * 1e3, steps=steps, value=rate, clocks=ck)
         if prec == "bf16":
-            P.pnp_kernel_timer(True)
-            b.step(10)
-            torch.cuda.synchronize()
-            kms, kn = P.pnp_kernel_timer_read("conv_tc")
-            nall = sum(P.pnp_kernel_timer_read(k)[1] for k in
-                       ("blur", "update", "conv_fp32", "conv_tc", "conv_edge", "conv_last"))
-            P.pnp_kernel_timer(False)
-            out[prec]["conv_tc_avg_ms"] = kms / max(kn, 1)
-            out[prec]["launches_per_iter"] = nall / 10
+            kb, kc = _timed_kernels(P, torch, b.step, 10)
+            out[prec]["conv_tc_avg_ms"] = kb["conv_tc"] / max(kc["conv_tc"], 1)
+            out[prec]["launches_per_iter"] = sum(kc.values()) / 10
+            out[prec]["kb"], out[prec]["kc"] = kb, kc
         b.close()
     if rank != 0:
         return
@@ -444,7 +440,11 @@ def run_batch(args, P, torch, stream, ws, rank, local):
         fp32_plain=dict(value=round(out["fp32"]["value"], 3), unit=UNIT, steps=out["fp32"]["steps"],
                         speedup_bf16=round(out["bf16"]["value"] / out["fp32"]["value"], 3)),
         gpu_launches=int(round(out["bf16"]["launches_per_iter"])) * args.steps,
+        launches_per_iter=out["bf16"]["launches_per_iter"],
         clocks=out["bf16"]["clocks"],
+        kernel_breakdown_ms=dict(bf16=out["bf16"]["kb"], launches=out["bf16"]["kc"], iterations=10),
+        stencil_roofline=_stencil_roofline(peaks, dict(breakdown=out["bf16"]["kb"],
+                                                       counts=out["bf16"]["kc"]), npix, iters=10),
         latency=dict(p50_s=None, p99_s=None, note="batch of 48 jobs stepped together"),
     )
     print(json.dumps(line), flush=True)
@@ -565,7 +565,7 @@ def run_serve(args, P, torch, stream, ws, rank, local):
     # roofline: the tensor-core conv over a table of the stream's jobs (one
     # launch per layer over all of them, as in the server's rounds), timed alone
     sub = probs[:min(n, 8)]
-    b = P.Batch([dict(y=p.y, h=p.h, sigma=p.sigma, seed=p.seed, burn_in=TB) for p in sub], den,
+    b = P.Batch([dict(y=p.y, h=p.h, sigma=p.sigma, seed=p.seed, burn_in=0) for p in sub], den,
                 precision="bf16", stream=stream.cuda_stream)
     b.step(3)
     kb, kc = _timed_kernels(P, torch, b.step, 10)
@@ -647,6 +647,12 @@ def measure_single(args, P, torch, stream, ws, rank, local, workload, precs, ste
     ddfb = workload == "ddfb1024"
     prob = (poisson_problem(rank) if poisson else inpainting_problem(rank) if inpaint
             else synth.workload_problem(cfg_id, job=rank))
+    if getattr(args, "size", 0) and not (poisson or inpaint):
+        # the same posterior (blur, BSNR, denoiser) on an n x n image: profiling runs
+        n = args.size
+        prob = synth.make_problem(n, n, synth.blur_from_spec(w["blur"]), w["bsnr"],
+                                  synth.gt_seed(cfg_id, rank), name=f"{w['name']}@{n}",
+                                  blocks=w["blocks"], halo=w["halo"], T=w["T"], burn_in=w["burn_in"])
     dw = synth.workload_denoiser(cfg_id)
     if ddfb:
         dd = ddfb_net()
@@ -673,9 +679,12 @@ def measure_single(args, P, torch, stream, ws, rank, local, workload, precs, ste
     results = {}
     clocks = None
     for prec in precs:
-        gp = make_problem(prec, w["burn_in"])
+        # the timed iterations sample (burn-in 0): the Welford accumulation runs,
+        # as in 80 % of a chain's iterations, and the stencil moves 32 B/pixel
+        gp = make_problem(prec, 0)
         st = steps if prec == precs[0] else min(steps, 200)
         gp.step(warmup)
+        gp.prepare_graphs()
         torch.cuda.synchronize()
         rank_barrier(ws)
         torch.cuda.synchronize()
@@ -775,8 +784,8 @@ def measure_single(args, P, torch, stream, ws, rank, local, workload, precs, ste
         wl = (f"ddfb1024: {ny}x{nx} grayscale, {w['bsnr']} dB BSNR, DDFB prior K=4 P=64 (FP32), "
               f"blur {w['blur'][0]} {w['blur'][1]}x{w['blur'][1]}, ")
     else:
-        wl = (f"{w['name']}: {ny}x{nx} grayscale, {w['bsnr']} dB BSNR, "
-              f"blur {w['blur'][0]} {w['blur'][1]}x{w['blur'][1]}, ")
+        wl = (f"{w['name']}{' resized' if getattr(args, 'size', 0) else ''}: {ny}x{nx} grayscale, "
+              f"{w['bsnr']} dB BSNR, blur {w['blur'][0]} {w['blur'][1]}x{w['blur'][1]}, ")
     wl += ("" if ddfb else f"DnCNN-form K={K} F={F}, ") + \
         f"{w['blocks'][0]}x{w['blocks'][1]} blocks (halo-exchange-free), 1 chain per GPU"
     line = dict(
@@ -830,6 +839,8 @@ def main():
                     help="serve: skip the nested single-job deconv1024 / deconv8192 lines")
     ap.add_argument("--precisions", default="bf16,fp32,fp8")
     ap.add_argument("--jobs", type=int, default=0, help="serve: number of arrivals (default: --steps)")
+    ap.add_argument("--size", type=int, default=0,
+                    help="single-job Gaussian workloads: the same posterior on a size x size image")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -283,6 +283,12 @@ pnp_status pnp_problem_params(const pnp_problem* p, double* lambda, double* gamm
 /* Enqueue n_iters iterations (asynchronous on the problem's stream). Uses a
  * captured CUDA graph of one iteration when use_graph != 0. */
 pnp_status pnp_step(pnp_problem* p, int n_iters);
+/* Captures and instantiates now the CUDA graphs that later pnp_step calls
+ * replay (one and kGraphBatch = 8 iterations, for each state-buffer parity),
+ * so that no capture happens inside a caller's timed region. Host work only;
+ * needs one earlier pnp_step (its first iteration runs eagerly). PNP_OK and
+ * nothing done when graph mode is off. */
+pnp_status pnp_prepare_graphs(pnp_problem* p);
 /* Run T iterations with the given burn-in (resets nothing) and wait. */
 pnp_status pnp_run_chain(pnp_problem* p, int T, int burn_in);
 /* Wait for the problem's stream. PNP_ETIMEOUT if a bounded device-side wait

@@ -313,6 +313,10 @@ class Problem:
     def sync(self):
         check(load().pnp_sync(self.handle))
 
+    def prepare_graphs(self):
+        """pnp_prepare_graphs: capture the replayed graphs now (after one step)."""
+        check(load().pnp_prepare_graphs(self.handle))
+
     def run_chain(self, T, burn_in):
         check(load().pnp_run_chain(self.handle, int(T), int(burn_in)))
 

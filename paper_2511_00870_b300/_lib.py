@@ -73,6 +73,7 @@ SIGNATURES = {
     "pnp_step": ([vp, i32], i32),
     "pnp_run_chain": ([vp, i32, i32], i32),
     "pnp_sync": ([vp], i32),
+    "pnp_prepare_graphs": ([vp], i32),
     "pnp_get_moments": ([vp, i32, dp, dp, C.POINTER(i64), i32], i32),
     "pnp_get_state": ([vp, fp, C.POINTER(i64)], i32),
     "pnp_set_state": ([vp, fp, i64], i32),

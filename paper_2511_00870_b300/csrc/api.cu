@@ -727,7 +727,7 @@ pnp_status problem_pre(pnp_problem* p, cudaStream_t s) {
 
 // The update of one iteration on the problem's buffers; the kernel reads the
 // step counter from the device and its last block advances it.
-static pnp_status problem_update_params(const pnp_problem* p, UpdateParams& u) {
+pnp_status problem_update_params(const pnp_problem* p, UpdateParams& u) {
     const bool prior = p->D && p->alpha != 0.0;
     // Poisson: the H^T r coefficient eta / rho1 takes the place of 1 / sigma^2
     const double sig = p->poisson ? std::sqrt(p->rho1 / p->eta) : p->sigma;
@@ -764,7 +764,7 @@ static pnp_status problem_update_params(const pnp_problem* p, UpdateParams& u) {
     return PNP_OK;
 }
 
-static ZParams problem_z_params(const pnp_problem* p) {
+ZParams problem_z_params(const pnp_problem* p) {
     ZParams z;
     z.x = p->x;
     z.z1 = p->z1;
@@ -1331,6 +1331,26 @@ extern "C" pnp_status pnp_step(pnp_problem* p, int n_iters) {
     }
     p->t += n_iters;
     return PNP_OK;
+}
+
+extern "C" pnp_status pnp_prepare_graphs(pnp_problem* p) {
+    if (!p) return fail(PNP_EINVAL, "problem is NULL");
+    if (!g_use_graph || g_timing) return PNP_OK;
+    if (!p->eager_done)
+        return fail(PNP_ESTATE, "pnp_prepare_graphs: step the problem once first (its first "
+                                "iteration runs eagerly and performs the lazy kernel setup)");
+    const int par0 = p->par;
+    const int npar = p->xb[0] == p->xb[1] ? 1 : 2;
+    pnp_status st = PNP_OK;
+    for (int k = 0; k < npar && st == PNP_OK; ++k) {
+        p->par = k;
+        p->x = p->xb[k];
+        if (!p->graph[k]) st = capture_graph(p, 1, &p->graph[k]);
+        if (st == PNP_OK && !p->graph_batch[k]) st = capture_graph(p, kGraphBatch, &p->graph_batch[k]);
+    }
+    p->par = par0;
+    p->x = p->xb[par0];
+    return st;
 }
 
 extern "C" pnp_status pnp_sync(pnp_problem* p) {

@@ -10,6 +10,7 @@
 // Philox stream and step counter).
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "pnp_internal.h"
@@ -75,10 +76,57 @@ void plan_free(BatchPlan& plan) {
     plan.cap = 0;
 }
 
+// r = H x - y for every job that forms it: one grouped launch per (kernel
+// width, form) over the jobs with small kernels; wide kernels per job.
+static pnp_status enqueue_residuals(const std::vector<pnp_problem*>& jobs, cudaStream_t s) {
+    std::map<std::pair<int, bool>, std::vector<BlurArgs>> groups;
+    for (pnp_problem* p : jobs) {
+        if (p->inpaint || p->poisson || p->fused) continue;   // no residual plane this iteration
+        if (is_wide(p->kh, p->kw)) {
+            PNP_TRY(problem_pre(p, s));
+            continue;
+        }
+        BlurArgs a{p->x, p->y, p->hsep ? p->hsep : p->h, p->kh, p->ny, p->nx, p->nchain,
+                   1.0f, 0, p->r, 1.0f, 0};
+        groups[{p->kw, p->hsep != nullptr}].push_back(a);
+    }
+    for (auto& g : groups)
+        PNP_CUDA_TRY(launch_blur_group(g.second.data(), (int)g.second.size(), g.first.first,
+                                       g.first.second, s));
+    return PNP_OK;
+}
+
+// The x-updates (and Poisson z-updates) of every job: one grouped launch per
+// (stencil width, form); inpainting and wide-kernel jobs per job. Every job's
+// state buffer advances afterwards.
+static pnp_status enqueue_updates(const std::vector<pnp_problem*>& jobs, cudaStream_t s) {
+    std::map<std::pair<int, bool>, std::vector<UpdateParams>> ug;
+    std::map<std::pair<int, bool>, std::vector<ZParams>> zg;
+    std::vector<pnp_problem*> grouped;
+    for (pnp_problem* p : jobs) {
+        if (p->inpaint || is_wide(p->kh, p->kw)) {
+            PNP_TRY(problem_post(p, s));   // advances its own state buffer
+            continue;
+        }
+        UpdateParams u;
+        PNP_TRY(problem_update_params(p, u));
+        ug[{u.kw, u.hsep != nullptr}].push_back(u);
+        if (p->poisson) {
+            const ZParams z = problem_z_params(p);
+            zg[{z.kw, z.hsep != nullptr}].push_back(z);
+        }
+        grouped.push_back(p);
+    }
+    for (auto& g : ug) PNP_CUDA_TRY(launch_update_group(g.second.data(), (int)g.second.size(), s));
+    for (auto& g : zg) PNP_CUDA_TRY(launch_zupdate_group(g.second.data(), (int)g.second.size(), s));
+    for (pnp_problem* p : grouped) problem_flip(p);
+    return PNP_OK;
+}
+
 pnp_status plan_enqueue_step(const BatchPlan& plan, const std::vector<pnp_problem*>& jobs,
                              cudaStream_t s) {
     if (jobs.empty()) return PNP_OK;
-    for (pnp_problem* p : jobs) PNP_TRY(problem_pre(p, s));
+    PNP_TRY(enqueue_residuals(jobs, s));
     const pnp_problem* p0 = jobs[0];
     if (p0->D && p0->alpha != 0.0) {
         const DenoiserDev& D = p0->D->dev;
@@ -114,8 +162,7 @@ pnp_status plan_enqueue_step(const BatchPlan& plan, const std::vector<pnp_proble
                                           (float*)p->scratch, s));
         }
     }
-    for (pnp_problem* p : jobs) PNP_TRY(problem_post(p, s));
-    return PNP_OK;
+    return enqueue_updates(jobs, s);
 }
 
 }  // namespace pnp
@@ -130,6 +177,7 @@ struct pnp_batch {
     // one graph per phase: every job steps each iteration, so the jobs' state
     // buffers alternate together (phase = iterations since creation mod 2)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::vector<int> graph_par[2];   // every job's state buffer when graph[k] was captured
     int phase = 0;
     bool eager_done = false;
 };
@@ -200,10 +248,15 @@ extern "C" pnp_status pnp_batch_step(pnp_batch* b, int n_iters) {
             b->eager_done = true;
         } else {
             cudaGraphExec_t& ge = b->graph[b->phase];
+            std::vector<int> par0;
+            for (pnp_problem* p : b->jobs) par0.push_back(p->par);
+            if (ge && b->graph_par[b->phase] != par0) {
+                // a job was stepped outside the batch: its buffers changed roles
+                cudaGraphExecDestroy(ge);
+                ge = nullptr;
+            }
             if (!ge) {
                 // capturing executes nothing: the jobs' state buffers are restored
-                std::vector<int> par0;
-                for (pnp_problem* p : b->jobs) par0.push_back(p->par);
                 cudaGraph_t g = nullptr;
                 PNP_CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
                 pnp_status st = plan_enqueue_step(b->plan, b->jobs, b->stream);
@@ -223,6 +276,7 @@ extern "C" pnp_status pnp_batch_step(pnp_batch* b, int n_iters) {
                     ge = nullptr;
                     return cuda_fail(e, "cudaGraphInstantiate");
                 }
+                b->graph_par[b->phase] = par0;
             }
             PNP_CUDA_TRY(cudaGraphLaunch(ge, b->stream));
             for (pnp_problem* p : b->jobs) problem_flip(p);

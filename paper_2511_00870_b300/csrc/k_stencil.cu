@@ -21,9 +21,11 @@
 // strip T = window * v, then a vertical pass out = sum_a u[a] T[i + a] -
 // kh + kw instead of kh kw FMAs per output, again in a fixed order.
 #include <atomic>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 #include "pdl.cuh"
 #include "philox.cuh"
@@ -70,10 +72,33 @@ __device__ __forceinline__ int wrap(int c, int n) {
     return min(max(c, 0), n - 1);
 }
 
+// Asynchronous global -> shared copies (cp.async): every thread issues all of
+// its copies of a window before waiting for any, so the whole window is in
+// flight at once instead of one load per thread at a time.
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void prefetch_l2(const float* p) {
+    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Window rows [0, rows + kh - 1) x cols [0, WXA) of image `img` starting at
-// image coordinate (i0 - ry, j0 - AL), wrapped circularly. Interior tiles of
-// images whose rows are whole 16-byte units load 16 bytes per thread and
-// access; others one float at a time.
+// image coordinate (i0 - ry, j0 - AL), wrapped circularly, copied
+// asynchronously (the caller waits with cp_async_wait_all before its
+// barrier). Interior tiles of images whose rows are whole 16-byte units copy
+// 16 bytes per access; others one float at a time.
 template <int KW>
 __device__ __forceinline__ void fill_window(const float* __restrict__ img, int ny, int nx, int i0,
                                             int j0, int kh, int rows, float* win) {
@@ -90,20 +115,19 @@ __device__ __forceinline__ void fill_window(const float* __restrict__ img, int n
         const float* base = img + (int64_t)(i0 - ry) * nx + (j0 - G::AL);
         for (int e = tid; e < wy * NV; e += nt) {
             const int u = e / NV, c4 = e - u * NV;
-            const float4 v = __ldg(reinterpret_cast<const float4*>(base + (int64_t)u * nx) + c4);
-            *reinterpret_cast<float4*>(win + u * G::WP + 4 * c4) = v;
+            cp_async16(win + u * G::WP + 4 * c4, base + (int64_t)u * nx + 4 * c4);
         }
     } else if (interior) {
         const float* base = img + (int64_t)(i0 - ry) * nx + (j0 - G::AL);
         for (int e = tid; e < wy * G::WXA; e += nt) {
             const int u = e / G::WXA, v = e - u * G::WXA;
-            win[u * G::WP + v] = __ldg(base + (int64_t)u * nx + v);
+            cp_async4(win + u * G::WP + v, base + (int64_t)u * nx + v);
         }
     } else {
         for (int e = tid; e < wy * G::WXA; e += nt) {
             const int u = e / G::WXA, v = e - u * G::WXA;
             const int gi = wrap(i0 - ry + u, ny), gj = wrap(j0 - G::AL + v, nx);
-            win[u * G::WP + v] = __ldg(img + (int64_t)gi * nx + gj);
+            cp_async4(win + u * G::WP + v, img + (int64_t)gi * nx + gj);
         }
     }
 }
@@ -280,6 +304,7 @@ __device__ __forceinline__ void stencil_tile(const float* img, int ny, int nx, i
         float* vs = T + wy * ST_TX;
         float* us = vs + G::KWP;
         load_taps_sep<KW>(h, kh, flip, vs, us);
+        cp_async_wait_all();
         __syncthreads();
         sep_rows<KW>(win, vs, wy, T);
         __syncthreads();
@@ -287,6 +312,7 @@ __device__ __forceinline__ void stencil_tile(const float* img, int ny, int nx, i
     } else {
         float* hs = win + wy * G::WP;
         load_taps2d<KW>(h, kh, flip, hs);
+        cp_async_wait_all();
         __syncthreads();
         if (active) correlate<KW, R>(win, hs, kh, threadIdx.y, threadIdx.x, acc);
     }
@@ -295,16 +321,18 @@ __device__ __forceinline__ void stencil_tile(const float* img, int ny, int nx, i
 // out = (a (h * x) - y) scale; y is shared by the images (y_img_stride 0) or
 // one plane per image (the Poisson sampler's z1).
 template <int KW, int R, bool SEP>
-__global__ void __launch_bounds__(256) k_blur(const float* __restrict__ x,
-                                              const float* __restrict__ y,
-                                              const float* __restrict__ h, int kh, int ny, int nx,
-                                              float scale, int adjoint, float* __restrict__ out,
-                                              float a, int64_t y_img_stride) {
+__device__ __forceinline__ void blur_body(const BlurArgs& A, int bx, int by, int img) {
     extern __shared__ float4 sm4[];
+    const float* __restrict__ x = A.x;
+    const float* __restrict__ y = A.y;
+    const float* __restrict__ h = A.h;
+    const int kh = A.kh, ny = A.ny, nx = A.nx, adjoint = A.adjoint;
+    const float scale = A.scale, a = A.a;
+    float* __restrict__ out = A.out;
+    const int64_t y_img_stride = A.y_img_stride;
     const int rows = R * blockDim.y;
     const int64_t plane = (int64_t)ny * nx;
-    const int img = blockIdx.z;
-    const int i0 = blockIdx.y * rows, j0 = blockIdx.x * ST_TX;
+    const int i0 = by * rows, j0 = bx * ST_TX;
     pdl_wait();
     pdl_launch_dependents();
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -325,7 +353,10 @@ __global__ void __launch_bounds__(256) k_blur(const float* __restrict__ x,
         if (i >= ny) break;
         const int64_t n = (int64_t)i * nx + j;
         if (vec) {
-            float4 v = make_float4(a * acc[o][0], a * acc[o][1], a * acc[o][2], a * acc[o][3]);
+            // a (h * x) rounded before y is subtracted (no fused multiply-add),
+            // so the per-job and the grouped launches give the same r
+            float4 v = make_float4(__fmul_rn(a, acc[o][0]), __fmul_rn(a, acc[o][1]),
+                                   __fmul_rn(a, acc[o][2]), __fmul_rn(a, acc[o][3]));
             if (y) {
                 const float4 yv = __ldg(reinterpret_cast<const float4*>(y + n));
                 v.x -= yv.x; v.y -= yv.y; v.z -= yv.z; v.w -= yv.w;
@@ -336,13 +367,18 @@ __global__ void __launch_bounds__(256) k_blur(const float* __restrict__ x,
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if (j + q < nx) {
-                    float v = a * acc[o][q];
+                    float v = __fmul_rn(a, acc[o][q]);
                     if (y) v -= __ldg(y + n + q);
                     out[img * plane + n + q] = v * scale;
                 }
             }
         }
     }
+}
+
+template <int KW, int R, bool SEP>
+__global__ void __launch_bounds__(256) k_blur(const BlurArgs A) {
+    blur_body<KW, R, SEP>(A, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -394,19 +430,36 @@ __device__ __forceinline__ void welford1(float v, float inv_n, float& mo, float&
 }
 
 template <int KW, int R, bool SEP>
-__global__ void __launch_bounds__(256) k_update(UpdateParams p) {
+__device__ __forceinline__ void update_body(const UpdateParams& p, int bx, int by, int chain,
+                                            unsigned nblk) {
     extern __shared__ float4 sm4[];
     const int kh = p.kh, ny = p.ny, nx = p.nx;
     const int rows = R * blockDim.y;
     const int64_t plane = (int64_t)ny * nx;
-    const int chain = blockIdx.z;
-    const int i0 = blockIdx.y * rows, j0 = blockIdx.x * ST_TX;
+    const int i0 = by * rows, j0 = bx * ST_TX;
     pdl_wait();
     pdl_launch_dependents();
     const uint32_t t = p.t_dev ? *p.t_dev : p.t;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int j = j0 + 4 * tx;
     const bool active = j < nx && i0 + ty * R < ny;
+    if (active && (tx & 7) == 0) {
+        // the operands of this thread's outputs head for L2 while the window is
+        // copied and the stencil runs (one 128-byte line per 8 threads of a row)
+#pragma unroll
+        for (int o = 0; o < R; ++o) {
+            const int i = i0 + ty * R + o;
+            if (i >= ny) break;
+            const int64_t n0 = (int64_t)chain * plane + (int64_t)i * nx + j;
+            if (p.d) prefetch_l2(p.d + n0);
+            if (p.qb) prefetch_l2(p.qb + (int64_t)i * nx + j);
+            if (p.mean) {
+                prefetch_l2(p.mean + n0);
+                prefetch_l2(p.m2 + n0);
+            }
+            if (!p.qb) prefetch_l2(p.x + n0);
+        }
+    }
     float g[R][4];
     stencil_tile<KW, R, SEP>(p.r + chain * plane, ny, nx, i0, j0, kh, rows,
                              SEP ? p.hsep : p.h, false, reinterpret_cast<float*>(sm4), active, g);
@@ -498,13 +551,18 @@ __global__ void __launch_bounds__(256) k_update(UpdateParams p) {
     if (p.arrive) {
         __syncthreads();
         if (threadIdx.x == 0 && threadIdx.y == 0) {
-            const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
             if (atomicAdd(p.arrive, 1u) == nblk - 1) {
                 *p.arrive = 0u;
                 *const_cast<uint32_t*>(p.t_dev) = t + 1u;
             }
         }
     }
+}
+
+template <int KW, int R, bool SEP>
+__global__ void __launch_bounds__(256) k_update(const UpdateParams p) {
+    update_body<KW, R, SEP>(p, blockIdx.x, blockIdx.y, blockIdx.z,
+                            gridDim.x * gridDim.y * gridDim.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -528,13 +586,13 @@ __device__ __forceinline__ float kl_prox(float v, float y, float kappa) {
 }
 
 template <int KW, int R, bool SEP>
-__global__ void __launch_bounds__(256) k_zupdate(ZParams p) {
+__device__ __forceinline__ void zupdate_body(const ZParams& p, int bx, int by, int chain,
+                                             unsigned nblk) {
     extern __shared__ float4 sm4[];
     const int kh = p.kh, ny = p.ny, nx = p.nx;
     const int rows = R * blockDim.y;
     const int64_t plane = (int64_t)ny * nx;
-    const int chain = blockIdx.z;
-    const int i0 = blockIdx.y * rows, j0 = blockIdx.x * ST_TX;
+    const int i0 = by * rows, j0 = bx * ST_TX;
     pdl_wait();
     pdl_launch_dependents();
     const uint32_t t = p.t_dev ? *p.t_dev : p.t;
@@ -563,7 +621,10 @@ __global__ void __launch_bounds__(256) k_zupdate(ZParams p) {
             for (int q = 0; q < 4; ++q) {
                 if (j + q >= nx) break;
                 const int64_t n = n0 + q;
-                const float w = p.eta * hx[o][q];
+                // eta H x+ rounded once: every kernel that inlines this body
+                // (per job or grouped) then forms z1+ and r from the same w,
+                // whatever multiply-add fusion the compiler picks around it
+                const float w = __fmul_rn(p.eta, hx[o][q]);
                 const float z1 = z1c[n];
                 const float v1 = z1 - p.a1 * (z1 - w) + p.s1 * e1[q];
                 const float z1n = kl_prox(v1, __ldg(p.y + n), p.kappa1);
@@ -578,13 +639,85 @@ __global__ void __launch_bounds__(256) k_zupdate(ZParams p) {
     if (p.arrive) {
         __syncthreads();
         if (threadIdx.x == 0 && threadIdx.y == 0) {
-            const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
             if (atomicAdd(p.arrive, 1u) == nblk - 1) {
                 *p.arrive = 0u;
                 *const_cast<uint32_t*>(p.t_dev) = t + 1u;
             }
         }
     }
+}
+
+template <int KW, int R, bool SEP>
+__global__ void __launch_bounds__(256) k_zupdate(const ZParams p) {
+    zupdate_body<KW, R, SEP>(p, blockIdx.x, blockIdx.y, blockIdx.z,
+                             gridDim.x * gridDim.y * gridDim.z);
+}
+
+// ---------------------------------------------------------------------------
+// Grouped launches (batches of jobs): one launch runs the tiles of several jobs
+// that share a kernel width, form and tile shape. The arguments of every job
+// travel by value; block b works on the last job j with tile_begin[j] <= b,
+// whose tiles are ordered (image, tile row, tile column) as in a per-job
+// launch, so every output is the same sum as when the job runs alone.
+// ---------------------------------------------------------------------------
+template <typename A>
+struct StencilTable {
+    A a[STENCIL_TABLE_MAXJ];
+    uint32_t tile_begin[STENCIL_TABLE_MAXJ];
+    int n;
+};
+constexpr int GRP_R = 4, GRP_BY = 16;   // the grouped launches' tile: 64 x 64 outputs
+
+__device__ __forceinline__ int table_job(const uint32_t* begin, int n, uint32_t b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// (tile column, tile row, image, tiles of the job) of block b of job j
+struct TilePos {
+    int bx, by, img;
+    unsigned nblk;
+};
+__device__ __forceinline__ TilePos table_tile(uint32_t local, int ny, int nx, int nimg) {
+    const uint32_t tx = (uint32_t)(nx + ST_TX - 1) / ST_TX;
+    const uint32_t ty = (uint32_t)(ny + GRP_R * GRP_BY - 1) / (GRP_R * GRP_BY);
+    const uint32_t per = tx * ty;
+    const uint32_t img = local / per, rem = local - img * per;
+    TilePos t;
+    t.by = (int)(rem / tx);
+    t.bx = (int)(rem - (uint32_t)t.by * tx);
+    t.img = (int)img;
+    t.nblk = per * (uint32_t)nimg;
+    return t;
+}
+
+template <int KW, bool SEP>
+__global__ void __launch_bounds__(256) k_blur_jobs(const __grid_constant__ StencilTable<BlurArgs> T) {
+    const int j = table_job(T.tile_begin, T.n, blockIdx.x);
+    const BlurArgs& A = T.a[j];
+    const TilePos q = table_tile(blockIdx.x - T.tile_begin[j], A.ny, A.nx, A.nimg);
+    blur_body<KW, GRP_R, SEP>(A, q.bx, q.by, q.img);
+}
+
+template <int KW, bool SEP>
+__global__ void __launch_bounds__(256) k_update_jobs(const __grid_constant__ StencilTable<UpdateParams> T) {
+    const int j = table_job(T.tile_begin, T.n, blockIdx.x);
+    const UpdateParams& p = T.a[j];
+    const TilePos q = table_tile(blockIdx.x - T.tile_begin[j], p.ny, p.nx, p.nchain);
+    update_body<KW, GRP_R, SEP>(p, q.bx, q.by, q.img, q.nblk);
+}
+
+template <int KW, bool SEP>
+__global__ void __launch_bounds__(256) k_zupdate_jobs(const __grid_constant__ StencilTable<ZParams> T) {
+    const int j = table_job(T.tile_begin, T.n, blockIdx.x);
+    const ZParams& p = T.a[j];
+    const TilePos q = table_tile(blockIdx.x - T.tile_begin[j], p.ny, p.nx, p.nchain);
+    zupdate_body<KW, GRP_R, SEP>(p, q.bx, q.by, q.img, q.nblk);
 }
 
 // ---------------------------------------------------------------------------
@@ -911,8 +1044,7 @@ std::vector<WTap> wide_taps(const float* h, int kh, int kw, bool adjoint) {
 
 // ------------------------------------------------------------ dispatch
 
-using BlurFn = void (*)(const float*, const float*, const float*, int, int, int, float, int,
-                        float*, float, int64_t);
+using BlurFn = void (*)(BlurArgs);
 using UpdFn = void (*)(UpdateParams);
 using ZFn = void (*)(ZParams);
 
@@ -946,6 +1078,19 @@ static UpdFn upd_fn_r(int R, bool sep) {
 static BlurFn blur_fn(int kw, int R, bool sep) { PNP_KW_CASES(blur_fn_r) }
 static UpdFn upd_fn(int kw, int R, bool sep) { PNP_KW_CASES(upd_fn_r) }
 static ZFn z_fn(int kw, int R, bool sep) { PNP_KW_CASES(z_fn_r) }
+
+using BlurJFn = void (*)(StencilTable<BlurArgs>);
+using UpdJFn = void (*)(StencilTable<UpdateParams>);
+using ZJFn = void (*)(StencilTable<ZParams>);
+template <int KW>
+static BlurJFn blurj_fn_r(int, bool sep) { return sep ? k_blur_jobs<KW, true> : k_blur_jobs<KW, false>; }
+template <int KW>
+static UpdJFn updj_fn_r(int, bool sep) { return sep ? k_update_jobs<KW, true> : k_update_jobs<KW, false>; }
+template <int KW>
+static ZJFn zj_fn_r(int, bool sep) { return sep ? k_zupdate_jobs<KW, true> : k_zupdate_jobs<KW, false>; }
+static BlurJFn blurj_fn(int kw, bool sep) { const int R = 0; PNP_KW_CASES(blurj_fn_r) }
+static UpdJFn updj_fn(int kw, bool sep) { const int R = 0; PNP_KW_CASES(updj_fn_r) }
+static ZJFn zj_fn(int kw, bool sep) { const int R = 0; PNP_KW_CASES(zj_fn_r) }
 #undef PNP_KW_CASES
 
 // Tiles whose shared memory exceeds the 48 KB default need the opt-in, once
@@ -983,8 +1128,8 @@ static cudaError_t blur_raw(const float* x, const float* y, const float* h, cons
     cudaError_t e = allow_smem(fn, smem);
     if (e != cudaSuccess) return e;
     dim3 grid(ceil_div(nx, ST_TX), ceil_div(ny, rows), nimg);
-    return launch_pdl(fn, grid, dim3(16, ts.BY), smem, s, x, y, sep ? hsep : h, kh, ny, nx, scale,
-                      adjoint ? 1 : 0, out, a, y_img_stride);
+    BlurArgs A{x, y, sep ? hsep : h, kh, ny, nx, nimg, scale, adjoint ? 1 : 0, out, a, y_img_stride};
+    return launch_pdl(fn, grid, dim3(16, ts.BY), smem, s, A);
 }
 
 static cudaError_t zupdate_raw(const ZParams& p, int tile, cudaStream_t s) {
@@ -1075,6 +1220,72 @@ cudaError_t launch_update_mask(const UpdateParams& p, cudaStream_t s) {
 cudaError_t launch_zupdate(const ZParams& p, cudaStream_t s) {
     timer_begin(T_ZUPDATE, s);
     cudaError_t e = zupdate_raw(p, resolve_tile(p.tile), s);
+    timer_end(T_ZUPDATE, s);
+    return e;
+}
+
+// Grouped launch of jobs sharing kernel width kw and form (sep); chunks of
+// STENCIL_TABLE_MAXJ jobs per launch. tiles(a) = a job's tile count, kh(a) its
+// kernel height (the shared memory is sized for the tallest).
+template <typename A, typename Fn, typename Tiles, typename Kh>
+static cudaError_t launch_group(Fn fn, const A* jobs, int n, int kw, bool sep, cudaStream_t s,
+                                Tiles tiles, Kh kh_of) {
+    if (!fn) return cudaErrorInvalidValue;
+    for (int c0 = 0; c0 < n; c0 += STENCIL_TABLE_MAXJ) {
+        StencilTable<A> T;
+        memset(&T, 0, sizeof(T));
+        uint64_t total = 0;
+        int khmax = 1;
+        for (int k = c0; k < std::min(n, c0 + STENCIL_TABLE_MAXJ); ++k) {
+            T.a[T.n] = jobs[k];
+            T.tile_begin[T.n] = (uint32_t)total;
+            total += tiles(jobs[k]);
+            khmax = std::max(khmax, kh_of(jobs[k]));
+            ++T.n;
+        }
+        if (total == 0) continue;
+        if (total >= (1ull << 31) || khmax > ST_MAXK) return cudaErrorInvalidValue;
+        const size_t smem = tile_smem(kw, khmax, GRP_R * GRP_BY, sep);
+        cudaError_t e = allow_smem(fn, smem);
+        if (e != cudaSuccess) return e;
+        e = launch_pdl(fn, dim3((unsigned)total), dim3(16, GRP_BY), smem, s, T);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static uint64_t group_tiles(int ny, int nx, int nimg) {
+    return (uint64_t)ceil_div(nx, ST_TX) * ceil_div(ny, GRP_R * GRP_BY) * (uint64_t)nimg;
+}
+
+cudaError_t launch_blur_group(const BlurArgs* jobs, int n, int kw, bool sep, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    timer_begin(T_BLUR, s);
+    cudaError_t e = launch_group(blurj_fn(kw, sep), jobs, n, kw, sep, s,
+                                 [](const BlurArgs& a) { return group_tiles(a.ny, a.nx, a.nimg); },
+                                 [](const BlurArgs& a) { return a.kh; });
+    timer_end(T_BLUR, s);
+    return e;
+}
+
+cudaError_t launch_update_group(const UpdateParams* jobs, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const bool sep = jobs[0].hsep != nullptr;
+    timer_begin(T_UPDATE, s);
+    cudaError_t e = launch_group(updj_fn(jobs[0].kw, sep), jobs, n, jobs[0].kw, sep, s,
+                                 [](const UpdateParams& p) { return group_tiles(p.ny, p.nx, p.nchain); },
+                                 [](const UpdateParams& p) { return p.kh; });
+    timer_end(T_UPDATE, s);
+    return e;
+}
+
+cudaError_t launch_zupdate_group(const ZParams* jobs, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const bool sep = jobs[0].hsep != nullptr;
+    timer_begin(T_ZUPDATE, s);
+    cudaError_t e = launch_group(zj_fn(jobs[0].kw, sep), jobs, n, jobs[0].kw, sep, s,
+                                 [](const ZParams& p) { return group_tiles(p.ny, p.nx, p.nchain); },
+                                 [](const ZParams& p) { return p.kh; });
     timer_end(T_ZUPDATE, s);
     return e;
 }

@@ -171,6 +171,19 @@ cudaError_t launch_blur(const float* x, const float* y, const float* h, int kh, 
                         const WTap* wt = nullptr, int nwt = 0);
 cudaError_t launch_blur_adjoint(const float* r, const float* h, int kh, int kw, int ny, int nx,
                                 int nimg, float scale, float* g, cudaStream_t s, int tile = -1);
+// Arguments of one r = (a (h * x) - y) scale stencil launch (or of its
+// adjoint), one entry of a grouped launch.
+struct BlurArgs {
+    const float* x;
+    const float* y;
+    const float* h;        // 2-D taps, or the separable taps of a rank-one h
+    int kh, ny, nx, nimg;
+    float scale;
+    int adjoint;
+    float* out;
+    float a;
+    int64_t y_img_stride;
+};
 int stencil_tile_count();
 bool set_forced_stencil_tile(int tile);   // -1 = use each launch's own choice
 
@@ -232,6 +245,15 @@ struct ZParams {
     int tile;
 };
 cudaError_t launch_zupdate(const ZParams& p, cudaStream_t s);
+// Grouped launches for batches: the jobs of one call share the stencil width
+// (kw, a template parameter of the kernels) and form (separable or 2-D taps);
+// each job keeps its own sizes, buffers and step counter, and its outputs are
+// the same sums as in its own launch. At most STENCIL_TABLE_MAXJ jobs travel
+// by value per launch; more jobs take several launches.
+constexpr int STENCIL_TABLE_MAXJ = 48;
+cudaError_t launch_blur_group(const BlurArgs* jobs, int n, int kw, bool sep, cudaStream_t s);
+cudaError_t launch_update_group(const UpdateParams* jobs, int n, cudaStream_t s);
+cudaError_t launch_zupdate_group(const ZParams* jobs, int n, cudaStream_t s);
 // Inpainting x-update: p.r is the observation with NaN at missing pixels
 // (shared by the chains); no stencil, p.h unused.
 cudaError_t launch_update_mask(const UpdateParams& p, cudaStream_t s);
@@ -414,6 +436,10 @@ constexpr int kGraphBatch = 8;   // iterations per replayed graph
 // fused update (+ step counter advance).
 pnp_status problem_pre(pnp_problem* p, cudaStream_t s);
 pnp_status problem_post(pnp_problem* p, cudaStream_t s);
+// Arguments of the problem's update (and Poisson z-update) launches for the
+// iteration that starts from its current state buffer.
+pnp_status problem_update_params(const pnp_problem* p, UpdateParams& u);
+ZParams problem_z_params(const pnp_problem* p);
 // Advances the host-side state buffer after an iteration has been enqueued
 // (problem_post does it; graph replays do it for the iterations they hold).
 inline void problem_flip(pnp_problem* p) {

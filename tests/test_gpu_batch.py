@@ -62,6 +62,40 @@ def test_batch_jobs_equal_alone(P, den, prec):
         np.testing.assert_array_equal(va, vb)
 
 
+def test_batch_launches_are_grouped(P, den):
+    """One batch iteration launches one first layer, the shared conv layers and
+    one residual / update launch per (stencil width, form), not one per job."""
+    jobs = mixed_jobs(6) + mixed_jobs(6, seed=12)
+    widths = {np.asarray(j["h"]).shape for j in jobs}
+    b = P.Batch(jobs, den, precision="bf16")
+    b.step(2)
+    P.pnp_kernel_timer(True)            # eager launches, counted
+    n0 = P.pnp_launch_count()
+    b.step(1)
+    b.sync()
+    n = P.pnp_launch_count() - n0
+    P.pnp_kernel_timer(False)
+    K = 8
+    assert n <= 2 * len(widths) + K, (n, len(widths))
+    assert n < 3 * len(jobs) + K - 1
+
+
+def test_batch_job_stepped_alone_between_batch_steps(P, den):
+    """A batch job stepped through its own handle between batch steps keeps the
+    same chain as the job run alone for the same total number of steps."""
+    jobs = mixed_jobs(3)
+    b = P.Batch(jobs, den, precision="fp32")
+    b.step(3)
+    b.job(1).step(1)
+    b.step(2)
+    b.sync()
+    jb = jobs[1]
+    alone = P.Problem(jb["y"], jb["h"], jb["sigma"], den, seed=jb["seed"], burn_in=3,
+                      precision="fp32")
+    alone.step(6)
+    np.testing.assert_array_equal(b.job(1).state()[0], alone.state()[0])
+
+
 def test_batch_one_step_parity_with_oracle(P, den, orc):
     """A batched job's one-step x+ matches the FP64 oracle (FP32 path)."""
     jobs = mixed_jobs(3)

@@ -117,6 +117,7 @@ def test_denoise_bf16_close_to_oracle(P, orc, ny, nx):
     d = den.denoise(dev(x[None]), precision="bf16").cpu().numpy()[0]
     G = x - orc.denoise(x, net)
     err = np.abs((x - d) - G)
+    print("bf16 denoiser %dx%d: max|dG| / max|G| = %.3e" % (ny, nx, err.max() / np.abs(G).max()))
     assert err.max() <= 3e-2 * np.abs(G).max() + 1e-4, (err.max(), np.abs(G).max())
 
 
@@ -129,4 +130,5 @@ def test_denoise_bf16_matches_fp32_path(P):
     d32 = den.denoise(x, precision="fp32")
     d16 = den.denoise(x, precision="bf16")
     G = (x - d32).abs().max().item()
+    print("bf16 vs fp32 denoiser 300x333: max|dG| / max|G| = %.3e" % ((d16 - d32).abs().max().item() / G))
     assert (d16 - d32).abs().max().item() <= 3e-2 * G + 1e-4
