@@ -17,9 +17,10 @@
 // tile be picked by timing (stencil_autotune) without changing any result.
 //
 // Rank-one kernels h = u v^T (Gaussian, uniform; detected on the host) take a
-// separable path: a horizontal pass over the window rows into a shared-memory
-// strip T = window * v, then a vertical pass out = sum_a u[a] T[i + a] -
-// kh + kw instead of kh kw FMAs per output, again in a fixed order.
+// separable path: a vertical pass over every window column into a
+// shared-memory strip V = u * window, then a horizontal pass
+// out = sum_b v[b] V[., j + b] - kh + kw instead of kh kw FMAs per output,
+// again in a fixed order.
 #include <atomic>
 #include <cstring>
 #include <map>
@@ -210,17 +211,93 @@ __device__ __forceinline__ void correlate(const float* win, const float* hs, int
     }
 }
 
-// Separable pass 1: T[r][c] = sum_b vs[b] win[r][c + b] for every window row r
-// and the 64 tile columns (4 per work item).
-template <int KW>
-__device__ __forceinline__ void sep_rows(const float* win, const float* vs, int wy, float* T) {
+// Separable kernels run the vertical pass first, over every window column:
+//   V[o][c] = sum_a us[a] win[o + a][c]          (a ascending, from 0)
+// for the tile's `rows` output rows, then the horizontal pass over V:
+//   out[o][j] = sum_b vs[b] V[o][j + SHIFT + b]  (b ascending, from 0).
+// The vertical pass does rows x window-width x kh FMAs, so its cost per
+// output does not grow with the window's (kh - 1)-row halo, and its FMAs pair
+// up on the two halves of each 128-bit shared-memory load (packed FP32 FMA,
+// each component rounded exactly as fmaf). Every output is the same
+// fixed-order sum whatever the tile.
+template <int KW, int R>
+__device__ __forceinline__ void sep_vert(const float* win, const float* us, int kh, int rows,
+                                         float* V) {
     using G = Geom<KW>;
+    constexpr int NC4 = G::WXA / 4;
     const int nt = blockDim.x * blockDim.y;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    for (int it = tid; it < wy * (ST_TX / 4); it += nt) {
-        const int r = it / (ST_TX / 4), c4 = it - r * (ST_TX / 4);
+    const int nrb = rows / R;
+    if (kh == KW) {
+        float2 u2[KW];
+#pragma unroll
+        for (int a = 0; a < KW; ++a) u2[a] = make_float2(us[a], us[a]);
+        for (int it = tid; it < nrb * NC4; it += nt) {
+            const int rb = it / NC4, c4 = it - rb * NC4;
+            const float* src = win + rb * R * G::WP + 4 * c4;
+            float2 lo[R], hi[R];
+#pragma unroll
+            for (int o = 0; o < R; ++o) lo[o] = hi[o] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < R + KW - 1; ++u) {
+                const float4 v = *reinterpret_cast<const float4*>(src + u * G::WP);
+                const float2 vl = make_float2(v.x, v.y), vh = make_float2(v.z, v.w);
+#pragma unroll
+                for (int o = 0; o < R; ++o) {
+                    const int a = u - o;
+                    if (a < 0 || a >= KW) continue;
+                    lo[o] = __ffma2_rn(u2[a], vl, lo[o]);
+                    hi[o] = __ffma2_rn(u2[a], vh, hi[o]);
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < R; ++o)
+                *reinterpret_cast<float4*>(V + (rb * R + o) * G::WP + 4 * c4) =
+                    make_float4(lo[o].x, lo[o].y, hi[o].x, hi[o].y);
+        }
+    } else {
+        for (int it = tid; it < nrb * NC4; it += nt) {
+            const int rb = it / NC4, c4 = it - rb * NC4;
+            const float* src = win + rb * R * G::WP + 4 * c4;
+            float acc[R][4];
+#pragma unroll
+            for (int o = 0; o < R; ++o)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[o][q] = 0.f;
+#pragma unroll 1
+            for (int u = 0; u < R + kh - 1; ++u) {
+                const float4 v = *reinterpret_cast<const float4*>(src + u * G::WP);
+#pragma unroll
+                for (int o = 0; o < R; ++o) {
+                    const int a = u - o;
+                    if (a < 0 || a >= kh) continue;
+                    const float ua = us[a];
+                    acc[o][0] = fmaf(ua, v.x, acc[o][0]);
+                    acc[o][1] = fmaf(ua, v.y, acc[o][1]);
+                    acc[o][2] = fmaf(ua, v.z, acc[o][2]);
+                    acc[o][3] = fmaf(ua, v.w, acc[o][3]);
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < R; ++o)
+                *reinterpret_cast<float4*>(V + (rb * R + o) * G::WP + 4 * c4) =
+                    make_float4(acc[o][0], acc[o][1], acc[o][2], acc[o][3]);
+        }
+    }
+}
+
+// Horizontal pass: acc[o][q] = sum_b vs[b] V[ty R + o][4 tx + SHIFT + q + b].
+template <int KW, int R>
+__device__ __forceinline__ void sep_horz(const float* V, const float* vs, int ty, int tx,
+                                         float acc[R][4]) {
+    using G = Geom<KW>;
+    float hr[KW];
+#pragma unroll
+    for (int b = 0; b < KW; ++b) hr[b] = vs[b];
+#pragma unroll
+    for (int o = 0; o < R; ++o) {
         float w[4 * G::NW4];
-        const float4* src = reinterpret_cast<const float4*>(win + r * G::WP + 4 * c4);
+        const float4* src = reinterpret_cast<const float4*>(V + (ty * R + o) * G::WP + 4 * tx);
 #pragma unroll
         for (int k = 0; k < G::NW4; ++k) {
             const float4 v = src[k];
@@ -229,45 +306,12 @@ __device__ __forceinline__ void sep_rows(const float* win, const float* vs, int 
             w[4 * k + 2] = v.z;
             w[4 * k + 3] = v.w;
         }
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        const float4* vp = reinterpret_cast<const float4*>(vs);
-#pragma unroll
-        for (int b4 = 0; b4 < G::KWP / 4; ++b4) {
-            const float4 hv = vp[b4];
-            const float hh[4] = {hv.x, hv.y, hv.z, hv.w};
-#pragma unroll
-            for (int bb = 0; bb < 4; ++bb) {
-                const int b = 4 * b4 + bb;
-                if (b < KW) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[q] = fmaf(hh[bb], w[G::SHIFT + q + b], acc[q]);
-                }
-            }
-        }
-        *reinterpret_cast<float4*>(T + r * ST_TX + 4 * c4) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    }
-}
-
-// Separable pass 2: acc[o][q] = sum_a us[a] T[ty R + o + a][4 tx + q]
-template <int R>
-__device__ __forceinline__ void sep_cols(const float* T, const float* us, int kh, int ty, int tx,
-                                         float acc[R][4]) {
-#pragma unroll
-    for (int o = 0; o < R; ++o)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[o][q] = 0.f;
-#pragma unroll 1
-    for (int u = 0; u < R + kh - 1; ++u) {
-        const float4 tv = *reinterpret_cast<const float4*>(T + (ty * R + u) * ST_TX + 4 * tx);
 #pragma unroll
-        for (int o = 0; o < R; ++o) {
-            const int a = u - o;
-            if (a < 0 || a >= kh) continue;
-            const float hu = us[a];
-            acc[o][0] = fmaf(hu, tv.x, acc[o][0]);
-            acc[o][1] = fmaf(hu, tv.y, acc[o][1]);
-            acc[o][2] = fmaf(hu, tv.z, acc[o][2]);
-            acc[o][3] = fmaf(hu, tv.w, acc[o][3]);
+        for (int b = 0; b < KW; ++b) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[o][q] = fmaf(hr[b], w[G::SHIFT + q + b], acc[o][q]);
         }
     }
 }
@@ -285,7 +329,7 @@ static size_t tile_smem(int kw, int kh, int rows, bool sep) {
     const int wp = window_pitch(kw), kwp = (kw + 3) & ~3;
     const size_t wy = (size_t)rows + kh - 1;
     if (!sep) return sizeof(float) * (wy * wp + (size_t)kh * kwp);
-    return sizeof(float) * (wy * wp + wy * ST_TX + kwp + ((kh + 3) & ~3));
+    return sizeof(float) * (wy * wp + (size_t)rows * wp + kwp + ((kh + 3) & ~3));
 }
 
 // The R x 4 outputs of thread (threadIdx.x, threadIdx.y) of the tile at
@@ -300,15 +344,15 @@ __device__ __forceinline__ void stencil_tile(const float* img, int ny, int nx, i
     float* win = sm;
     fill_window<KW>(img, ny, nx, i0, j0, kh, rows, win);
     if constexpr (SEP) {
-        float* T = win + wy * G::WP;
-        float* vs = T + wy * ST_TX;
+        float* V = win + wy * G::WP;      // rows x WP
+        float* vs = V + rows * G::WP;
         float* us = vs + G::KWP;
         load_taps_sep<KW>(h, kh, flip, vs, us);
         cp_async_wait_all();
         __syncthreads();
-        sep_rows<KW>(win, vs, wy, T);
+        sep_vert<KW, R>(win, us, kh, rows, V);
         __syncthreads();
-        if (active) sep_cols<R>(T, us, kh, threadIdx.y, threadIdx.x, acc);
+        if (active) sep_horz<KW, R>(V, vs, threadIdx.y, threadIdx.x, acc);
     } else {
         float* hs = win + wy * G::WP;
         load_taps2d<KW>(h, kh, flip, hs);
@@ -830,36 +874,52 @@ __device__ __forceinline__ void wide_tile(const float* __restrict__ img, int ny,
                                           float* win, float acc[WD_R][4]) {
     const int ay = kh >> 1, ax = kw >> 1;
     const int wy = WD_TR + kh + 2, wp = WD_TW + kw - 1;   // + 3 rows read by the last group
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int it = tid; it < wy * wp; it += 32 * WD_BY) {
-        const int r = it / wp, c = it - r * wp;
+    // window fill: each row of threads copies whole window rows (circular
+    // wrap of the row once per row; columns wrap only on border tiles), all
+    // copies asynchronous
+    const int c0 = j0 - ax;
+    const bool col_interior = c0 >= 0 && c0 + wp <= nx;
+    for (int r = threadIdx.y; r < wy; r += WD_BY) {
         int gi = (i0 - ay + r) % ny;
         if (gi < 0) gi += ny;
-        int gj = (j0 - ax + c) % nx;
-        if (gj < 0) gj += nx;
-        win[it] = __ldg(img + (int64_t)gi * nx + gj);
+        const float* src = img + (int64_t)gi * nx;
+        float* dst = win + r * wp;
+        if (col_interior) {
+            for (int c = threadIdx.x; c < wp; c += 32) cp_async4(dst + c, src + c0 + c);
+        } else {
+            for (int c = threadIdx.x; c < wp; c += 32) {
+                int gj = (c0 + c) % nx;
+                if (gj < 0) gj += nx;
+                cp_async4(dst + c, src + gj);
+            }
+        }
     }
+    cp_async_wait_all();
     __syncthreads();
+    // accumulators of the column pairs (q, q + 1) = (2 p, 2 p + 1): packed FP32
+    // FMAs, each component rounded exactly as fmaf, in the same order
+    float2 acc2[WD_R][2];
 #pragma unroll
-    for (int o = 0; o < WD_R; ++o)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[o][q] = 0.f;
+    for (int o = 0; o < WD_R; ++o) acc2[o][0] = acc2[o][1] = make_float2(0.f, 0.f);
     const float* base = win + threadIdx.y * WD_R * wp + threadIdx.x;
     auto group = [&](int off, float w0, float w1, float w2, float w3) {
         const float* b = base + off;
+        const float2 t0 = make_float2(w0, w0), t1 = make_float2(w1, w1);
+        const float2 t2 = make_float2(w2, w2), t3 = make_float2(w3, w3);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float v[WD_R + 3];
+        for (int pq = 0; pq < 2; ++pq) {
+            float2 v[WD_R + 3];
 #pragma unroll
-            for (int o = 0; o < WD_R + 3; ++o) v[o] = b[o * wp + 32 * q];
+            for (int o = 0; o < WD_R + 3; ++o)
+                v[o] = make_float2(b[o * wp + 64 * pq], b[o * wp + 64 * pq + 32]);
 #pragma unroll
             for (int o = 0; o < WD_R; ++o) {
-                float s = acc[o][q];
-                s = fmaf(w0, v[o], s);
-                s = fmaf(w1, v[o + 1], s);
-                s = fmaf(w2, v[o + 2], s);
-                s = fmaf(w3, v[o + 3], s);
-                acc[o][q] = s;
+                float2 sacc = acc2[o][pq];
+                sacc = __ffma2_rn(t0, v[o], sacc);
+                sacc = __ffma2_rn(t1, v[o + 1], sacc);
+                sacc = __ffma2_rn(t2, v[o + 2], sacc);
+                sacc = __ffma2_rn(t3, v[o + 3], sacc);
+                acc2[o][pq] = sacc;
             }
         }
     };
@@ -884,6 +944,13 @@ __device__ __forceinline__ void wide_tile(const float* __restrict__ img, int ny,
                 if (w[0] == 0.f && w[1] == 0.f && w[2] == 0.f && w[3] == 0.f) continue;
                 group(r0 * wp + wc, w[0], w[1], w[2], w[3]);
             }
+    }
+#pragma unroll
+    for (int o = 0; o < WD_R; ++o) {
+        acc[o][0] = acc2[o][0].x;
+        acc[o][1] = acc2[o][0].y;
+        acc[o][2] = acc2[o][1].x;
+        acc[o][3] = acc2[o][1].y;
     }
 }
 

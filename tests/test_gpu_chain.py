@@ -215,7 +215,7 @@ def test_bf16_mmse_psnr_matches_fp32(P):
 def test_bf16_one_step_against_oracle(P, orc, blocks, halo):
     """One BF16 step from an injected state against the FP64 oracle, in the
     direct and the block + halo layouts: the difference is the prior term's
-    BF16 error, c_prior |G_bf16 - G|, bounded like the denoiser tests (3 % of
+    BF16 error, c_prior |G_bf16 - G|, bounded like the denoiser tests (1 % of
     max |G|), on a ragged 72 x 136 image."""
     prob = synth.make_problem(72, 136, synth.uniform_kernel(5), 25.0, 909)
     dw = synth.workload_denoiser(2)
@@ -232,5 +232,5 @@ def test_bf16_one_step_against_oracle(P, orc, blocks, halo):
     ref = orc.langevin_step(op, x0, 3)
     G = x0 - orc.denoise(x0, net)
     c_prior = prm["alpha"] * prm["gamma"] / prm["eps"] ** 2
-    bound = c_prior * 3e-2 * np.abs(G).max() + 1e-5 * np.abs(ref).max()
+    bound = c_prior * 1e-2 * np.abs(G).max() + 1e-5 * np.abs(ref).max()
     assert np.abs(x1[0] - ref).max() <= bound, (np.abs(x1[0] - ref).max(), bound)

@@ -12,6 +12,14 @@ import pytest
 
 import synth
 
+# BF16 denoiser error bound, relative to max|G| (G = x - D(x)): seven layers
+# take BF16 operands, each rounding its input activations and weights to 8
+# significant bits (unit roundoff u = 2^-9), with FP32 accumulation. The 14
+# roundings are independent and the 0.9-Lipschitz layers do not amplify them,
+# so they add like a random walk: sqrt(14) u = 7.3e-3 of the activation
+# scale (the worst case, all aligned, is 14 u = 2.7e-2). Measured: 3-6e-3.
+BF16_G_TOL = 1e-2
+
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
@@ -118,7 +126,7 @@ def test_denoise_bf16_close_to_oracle(P, orc, ny, nx):
     G = x - orc.denoise(x, net)
     err = np.abs((x - d) - G)
     print("bf16 denoiser %dx%d: max|dG| / max|G| = %.3e" % (ny, nx, err.max() / np.abs(G).max()))
-    assert err.max() <= 3e-2 * np.abs(G).max() + 1e-4, (err.max(), np.abs(G).max())
+    assert err.max() <= BF16_G_TOL * np.abs(G).max(), (err.max(), np.abs(G).max())
 
 
 def test_denoise_bf16_matches_fp32_path(P):
@@ -131,4 +139,4 @@ def test_denoise_bf16_matches_fp32_path(P):
     d16 = den.denoise(x, precision="bf16")
     G = (x - d32).abs().max().item()
     print("bf16 vs fp32 denoiser 300x333: max|dG| / max|G| = %.3e" % ((d16 - d32).abs().max().item() / G))
-    assert (d16 - d32).abs().max().item() <= 3e-2 * G + 1e-4
+    assert (d16 - d32).abs().max().item() <= BF16_G_TOL * G

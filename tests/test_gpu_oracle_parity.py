@@ -24,11 +24,11 @@ torch = pytest.importorskip("torch")
 
 # BF16 denoiser error bound, relative to max|G| (G = x - D(x)): seven layers
 # take BF16 operands (activations and weights rounded to 8 significant bits,
-# unit roundoff u = 2^-9); with 0.9-Lipschitz layers an input perturbation is
-# not amplified, so the worst case is about 2u per rounded layer input and
-# weight, 7 x 2 x 2^-9 = 2.7e-2, with FP32 accumulation adding nothing at this
-# scale.
-BF16_G_TOL = 3e-2
+# unit roundoff u = 2^-9) with FP32 accumulation; the 14 roundings are
+# independent and the 0.9-Lipschitz layers do not amplify them, so they add
+# like a random walk, sqrt(14) u = 7.3e-3 (worst case 14 u = 2.7e-2; measured
+# 3-6e-3 on the denoiser tests).
+BF16_G_TOL = 1e-2
 
 
 @pytest.fixture(scope="module")
