@@ -358,20 +358,33 @@ def _source_sha(kernel):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:12]
 
 
-def ncu_traffic(kernel, workload, precision):
-    """(DRAM bytes per launch, note) of `kernel` from the committed ncu summary:
-    bytes only when the line was captured on the current kernel source."""
+def ncu_traffic(kernel, workload, precision, npix=None):
+    """(DRAM bytes per launch, note) of `kernel` from the committed ncu summary,
+    only when the line was captured on the current kernel source. Without a
+    line for this workload, a line of the same kernel and precision that
+    records the pixels of its captured launch is scaled to `npix` pixels (the
+    kernel's traffic grows in proportion to the pixels it processes)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None, "no ncu capture committed"
-    cur = _source_sha(kernel)
+    cur = _source_sha(kernel.split(" ")[0])
+    scaled = None
     for line in open(path):
         f = line.split()
-        if len(f) >= 5 and not f[0].startswith("#") and f[:3] == [kernel, workload, precision]:
-            if len(f) >= 6 and f[5] == cur:
+        if len(f) < 5 or f[0].startswith("#") or f[0] != kernel.split(" ")[0] or f[2] != precision:
+            continue
+        fresh = len(f) >= 6 and f[5] == cur
+        if f[1] == workload:
+            if fresh:
                 return int(f[3]) + int(f[4]), f"profiles/ncu_traffic.txt, ncu capture of source {cur}"
             return None, "kernel source changed since the committed ncu capture"
-    return None, "no ncu capture of this kernel and workload committed"
+        if fresh and len(f) >= 7 and npix and scaled is None:
+            b = (int(f[3]) + int(f[4])) * npix / int(f[6])
+            scaled = (int(round(b)), f"profiles/ncu_traffic.txt: the {f[1]} capture ({int(f[6])} "
+                                     f"pixels per launch, source {cur}) scaled to {npix} pixels")
+    if scaled:
+        return scaled
+    return None, "no ncu capture of this kernel on the current source committed"
 
 
 def _tc_roofline(peaks, prec, flop, avg_ms, kernel, workload):
@@ -379,7 +392,7 @@ def _tc_roofline(peaks, prec, flop, avg_ms, kernel, workload):
     events in a short eager pass: the burst peak (FP8: x nominal ratio 2)."""
     achieved = flop / (avg_ms * 1e-3) / 1e12
     pk = peaks["bf16"] * (2 if prec == "fp8" else 1)
-    traffic, tnote = ncu_traffic(kernel, workload, prec)
+    traffic, tnote = ncu_traffic(kernel, workload, prec, npix=int(round(flop / 73728.0)))
     return dict(bound="tensor", achieved=round(achieved, 2), peak=pk, unit="TFLOP/s",
                 frac=round(achieved / pk, 4), traffic=traffic, traffic_source=tnote, kernel=kernel,
                 flop_per_launch=flop, avg_launch_ms=round(avg_ms, 5),
@@ -796,7 +809,9 @@ def measure_single(args, P, torch, stream, ws, rank, local, workload, precs, ste
         data="synthetic",
         config=dict(workload=wl, precision=precs[0],
                     l2="working set per step > 126 MB L2 (activation planes)",
-                    graph="one CUDA graph per iteration"),
+                    graph="one CUDA graph per iteration",
+                    stencil_tile=("forced %d" % args.stencil_tile if args.stencil_tile >= 0
+                                  else "autotuned")),
         roofline=roof,
         cpu_baseline=cpu,
         e2e=e2e,
@@ -841,6 +856,8 @@ def main():
     ap.add_argument("--jobs", type=int, default=0, help="serve: number of arrivals (default: --steps)")
     ap.add_argument("--size", type=int, default=0,
                     help="single-job Gaussian workloads: the same posterior on a size x size image")
+    ap.add_argument("--stencil-tile", type=int, default=-1,
+                    help="force stencil tile shape k for every launch (profiling; default: autotuned)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -859,6 +876,8 @@ def main():
         build.build()
     if ws > 1:
         torch.distributed.barrier()
+    if args.stencil_tile >= 0:
+        P.pnp_set_stencil_tile(args.stencil_tile)
     # a dedicated stream: the problems enqueue on it and the events are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)

@@ -43,6 +43,10 @@ struct TileShape {
 };
 constexpr TileShape kTiles[] = {{1, 16}, {2, 8}, {2, 16}, {4, 8}, {1, 8}, {4, 16}};
 constexpr int kNumTiles = (int)(sizeof(kTiles) / sizeof(kTiles[0]));
+// Rows per item of the separable vertical pass, independent of the tile's R:
+// an item reads SEP_VR + kh - 1 window rows for 4 SEP_VR outputs. Every tile
+// height (R * BY, BY a multiple of 8) is a multiple of it.
+constexpr int SEP_VR = 4;
 static std::atomic<int> g_forced_tile{-1};
 
 // Shared-memory window of a tile: its column 0 is image column j0 - AL (AL =
@@ -218,8 +222,12 @@ __device__ __forceinline__ void correlate(const float* win, const float* hs, int
 // The vertical pass does rows x window-width x kh FMAs, so its cost per
 // output does not grow with the window's (kh - 1)-row halo, and its FMAs pair
 // up on the two halves of each 128-bit shared-memory load (packed FP32 FMA,
-// each component rounded exactly as fmaf). Every output is the same
-// fixed-order sum whatever the tile.
+// each component rounded exactly as fmaf). V is stored with row pairs
+// interleaved, element (o, c) at ((o / 2) WP + c) 2 + o % 2, so that the
+// horizontal pass can advance two output rows per packed FMA. Every output is
+// the same fixed-order sum whatever the tile.
+__device__ __forceinline__ int vidx(int o, int c, int wp) { return ((o >> 1) * wp + c) * 2 + (o & 1); }
+
 template <int KW, int R>
 __device__ __forceinline__ void sep_vert(const float* win, const float* us, int kh, int rows,
                                          float* V) {
@@ -228,6 +236,19 @@ __device__ __forceinline__ void sep_vert(const float* win, const float* us, int 
     const int nt = blockDim.x * blockDim.y;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nrb = rows / R;
+    // the four columns of rows o, o + 1 of an item into V
+    auto put2 = [&](int o, int c4, float a0, float a1, float a2, float a3, float b0, float b1,
+                    float b2, float b3) {
+        float* d = V + vidx(o, 4 * c4, G::WP);
+        *reinterpret_cast<float4*>(d) = make_float4(a0, b0, a1, b1);
+        *reinterpret_cast<float4*>(d + 4) = make_float4(a2, b2, a3, b3);
+    };
+    auto put1 = [&](int o, int c4, float a0, float a1, float a2, float a3) {
+        V[vidx(o, 4 * c4, G::WP)] = a0;
+        V[vidx(o, 4 * c4 + 1, G::WP)] = a1;
+        V[vidx(o, 4 * c4 + 2, G::WP)] = a2;
+        V[vidx(o, 4 * c4 + 3, G::WP)] = a3;
+    };
     if (kh == KW) {
         float2 u2[KW];
 #pragma unroll
@@ -250,10 +271,15 @@ __device__ __forceinline__ void sep_vert(const float* win, const float* us, int 
                     hi[o] = __ffma2_rn(u2[a], vh, hi[o]);
                 }
             }
+            if constexpr (R % 2 == 0) {
 #pragma unroll
-            for (int o = 0; o < R; ++o)
-                *reinterpret_cast<float4*>(V + (rb * R + o) * G::WP + 4 * c4) =
-                    make_float4(lo[o].x, lo[o].y, hi[o].x, hi[o].y);
+                for (int o = 0; o < R; o += 2)
+                    put2(rb * R + o, c4, lo[o].x, lo[o].y, hi[o].x, hi[o].y, lo[o + 1].x,
+                         lo[o + 1].y, hi[o + 1].x, hi[o + 1].y);
+            } else {
+#pragma unroll
+                for (int o = 0; o < R; ++o) put1(rb * R + o, c4, lo[o].x, lo[o].y, hi[o].x, hi[o].y);
+            }
         }
     } else {
         for (int it = tid; it < nrb * NC4; it += nt) {
@@ -278,40 +304,72 @@ __device__ __forceinline__ void sep_vert(const float* win, const float* us, int 
                     acc[o][3] = fmaf(ua, v.w, acc[o][3]);
                 }
             }
+            if constexpr (R % 2 == 0) {
 #pragma unroll
-            for (int o = 0; o < R; ++o)
-                *reinterpret_cast<float4*>(V + (rb * R + o) * G::WP + 4 * c4) =
-                    make_float4(acc[o][0], acc[o][1], acc[o][2], acc[o][3]);
+                for (int o = 0; o < R; o += 2)
+                    put2(rb * R + o, c4, acc[o][0], acc[o][1], acc[o][2], acc[o][3],
+                         acc[o + 1][0], acc[o + 1][1], acc[o + 1][2], acc[o + 1][3]);
+            } else {
+#pragma unroll
+                for (int o = 0; o < R; ++o)
+                    put1(rb * R + o, c4, acc[o][0], acc[o][1], acc[o][2], acc[o][3]);
+            }
         }
     }
 }
 
-// Horizontal pass: acc[o][q] = sum_b vs[b] V[ty R + o][4 tx + SHIFT + q + b].
+// Horizontal pass: acc[o][q] = sum_b vs[b] V[ty R + o][4 tx + SHIFT + q + b];
+// with an even R, rows (o, o + 1) advance together in packed FMAs on the
+// interleaved pairs (V[o][c], V[o + 1][c]).
 template <int KW, int R>
 __device__ __forceinline__ void sep_horz(const float* V, const float* vs, int ty, int tx,
                                          float acc[R][4]) {
     using G = Geom<KW>;
-    float hr[KW];
+    if constexpr (R % 2 == 0) {
+        float2 h2[KW];
 #pragma unroll
-    for (int b = 0; b < KW; ++b) hr[b] = vs[b];
+        for (int b = 0; b < KW; ++b) h2[b] = make_float2(vs[b], vs[b]);
 #pragma unroll
-    for (int o = 0; o < R; ++o) {
-        float w[4 * G::NW4];
-        const float4* src = reinterpret_cast<const float4*>(V + (ty * R + o) * G::WP + 4 * tx);
+        for (int o = 0; o < R; o += 2) {
+            float2 p[4 * G::NW4];
+            const float4* src = reinterpret_cast<const float4*>(V + vidx(ty * R + o, 4 * tx, G::WP));
 #pragma unroll
-        for (int k = 0; k < G::NW4; ++k) {
-            const float4 v = src[k];
-            w[4 * k] = v.x;
-            w[4 * k + 1] = v.y;
-            w[4 * k + 2] = v.z;
-            w[4 * k + 3] = v.w;
+            for (int k = 0; k < 2 * G::NW4; ++k) {
+                const float4 v = src[k];
+                p[2 * k] = make_float2(v.x, v.y);
+                p[2 * k + 1] = make_float2(v.z, v.w);
+            }
+            float2 a2[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a2[q] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int b = 0; b < KW; ++b) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) a2[q] = __ffma2_rn(h2[b], p[G::SHIFT + q + b], a2[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                acc[o][q] = a2[q].x;
+                acc[o + 1][q] = a2[q].y;
+            }
         }
+    } else {
+        float hr[KW];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[o][q] = 0.f;
+        for (int b = 0; b < KW; ++b) hr[b] = vs[b];
 #pragma unroll
-        for (int b = 0; b < KW; ++b) {
+        for (int o = 0; o < R; ++o) {
+            const int row = ty * R + o;
+            float w[4 * G::NW4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[o][q] = fmaf(hr[b], w[G::SHIFT + q + b], acc[o][q]);
+            for (int c = 0; c < 4 * G::NW4; ++c) w[c] = V[vidx(row, 4 * tx + c, G::WP)];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[o][q] = 0.f;
+#pragma unroll
+            for (int b = 0; b < KW; ++b) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[o][q] = fmaf(hr[b], w[G::SHIFT + q + b], acc[o][q]);
+            }
         }
     }
 }
@@ -350,7 +408,7 @@ __device__ __forceinline__ void stencil_tile(const float* img, int ny, int nx, i
         load_taps_sep<KW>(h, kh, flip, vs, us);
         cp_async_wait_all();
         __syncthreads();
-        sep_vert<KW, R>(win, us, kh, rows, V);
+        sep_vert<KW, SEP_VR>(win, us, kh, rows, V);
         __syncthreads();
         if (active) sep_horz<KW, R>(V, vs, threadIdx.y, threadIdx.x, acc);
     } else {
@@ -535,28 +593,30 @@ __device__ __forceinline__ void update_body(const UpdateParams& p, int bx, int b
             if (i >= ny) break;
             const int64_t n0 = (int64_t)i * nx + j;
             float z[4] = {0.f, 0.f, 0.f, 0.f};
-            if (p.c_noise != 0.f) normals4(p.key0, p.key1, n0, t, (uint32_t)chain, z);
-            if (fused) {
-                // g = (H^T H) x - H^T y
-                if (vec) {
-                    const float4 bv = __ldg(reinterpret_cast<const float4*>(p.qb + n0));
+            if (vec) {
+                // this row's operands (prefetched to L2 above) are loaded before
+                // the noise is drawn, so their latency overlaps the Philox
+                // rounds; mean and m2 are read before x+ is stored
+                const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 bv = fused ? __ldg(reinterpret_cast<const float4*>(p.qb + n0)) : zero4;
+                const float4 dv = dc ? __ldg(reinterpret_cast<const float4*>(dc + n0)) : zero4;
+                const float4 z2v =
+                    p.z2 ? __ldg(reinterpret_cast<const float4*>(p.z2 + chain * plane + n0)) : zero4;
+                float4 mo = zero4, qo = zero4;
+                if (inv_n > 0.f) {
+                    mo = *reinterpret_cast<const float4*>(mc + n0);
+                    qo = *reinterpret_cast<const float4*>(qc + n0);
+                }
+                const float4 xv = fused ? *reinterpret_cast<const float4*>(xwin + o * Geom<KW>::WP)
+                                        : *reinterpret_cast<const float4*>(xc + n0);
+                if (p.c_noise != 0.f) normals4(p.key0, p.key1, n0, t, (uint32_t)chain, z);
+                if (fused) {
+                    // g = (H^T H) x - H^T y
                     g[o][0] -= bv.x;
                     g[o][1] -= bv.y;
                     g[o][2] -= bv.z;
                     g[o][3] -= bv.w;
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (j + q < nx) g[o][q] -= __ldg(p.qb + n0 + q);
                 }
-            }
-            if (vec) {
-                float4 xv = fused ? *reinterpret_cast<const float4*>(xwin + o * Geom<KW>::WP)
-                                  : *reinterpret_cast<const float4*>(xc + n0);
-                float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (dc) dv = __ldg(reinterpret_cast<const float4*>(dc + n0));
-                float4 z2v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (p.z2) z2v = __ldg(reinterpret_cast<const float4*>(p.z2 + chain * plane + n0));
                 float4 v;
                 v.x = update1(p, xv.x, g[o][0], dv.x, z[0], z2v.x);
                 v.y = update1(p, xv.y, g[o][1], dv.y, z[1], z2v.y);
@@ -564,8 +624,6 @@ __device__ __forceinline__ void update_body(const UpdateParams& p, int bx, int b
                 v.w = update1(p, xv.w, g[o][3], dv.w, z[3], z2v.w);
                 *reinterpret_cast<float4*>(xo + n0) = v;
                 if (inv_n > 0.f) {
-                    float4 mo = *reinterpret_cast<const float4*>(mc + n0);
-                    float4 qo = *reinterpret_cast<const float4*>(qc + n0);
                     welford1(v.x, inv_n, mo.x, qo.x);
                     welford1(v.y, inv_n, mo.y, qo.y);
                     welford1(v.z, inv_n, mo.z, qo.z);
@@ -574,10 +632,12 @@ __device__ __forceinline__ void update_body(const UpdateParams& p, int bx, int b
                     *reinterpret_cast<float4*>(qc + n0) = qo;
                 }
             } else {
+                if (p.c_noise != 0.f) normals4(p.key0, p.key1, n0, t, (uint32_t)chain, z);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     if (j + q >= nx) break;
                     const int64_t n = n0 + q;
+                    if (fused) g[o][q] -= __ldg(p.qb + n);   // g = (H^T H) x - H^T y
                     const float xv = fused ? xwin[o * Geom<KW>::WP + q] : xc[n];
                     const float v = update1(p, xv, g[o][q], dc ? __ldg(dc + n) : 0.f, z[q],
                                             p.z2 ? __ldg(p.z2 + chain * plane + n) : 0.f);

@@ -63,7 +63,15 @@ def test_blur_and_adjoint(P, orc, ny, nx, kh, kw):
 def test_normals_match_oracle(P, orc):
     """x = 0, y = 0, no prior, no projection: x+ = sqrt(2 gamma) xi, so the GPU's
     xi can be read back and compared with the oracle's Philox/Box-Muller draws,
-    including widths that are not multiples of 4 and several chains."""
+    including widths that are not multiples of 4 and several chains.
+
+    Bound: the GPU forms -2 ln u from __logf and a series, and sin / cos of
+    2 pi u from __sincosf, with the error bounds CUDA documents for them. The
+    relative error of rad = sqrt(-2 ln u) stays below 2.5e-7 for u < 1/2
+    (rad <= 5.9) and 1.7e-6 for u in [1/2, 7/8] (rad <= 1.18); sin and cos are
+    off by at most 5.7e-7. So |dz| <= max(5.9 * 3.7e-7, 1.18 * 1.8e-6)
+    + 5.9 * 5.7e-7 < 5.5e-6, plus 6e-7 for the FP32 x+ = sqrt(2 gamma) xi and
+    its readback: 7e-6 (measured over 2.7e8 draws: 1.9e-6)."""
     for ny, nx, nch in [(8, 8, 3), (5, 7, 2), (33, 129, 1)]:
         h = dev(np.ones((1, 1)))
         x = torch.zeros((nch, ny, nx), device="cuda")
@@ -75,7 +83,7 @@ def test_normals_match_oracle(P, orc):
         xi = (x / np.sqrt(2 * gamma)).cpu().numpy().astype(np.float64)
         for c in range(nch):
             ref = orc.normals(seed, 9, c, ny * nx).reshape(ny, nx)
-            np.testing.assert_allclose(xi[c], ref, rtol=0, atol=2e-6 * max(1.0, np.abs(ref).max()))
+            np.testing.assert_allclose(xi[c], ref, rtol=0, atol=7e-6)
 
 
 def _net(K, F, seed=11):
