@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libpnp.so")
-SOURCES = ["api.cu", "k_stencil.cu", "k_conv_simt.cu", "k_conv_tc.cu", "k_ddfb.cu", "noalloc.cu", "batch.cu",
+SOURCES = ["api.cu", "k_stencil.cu", "k_update_os.cu", "k_conv_simt.cu", "k_conv_tc.cu", "k_ddfb.cu", "noalloc.cu", "batch.cu",
            "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

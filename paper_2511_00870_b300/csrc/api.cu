@@ -754,6 +754,8 @@ pnp_status problem_update_params(const pnp_problem* p, UpdateParams& u) {
         u.h = nullptr;
         u.kh = 2 * p->kh - 1;
         u.kw = 2 * p->kw - 1;
+        u.os = 1;
+        u.err = p->err;
     }
     if (p->poisson) {
         u.inv_s2 = (float)(p->eta / p->rho1);

@@ -221,6 +221,11 @@ struct UpdateParams {
     // read the current state).
     const float* qb;
     float* x_out;
+    // One-pass form: os != 0 lets the launch use the pipelined kernel
+    // (k_update_os) when the form fits it; err receives 1 if one of that
+    // kernel's bounded waits ran out.
+    int os = 0;
+    int* err = nullptr;
 };
 
 // Auxiliary-variable update of the Poisson sampler (k_zupdate).
@@ -258,6 +263,16 @@ cudaError_t launch_zupdate_group(const ZParams* jobs, int n, cudaStream_t s);
 // (shared by the chains); no stencil, p.h unused.
 cudaError_t launch_update_mask(const UpdateParams& p, cudaStream_t s);
 cudaError_t launch_langevin_update(const UpdateParams& p, cudaStream_t s);
+// Pipelined one-pass update (k_update_os.cu) with stencil tile shape `tile`:
+// cudaErrorNotSupported when p is not of its form (the caller then launches
+// the per-tile kernel).
+cudaError_t launch_update_os(const UpdateParams& p, int tile, cudaStream_t s);
+// cuTensorMapEncodeTiled from the driver (nullptr if unavailable).
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                    const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                    const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+PFN_encodeTiled get_encode();
 // Times the stencil tile shapes for r = H x - y and for the update `u` (which it
 // runs, overwriting u.x / u.mean / u.m2) and returns the fastest of each.
 cudaError_t stencil_autotune(const float* x, const float* y, const float* h, const float* hsep,
