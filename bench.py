@@ -463,16 +463,25 @@ def run_batch(args, P, torch, stream, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
-def _stencil_roofline(peaks, kern, npix, poisson=False, wide_h=None, iters=None):
+def _pow2_side(n):
+    return 64 <= n <= 4096 and (n & (n - 1)) == 0
+
+
+def _stencil_roofline(peaks, kern, npix, poisson=False, wide_h=None, iters=None, spectral=False):
     """Stencils against HBM from the eager per-kernel timing: algorithmic bytes
     per pixel (r = Hx - y: read x, y, write r: 12 B; update while sampling:
     read r, x, d, mean, m2, write x, mean, m2: 32 B, Poisson + z2: 36 B;
     Poisson z-update: read x, z1, z2, y, write z1, z2: 24 B) x the pixels of
     one iteration (npix, all jobs) x iterations / the kernel's total time
     (iters = None: one launch per iteration). Large (wide) kernels add their
-    FMA rate against the FP32 FFMA peak."""
+    FMA rate against the FP32 FFMA peak. With the spectral gradient the "blur"
+    timer holds the row FFTs (read x, write the spectrum: 12 B) and the column
+    pass (read spectrum and |H^|^2, write spectrum: 20 B), and the "update"
+    timer the inverse row FFTs fused with the update (spectrum + 32 B)."""
     out = {}
-    for kname, bpp in (("blur", 12), ("update", 36 if poisson else 32), ("zupdate", 24)):
+    kinds = ((("blur", 32), ("update", 40)) if spectral else
+             (("blur", 12), ("update", 36 if poisson else 32), ("zupdate", 24)))
+    for kname, bpp in kinds:
         n = kern["counts"].get(kname, 0)
         if not n:
             continue
@@ -481,7 +490,9 @@ def _stencil_roofline(peaks, kern, npix, poisson=False, wide_h=None, iters=None)
         gbs = bpp * npix * it / (kern["breakdown"][kname] * 1e-3) / 1e9
         out[kname] = dict(avg_us=round(avg * 1e3, 2), bytes_per_pixel=bpp,
                           achieved_gbs=round(gbs, 1), frac=round(gbs / peaks["hbm"], 4))
-        if wide_h is not None and kname != "zupdate":
+        if spectral:
+            out[kname]["form"] = "spectral (FFT) gradient"
+        elif wide_h is not None and kname != "zupdate":
             nnz = int(np.count_nonzero(wide_h.astype(np.float32)))
             tf = 2.0 * nnz * npix * it / (kern["breakdown"][kname] * 1e-3) / 1e12
             alu = 148 * 128 * 2 * peaks["sm_max"] / 1e6
@@ -780,7 +791,9 @@ def measure_single(args, P, torch, stream, ws, rank, local, workload, precs, ste
                     unit="TFLOP/s", frac=round(achieved / alu_peak, 4), traffic=None,
                     kernel="k_conv3x3<64,64>", peak_kind="FP32 FFMA: 148 SM x 128 lanes x 2 x max clock")
     wide = prob.h if (not poisson and not inpaint and max(prob.h.shape) > 31) else None
-    stencils = _stencil_roofline(peaks, kern, npix, poisson=poisson, wide_h=wide)
+    spectral = (wide is not None and not args.no_spectral and _pow2_side(prob.y.shape[0]) and
+                _pow2_side(prob.y.shape[1]))
+    stencils = _stencil_roofline(peaks, kern, npix, poisson=poisson, wide_h=wide, spectral=spectral)
     cpu = None
     if cpu_baseline:
         try:
@@ -811,7 +824,9 @@ def measure_single(args, P, torch, stream, ws, rank, local, workload, precs, ste
                     l2="working set per step > 126 MB L2 (activation planes)",
                     graph="one CUDA graph per iteration",
                     stencil_tile=("forced %d" % args.stencil_tile if args.stencil_tile >= 0
-                                  else "autotuned")),
+                                  else "autotuned"),
+                    wide_gradient=(None if wide is None else
+                                   "spectral (FFT)" if spectral else "direct wide stencil")),
         roofline=roof,
         cpu_baseline=cpu,
         e2e=e2e,
@@ -856,6 +871,8 @@ def main():
     ap.add_argument("--jobs", type=int, default=0, help="serve: number of arrivals (default: --steps)")
     ap.add_argument("--size", type=int, default=0,
                     help="single-job Gaussian workloads: the same posterior on a size x size image")
+    ap.add_argument("--no-spectral", action="store_true",
+                    help="wide blurs: the direct stencil instead of the spectral (FFT) gradient")
     ap.add_argument("--stencil-tile", type=int, default=-1,
                     help="force stencil tile shape k for every launch (profiling; default: autotuned)")
     args = ap.parse_args()
@@ -878,6 +895,8 @@ def main():
         torch.distributed.barrier()
     if args.stencil_tile >= 0:
         P.pnp_set_stencil_tile(args.stencil_tile)
+    if args.no_spectral:
+        P.pnp_set_spectral(False)
     # a dedicated stream: the problems enqueue on it and the events are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)

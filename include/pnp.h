@@ -321,6 +321,15 @@ pnp_status pnp_set_graph_mode(int enable);
  * on): a kernel's prologue (barriers, TMEM, weights) overlaps its
  * predecessor's tail. Changes timings only, never results. */
 pnp_status pnp_set_pdl(int enable);
+/* Spectral likelihood gradient (default on) for problems created afterwards
+ * whose blur is wider than 31 taps, under Gaussian noise, on an image whose
+ * sides are powers of two in [64, 4096] (Sec. IV-A's motion blurs): since
+ * H^T H is a circular convolution, (H^T H) x = F^-1(|F h|^2 F x) is evaluated
+ * by hand-written FP32 FFTs (row FFTs, column FFTs with the product and their
+ * inverse, inverse row FFTs fused with the update), with H^T y formed once.
+ * Off: the direct wide stencil (r = H x - y, then H^T r). The two agree to
+ * FP32 FFT rounding (about 1e-6 of the gradient's scale), not bitwise. */
+pnp_status pnp_set_spectral(int enable);
 
 /* ------------------------------------------------------------------------
  * Stencil tile shapes (library tuning; the paper has no counterpart). The

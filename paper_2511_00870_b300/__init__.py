@@ -121,6 +121,12 @@ def pnp_set_pdl(enable: bool):
     check(load().pnp_set_pdl(int(bool(enable))))
 
 
+def pnp_set_spectral(enable: bool):
+    """Spectral (FFT) likelihood gradient for wide blurs on power-of-two images
+    (default on); applies to problems created afterwards."""
+    check(load().pnp_set_spectral(int(bool(enable))))
+
+
 def pnp_stencil_tile_count() -> int:
     return int(load().pnp_stencil_tile_count())
 

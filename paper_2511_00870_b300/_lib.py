@@ -82,6 +82,7 @@ SIGNATURES = {
     "pnp_problem_x_device": ([vp], vp),
     "pnp_set_graph_mode": ([i32], i32),
     "pnp_set_pdl": ([i32], i32),
+    "pnp_set_spectral": ([i32], i32),
     "pnp_stencil_tile_count": ([], i32),
     "pnp_set_stencil_tile": ([i32], i32),
     "pnp_problem_stencil_tiles": ([vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)], i32),

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libpnp.so")
-SOURCES = ["api.cu", "k_stencil.cu", "k_update_os.cu", "k_conv_simt.cu", "k_conv_tc.cu", "k_ddfb.cu", "noalloc.cu", "batch.cu",
+SOURCES = ["api.cu", "k_stencil.cu", "k_update_os.cu", "k_spectral.cu", "k_conv_simt.cu", "k_conv_tc.cu", "k_ddfb.cu", "noalloc.cu", "batch.cu",
            "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
@@ -38,8 +38,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(objdir, exist_ok=True)
     objs = []
     procs = []
+    # headers are shared: an object is reused only if it is newer than its own
+    # source and every header
+    headers = [f for f in _inputs() if not f.endswith(".cu")]
+    newest_header = max(os.path.getmtime(f) for f in headers)
     for src in SOURCES:
         obj = os.path.join(objdir, src.replace(".cu", ".o"))
+        if (not force and os.path.exists(obj) and
+                os.path.getmtime(obj) > max(newest_header, os.path.getmtime(os.path.join(CSRC, src)))):
+            objs.append(obj)
+            continue
         cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                "-I", os.path.join(ROOT, "include"), "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:

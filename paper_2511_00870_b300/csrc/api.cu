@@ -63,6 +63,7 @@ static bool g_timing = false;
 static bool g_pdl = true;
 bool pdl_enabled() { return g_pdl; }
 static std::atomic<int64_t> g_launches{0};
+static std::atomic<int> g_spectral{1};   // spectral gradient for eligible wide-blur problems
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 static const char* g_timer_names[T_COUNT] = {"blur", "update", "conv_fp32", "conv_tc", "conv_edge", "conv_last",
                                               "zupdate"};
@@ -697,6 +698,7 @@ extern "C" void pnp_destroy_problem(pnp_problem* p) {
                     (void*)p->hsep, (void*)p->z1, (void*)p->z2, (void*)p->wt_fwd,
                     (void*)p->wt_adj, (void*)p->err, (void*)p->qb, (void*)p->qsep})
         dfree(q);
+    pnp::spectral_free(p->sp);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
     delete p;
 }
@@ -716,6 +718,11 @@ static pnp_status poisson_refresh_r(pnp_problem* p) {
 pnp_status problem_pre(pnp_problem* p, cudaStream_t s) {
     if (p->inpaint) return PNP_OK;   // H = diag(mask): the update forms x - y itself
     if (p->fused) return PNP_OK;     // the update forms (H^T H) x - H^T y from x itself
+    if (p->sp) {
+        // P F(x) for every chain; the update's inverse row FFTs finish F^-1
+        PNP_CUDA_TRY(spectral_pre(*p->sp, p->x, p->nchain, s));
+        return PNP_OK;
+    }
     if (p->poisson) {
         return PNP_OK;               // r = eta H x - z1 was written by the last z-update
     } else {
@@ -757,6 +764,7 @@ pnp_status problem_update_params(const pnp_problem* p, UpdateParams& u) {
         u.os = 1;
         u.err = p->err;
     }
+    if (p->sp) u.qb = p->qb;   // spectral gradient: g = Re(F^-1(P F x)) - H^T y
     if (p->poisson) {
         u.inv_s2 = (float)(p->eta / p->rho1);
         u.z2 = p->z2;
@@ -800,6 +808,7 @@ pnp_status problem_post(pnp_problem* p, cudaStream_t s) {
     UpdateParams u;
     PNP_TRY(problem_update_params(p, u));
     if (p->inpaint) PNP_CUDA_TRY(launch_update_mask(u, s));
+    else if (p->sp) PNP_CUDA_TRY(spectral_update(*p->sp, u, s));
     else PNP_CUDA_TRY(launch_langevin_update(u, s));
     if (p->poisson) PNP_CUDA_TRY(launch_zupdate(problem_z_params(p), s));
     problem_flip(p);
@@ -1129,6 +1138,24 @@ extern "C" pnp_status pnp_create_problem(const pnp_problem_desc* dsc, pnp_proble
                 p->xb[1] = p->r;   // the residual plane is not needed: second state buffer
             }
         }
+        // Spectral gradient for wide blurs under Gaussian noise on power-of-two
+        // images: g = F^-1(|H^|^2 F(x)) - H^T y; H^T y by the direct adjoint
+        if (g_spectral.load() && !poisson && !inpaint && is_wide(q.kh, q.kw) &&
+            spectral_eligible(q.ny, q.nx, q.kh, q.kw)) {
+            if ((st = dalloc(&p->qb, (size_t)N)) != PNP_OK) {
+                pnp_destroy_problem(p);
+                return st;
+            }
+            cudaError_t e = launch_blur_adjoint(p->y, p->h, q.kh, q.kw, q.ny, q.nx, 1, 1.0f, p->qb,
+                                                p->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+            if (e == cudaSuccess)
+                e = spectral_setup(p->h, q.kh, q.kw, q.ny, q.nx, p->nchain, p->stream, &p->sp);
+            if (e != cudaSuccess && e != cudaErrorNotSupported) {
+                pnp_destroy_problem(p);
+                return cuda_fail(e, "pnp_create_problem: spectral gradient");
+            }
+        }
     }
     {
         // stencil tile shapes, timed on this problem's buffers before they are initialised
@@ -1278,6 +1305,11 @@ extern "C" pnp_status pnp_set_graph_mode(int enable) {
 
 extern "C" pnp_status pnp_set_pdl(int enable) {
     g_pdl = enable != 0;
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_set_spectral(int enable) {
+    g_spectral = enable != 0;
     return PNP_OK;
 }
 

@@ -267,6 +267,28 @@ cudaError_t launch_langevin_update(const UpdateParams& p, cudaStream_t s);
 // cudaErrorNotSupported when p is not of its form (the caller then launches
 // the per-tile kernel).
 cudaError_t launch_update_os(const UpdateParams& p, int tile, cudaStream_t s);
+// Spectral gradient of a wide blur (k_spectral.cu): g = F^-1(|H^|^2 F(x)) -
+// H^T y for power-of-two images, the spectrum in 4-column panels.
+struct SpectralPlan {
+    int ny = 0, nx = 0, lgny = 0, lgnx = 0;
+    float2* Z = nullptr;     // [nchain] spectra, panel layout
+    float* P = nullptr;      // |H^|^2 / (ny nx), panel layout
+    float2* twx = nullptr;   // exp(-2 pi i n / nx)
+    float2* twy = nullptr;   // exp(-2 pi i n / ny)
+};
+// ny, nx powers of two in [64, 4096] and the kernel no larger than the image
+bool spectral_eligible(int ny, int nx, int kh, int kw);
+// Allocates the plan and computes P from the device kernel h [kh][kw]
+// (synchronises s); cudaErrorNotSupported if not eligible.
+cudaError_t spectral_setup(const float* h, int kh, int kw, int ny, int nx, int nchain,
+                           cudaStream_t s, SpectralPlan** out);
+void spectral_free(SpectralPlan* S);
+// Z = F^-1-ready spectra P F(x) (row FFTs, then column FFTs, multiply,
+// inverse column FFTs) of the nchain planes of x.
+cudaError_t spectral_pre(const SpectralPlan& S, const float* x, int nchain, cudaStream_t s);
+// Inverse row FFTs and the x-update with g = Re(.) - p.qb, x updated in place.
+cudaError_t spectral_update(const SpectralPlan& S, const UpdateParams& p, cudaStream_t s);
+
 // cuTensorMapEncodeTiled from the driver (nullptr if unavailable).
 typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                     const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -443,6 +465,9 @@ struct pnp_problem {
     cudaGraphExec_t graph_batch[2] = {nullptr, nullptr};   // kGraphBatch iterations
     bool eager_done = false;                 // one eager iteration ran (lazy kernel setup)
     int* err = nullptr;                      // device timeout flag of the tensor-core layers
+    // spectral gradient of a wide blur (Gaussian noise, power-of-two image):
+    // no residual plane, qb = H^T y, x updated in place
+    pnp::SpectralPlan* sp = nullptr;
 };
 
 namespace pnp {

@@ -76,6 +76,10 @@ static size_t job_footprint(const pnp_problem_desc& d, const pnp_denoiser* D, pn
     const size_t N = (size_t)d.ny * d.nx, nc = (size_t)std::max(1, d.nchain);
     size_t b = N * 4 + (size_t)d.kh * d.kw * 4 + 5 * N * nc * 4 + 4096;
     if (d.noise_model == PNP_POISSON) b += 2 * N * nc * 4;   // z1, z2
+    else b += N * 4;                                        // H^T y (one-pass or spectral gradient)
+    if (d.noise_model == PNP_GAUSSIAN && !d.mask && is_wide(d.kh, d.kw) &&
+        spectral_eligible(d.ny, d.nx, d.kh, d.kw))
+        b += N * nc * 8 + N * 4 + (size_t)(d.ny + d.nx) * 8;   // spectra, |H^|^2, twiddles
     if (D) {
         b += prec == PNP_FP32 ? denoise_fp32_scratch(D->dev, d.ny, d.nx, (int)nc)
                               : denoise_bf16_scratch(D->dev, d.ny, d.nx, (int)nc);

@@ -151,3 +151,38 @@ def test_paper_scale_sampled_bf16(P, orc, n, L, nwin):
     gcrop = np.abs(x64[:96, :96] - orc.denoise(x64[:96, :96], net)).max()
     bound = c_prior * 1e-2 * max(gmax, gcrop) + 1e-5 * np.abs(xn[0]).max()
     assert err <= bound, (err, bound)
+
+
+@pytest.mark.parametrize("ny,nx,L,prior", [(256, 256, 65, False), (256, 512, 129, True),
+                                           (512, 128, 65, True)])
+def test_spectral_gradient_matches_direct_and_oracle(P, orc, ny, nx, L, prior):
+    """Power-of-two images take the spectral gradient (FFT of x, |H^|^2,
+    inverse FFT) instead of the direct wide stencil. One step from the same
+    state with each, and the oracle's direct FP64 sums: both within
+    1e-5 max|x+| of the oracle (the FP32 FFT's rounding, a few 1e-7 of the
+    gradient's scale times gamma / sigma^2, stays far below it)."""
+    prob = synth.make_problem(ny, nx, synth.motion_kernel(L, 0.45), 25.0, 90 + L)
+    dw = synth.workload_denoiser(1)
+    den = P.Denoiser.from_weights(dw) if prior else None
+    x0 = np.clip(prob.y + 0.03 * np.random.default_rng(L).standard_normal(prob.shape), -0.1,
+                 1.1).astype(np.float32)
+    out = {}
+    try:
+        for spectral in (True, False):
+            P.pnp_set_spectral(spectral)
+            gp = P.Problem(prob.y, prob.h, prob.sigma, den, seed=prob.seed, burn_in=0)
+            prm = gp.params()
+            gp.set_state(x0, 5)
+            gp.step(1)
+            out[spectral] = gp.state()[0][0]
+    finally:
+        P.pnp_set_spectral(True)
+    alpha = prm["alpha"] if prior else 0.0
+    op = orc.Problem(prob.y, prob.h, prob.sigma, alpha, prm["eps"], prm["lam"], prm["gamma"],
+                     prob.seed, net=orc.Net.from_weights(dw) if prior else None)
+    ref = orc.langevin_step(op, x0.astype(np.float64), 5)
+    bound = 1e-5 * np.abs(ref).max()
+    e_sp, e_dir = np.abs(out[True] - ref).max(), np.abs(out[False] - ref).max()
+    print("%dx%d L=%d: spectral %.3e, direct %.3e, |spectral - direct| %.3e (bound %.3e)" % (
+        ny, nx, L, e_sp, e_dir, np.abs(out[True] - out[False]).max(), bound))
+    assert e_sp <= bound and e_dir <= bound
