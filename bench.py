@@ -353,7 +353,9 @@ def _source_sha(kernel):
     ncu traffic figure to the kernel version it was measured on)."""
     import hashlib
     name = ("k_conv_tc.cu" if kernel.startswith("k_conv_tc") or kernel.startswith("k_first_tc")
-            else "k_ddfb.cu" if kernel.startswith("k_ddfb") else "k_stencil.cu")
+            else "k_ddfb.cu" if kernel.startswith("k_ddfb")
+            else "k_update_os.cu" if kernel.startswith("k_update_os")
+            else "k_spectral.cu" if kernel.startswith("k_sp_") else "k_stencil.cu")
     path = os.path.join(ROOT, "paper_2511_00870_b300", "csrc", name)
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:12]
 
