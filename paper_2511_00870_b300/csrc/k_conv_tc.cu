@@ -49,6 +49,14 @@
 
 namespace pnp {
 
+// Two FP32 values -> packed BF16x2 (lo in the low half) with ReLU applied by
+// the conversion itself (cvt.rn.relu: negative results become +0).
+__device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;\n" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
 namespace tc {
 constexpr int F = 64;
 constexpr int SEG = 128;                    // output pixels per row segment (UMMA M)
@@ -443,17 +451,14 @@ __global__ void __launch_bounds__(TcMode<LAST, FP8>::THREADS, 1)
                 } else {
                     // BF16 activations: [img][y][8 cg][xp][8]
                     __nv_bfloat16* o = J->out + ((((int64_t)p.img * J->ny + yy) * 8) * nxp + x) * 8;
+                    const uint32_t keep = valid ? 0xffffffffu : 0u;   // zero outside the valid rect
 #pragma unroll
                     for (int cg = 0; cg < 8; ++cg) {
                         uint32_t pk[4];
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int c0 = cg * 8 + 2 * e;
-                            float v0 = fmaxf(acc(c0) + c.bias[c0], 0.f);
-                            float v1 = fmaxf(acc(c0 + 1) + c.bias[c0 + 1], 0.f);
-                            if (!valid) v0 = v1 = 0.f;
-                            __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
-                            pk[e] = *reinterpret_cast<uint32_t*>(&h2);
+                            pk[e] = pack_bf16_relu(acc(c0) + c.bias[c0], acc(c0 + 1) + c.bias[c0 + 1]) & keep;
                         }
                         *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     }
@@ -682,16 +687,14 @@ __global__ void __launch_bounds__(128) k_first_tc(const __grid_constant__ FirstT
             }
         } else {
             __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(J.out) + ((((int64_t)img * ny + yy) * 8) * nxp + xx) * 8;
+            const uint32_t keep = valid ? 0xffffffffu : 0u;   // zero outside the valid rect
 #pragma unroll
             for (int cg = 0; cg < 8; ++cg) {
                 uint32_t pk[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    float v0 = fmaxf(__uint_as_float(acc[cg * 8 + 2 * e]), 0.f);
-                    float v1 = fmaxf(__uint_as_float(acc[cg * 8 + 2 * e + 1]), 0.f);
-                    if (!valid) v0 = v1 = 0.f;
-                    pk[e] = pack_bf16(v0, v1);
-                }
+                for (int e = 0; e < 4; ++e)
+                    pk[e] = pack_bf16_relu(__uint_as_float(acc[cg * 8 + 2 * e]),
+                                           __uint_as_float(acc[cg * 8 + 2 * e + 1])) & keep;
                 *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
         }
