@@ -477,11 +477,12 @@ def _stencil_roofline(peaks, kern, npix, poisson=False, wide_h=None, iters=None,
     one iteration (npix, all jobs) x iterations / the kernel's total time
     (iters = None: one launch per iteration). Large (wide) kernels add their
     FMA rate against the FP32 FFMA peak. With the spectral gradient the "blur"
-    timer holds the row FFTs (read x, write the spectrum: 12 B) and the column
-    pass (read spectrum and |H^|^2, write spectrum: 20 B), and the "update"
-    timer the inverse row FFTs fused with the update (spectrum + 32 B)."""
+    timer holds the row FFTs (read x, write the half spectrum: 4 + 4 B) and
+    the column pass (read and write the half spectrum, read |H^|^2: 4 + 4 + 2 B),
+    and the "update" timer the inverse row FFTs fused with the update (half
+    spectrum 4 B + 32 B)."""
     out = {}
-    kinds = ((("blur", 32), ("update", 40)) if spectral else
+    kinds = ((("blur", 18), ("update", 36)) if spectral else
              (("blur", 12), ("update", 36 if poisson else 32), ("zupdate", 24)))
     for kname, bpp in kinds:
         n = kern["counts"].get(kname, 0)

@@ -271,8 +271,9 @@ cudaError_t launch_update_os(const UpdateParams& p, int tile, cudaStream_t s);
 // H^T y for power-of-two images, the spectrum in 4-column panels.
 struct SpectralPlan {
     int ny = 0, nx = 0, lgny = 0, lgnx = 0;
-    float2* Z = nullptr;     // [nchain] spectra, panel layout
-    float* P = nullptr;      // |H^|^2 / (ny nx), panel layout
+    float2* Z = nullptr;     // [nchain] half spectra of the rows (nx / 2 columns), panel layout
+    float* P = nullptr;      // |H^|^2 / (2 ny nx) of the half spectrum, panel layout
+    float* PN = nullptr;     // the same for the Nyquist column nx / 2, [ny]
     float2* twx = nullptr;   // exp(-2 pi i n / nx)
     float2* twy = nullptr;   // exp(-2 pi i n / ny)
 };
