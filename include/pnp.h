@@ -292,7 +292,8 @@ pnp_status pnp_prepare_graphs(pnp_problem* p);
 /* Run T iterations with the given burn-in (resets nothing) and wait. */
 pnp_status pnp_run_chain(pnp_problem* p, int T, int burn_in);
 /* Wait for the problem's stream. PNP_ETIMEOUT if a bounded device-side wait
- * of a tensor-core denoiser layer ran out since the last synchronising call
+ * (a tensor-core denoiser layer, or the pipelined one-pass update's window
+ * copies) ran out since the last synchronising call
  * (pnp_sync, pnp_run_chain, pnp_get_state, pnp_get_moments report it once and
  * clear it; the chain state is then not trustworthy: reset it with
  * pnp_set_state). */
