@@ -176,6 +176,17 @@ pnp_status pnp_denoise_status(const pnp_denoiser* D, void* stream);
  * MMAs already in flight, releases its tensor memory and sets the caller's
  * timeout flag, which the next synchronising call reports as PNP_ETIMEOUT. */
 pnp_status pnp_debug_inject_tc_timeout(int cta, int load_index, long long budget_cycles);
+/* Test hook (no counterpart in the paper): arms a one-shot fault for the next
+ * launch of the pipelined one-pass update (k_update_os: a single problem with
+ * a separable blur of at most 15 taps under Gaussian noise) made outside
+ * stream capture: CTA `cta` does not issue the shared-memory window of its
+ * tile number `tile_index` (nothing is in flight for it), and the launch's
+ * waits give up after budget_cycles (>= 1000). That CTA then waits for its own
+ * copies in flight, sets the problem's timeout flag (PNP_ETIMEOUT at the next
+ * synchronising call), skips its remaining tiles and still arrives on the
+ * step counter. An out-of-range cta or tile_index leaves the launch
+ * unaffected. */
+pnp_status pnp_debug_inject_update_timeout(int cta, int tile_index, long long budget_cycles);
 
 /* One fused PnP-ULA x-update (Eq. 8) for nchain chains sharing y and h:
  *   g = H^T r / sigma^2 (r = H x - y from pnp_blur, device [nchain][ny][nx]),

@@ -112,6 +112,13 @@ def pnp_debug_inject_tc_timeout(cta: int, load_index: int, budget_cycles: int):
     check(load().pnp_debug_inject_tc_timeout(int(cta), int(load_index), int(budget_cycles)))
 
 
+def pnp_debug_inject_update_timeout(cta: int, tile_index: int, budget_cycles: int):
+    """Test hook: the next pipelined one-pass update launched outside stream
+    capture has CTA `cta` skip issuing the window of its tile `tile_index`, with
+    every wait bounded by budget_cycles; the problem then reports PNP_ETIMEOUT."""
+    check(load().pnp_debug_inject_update_timeout(int(cta), int(tile_index), int(budget_cycles)))
+
+
 def pnp_set_graph_mode(enable: bool):
     check(load().pnp_set_graph_mode(int(bool(enable))))
 

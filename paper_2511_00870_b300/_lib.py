@@ -60,6 +60,7 @@ SIGNATURES = {
     "pnp_denoise_noalloc": ([vp, i32, vp, i32, i32, i32, vp, vp], i32),
     "pnp_denoise_status": ([vp, vp], i32),
     "pnp_debug_inject_tc_timeout": ([i32, i32, C.c_longlong], i32),
+    "pnp_debug_inject_update_timeout": ([i32, i32, C.c_longlong], i32),
     "pnp_langevin_update": ([vp, vp, vp, vp, i32, i32, i32, i32, i32, f64, f64, f64, f64, f64,
                              u64, u32, i32, vp, vp, i64, vp], i32),
     "pnp_inpaint_update": ([vp, vp, vp, i32, i32, i32, f64, f64, f64, f64, f64, u64, u32, i32,

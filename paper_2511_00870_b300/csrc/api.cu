@@ -36,8 +36,8 @@ pnp_status take_timeout(int* flag, cudaStream_t s, const char* who) {
     PNP_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
     PNP_CUDA_TRY(cudaStreamSynchronize(s));
     return fail(PNP_ETIMEOUT, std::string(who) +
-                                  ": a bounded wait in a tensor-core denoiser layer ran out; the "
-                                  "affected results are incomplete");
+                                  ": a bounded wait on the device (tensor-core denoiser layer or "
+                                  "pipelined update) ran out; the affected results are incomplete");
 }
 
 int num_sms() {
@@ -590,6 +590,15 @@ extern "C" pnp_status pnp_debug_inject_tc_timeout(int cta, int load_index,
         return fail(PNP_EINVAL, "pnp_debug_inject_tc_timeout: need cta >= 0, load_index >= 0 and "
                                 "budget_cycles >= 1000");
     tc_inject_timeout(cta, load_index, budget_cycles);
+    return PNP_OK;
+}
+
+extern "C" pnp_status pnp_debug_inject_update_timeout(int cta, int tile_index,
+                                                      long long budget_cycles) {
+    if (cta < 0 || tile_index < 0 || budget_cycles < 1000)
+        return fail(PNP_EINVAL, "pnp_debug_inject_update_timeout: need cta >= 0, tile_index >= 0 "
+                                "and budget_cycles >= 1000");
+    os_inject_timeout(cta, tile_index, budget_cycles);
     return PNP_OK;
 }
 

@@ -173,10 +173,18 @@ __device__ __forceinline__ void os_epilogue(const UpdateParams& p, const OsTile&
     }
 }
 
+// Wait budget and the one-shot test fault (pnp_debug_inject_update_timeout):
+// CTA skip_cta does not issue the window of its tile number skip_k (no copy,
+// no arrival), so its wait on that window runs out.
+struct OsCtl {
+    long long budget;
+    int skip_cta, skip_k;
+};
+
 template <int KW, int R, int BY>
 __global__ void __launch_bounds__(16 * BY) k_update_os(const UpdateParams p,
                                                        const __grid_constant__ CUtensorMap map,
-                                                       int ntx, int nty, int ntiles) {
+                                                       int ntx, int nty, int ntiles, OsCtl ctl) {
     using G = Geom<KW>;
     using O = OsGeom<KW, R, BY>;
     extern __shared__ unsigned char os_raw[];
@@ -206,20 +214,27 @@ __global__ void __launch_bounds__(16 * BY) k_update_os(const UpdateParams p,
         const int64_t n = (int64_t)t + 1 - *p.burn_dev;
         inv_n = n > 0 ? 1.0f / (float)n : 0.0f;
     }
+    const bool inject = (int)blockIdx.x == ctl.skip_cta;
     int tile = blockIdx.x;
-    if (tile < ntiles) os_issue<KW, R, BY>(p, &map, tile, ntx, nty, win[0], &bar[0], tid);
+    if (tile < ntiles && !(inject && ctl.skip_k == 0))
+        os_issue<KW, R, BY>(p, &map, tile, ntx, nty, win[0], &bar[0], tid);
     for (int k = 0; tile < ntiles; ++k) {
         const int b = k & 1;
         const int next = tile + gridDim.x;
-        if (next < ntiles) os_issue<KW, R, BY>(p, &map, next, ntx, nty, win[b ^ 1], &bar[b ^ 1], tid);
+        if (next < ntiles && !(inject && ctl.skip_k == k + 1))
+            os_issue<KW, R, BY>(p, &map, next, ntx, nty, win[b ^ 1], &bar[b ^ 1], tid);
         const uint32_t par = (uint32_t)(k >> 1) & 1u;
-        const bool ok = ptx::mbar_wait(&bar[b], par, &abort_s, kOsBudget);
+        const bool ok = ptx::mbar_wait(&bar[b], par, &abort_s, ctl.budget);
         if (!__syncthreads_and(ok)) {
             // unwind: wait (bounded) for this CTA's own copies still in flight
-            ptx::mbar_wait_drain(&bar[b], par, kOsBudget);
-            if (next < ntiles) ptx::mbar_wait_drain(&bar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u, kOsBudget);
+            // (a window that was never issued simply runs out the budget
+            // again), report, and skip the remaining tiles; the CTA still
+            // arrives on the step counter below, so the count stays whole
+            ptx::mbar_wait_drain(&bar[b], par, ctl.budget);
+            if (next < ntiles)
+                ptx::mbar_wait_drain(&bar[b ^ 1], (uint32_t)((k + 1) >> 1) & 1u, ctl.budget);
             if (tid == 0 && p.err) atomicExch(p.err, 1);
-            return;
+            break;
         }
         sep_vert<KW, SEP_VR>(win[b], us, KW, O::ROWS, V);
         __syncthreads();
@@ -239,7 +254,11 @@ __global__ void __launch_bounds__(16 * BY) k_update_os(const UpdateParams p,
 
 // ------------------------------------------------------------------ host side
 
-using OsFn = void (*)(const UpdateParams, const CUtensorMap, int, int, int);
+using OsFn = void (*)(const UpdateParams, const CUtensorMap, int, int, int, OsCtl);
+
+std::mutex g_os_inject_mu;
+bool g_os_inject_armed = false;
+OsCtl g_os_inject{kOsBudget, -1, 0};
 
 template <int KW>
 OsFn os_fn_kw(int tile) {
@@ -358,7 +377,24 @@ cudaError_t launch_update_os(const UpdateParams& p, int tile, cudaStream_t s) {
     if (ntiles64 > (1 << 30)) return cudaErrorNotSupported;
     const int ntiles = (int)ntiles64;
     const int grid = (int)std::min<int64_t>(ntiles64, (int64_t)per_sm * sm_count());
-    return launch_pdl(fn, dim3(grid), dim3(16, BY), smem, s, p, map, ntx, nty, ntiles);
+    OsCtl ctl{kOsBudget, -1, 0};
+    {
+        // the armed test fault goes to the next launch that is not being captured
+        std::lock_guard<std::mutex> lk(g_os_inject_mu);
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (g_os_inject_armed && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
+            cs == cudaStreamCaptureStatusNone) {
+            g_os_inject_armed = false;
+            ctl = g_os_inject;
+        }
+    }
+    return launch_pdl(fn, dim3(grid), dim3(16, BY), smem, s, p, map, ntx, nty, ntiles, ctl);
+}
+
+void os_inject_timeout(int cta, int tile_index, long long budget_cycles) {
+    std::lock_guard<std::mutex> lk(g_os_inject_mu);
+    g_os_inject_armed = true;
+    g_os_inject = OsCtl{budget_cycles, cta, tile_index};
 }
 
 }  // namespace pnp

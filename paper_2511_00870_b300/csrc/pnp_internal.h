@@ -267,6 +267,8 @@ cudaError_t launch_langevin_update(const UpdateParams& p, cudaStream_t s);
 // cudaErrorNotSupported when p is not of its form (the caller then launches
 // the per-tile kernel).
 cudaError_t launch_update_os(const UpdateParams& p, int tile, cudaStream_t s);
+// Arms the one-shot test fault of the next uncaptured k_update_os launch.
+void os_inject_timeout(int cta, int tile_index, long long budget_cycles);
 // Spectral gradient of a wide blur (k_spectral.cu): g = F^-1(|H^|^2 F(x)) -
 // H^T y for power-of-two images, the spectrum in 4-column panels.
 struct SpectralPlan {

@@ -78,3 +78,37 @@ def test_inject_hook_validates_its_arguments(P):
     for args in ((-1, 0, BUDGET), (0, -1, BUDGET), (0, 0, 10)):
         with pytest.raises(P.PnpError):
             P.pnp_debug_inject_tc_timeout(*args)
+        with pytest.raises(P.PnpError):
+            P.pnp_debug_inject_update_timeout(*args)
+
+
+def test_pipelined_update_reports_timeout_then_recovers_bitwise(P):
+    """The one-pass update's TMA-filled windows complete on mbarriers with
+    bounded waits. CTA 0 skips issuing the window of its first tile (nothing is
+    in flight for it), its wait gives up after BUDGET cycles, it reports
+    PNP_ETIMEOUT and still arrives on the step counter (t advances); after
+    pnp_set_state the chain steps bitwise as a fresh problem does."""
+    prob = synth.make_problem(256, 256, synth.gaussian_kernel(7, 1.5), 25.0, 79)   # one-pass form
+    x0 = np.clip(prob.y + 0.02, 0, 1).astype(np.float32)
+    P.pnp_set_graph_mode(False)            # the hook only reaches eager launches
+    try:
+        gp = P.Problem(prob.y, prob.h, prob.sigma, None, seed=prob.seed)
+        gp.set_state(x0, 0)
+        P.pnp_debug_inject_update_timeout(0, 0, BUDGET)
+        gp.step(1)
+        with pytest.raises(P.PnpError) as e:
+            gp.sync()
+        assert e.value.status == 5 and "bounded wait" in str(e.value)
+        gp.sync()                          # reported once, then cleared
+        assert gp.state()[1] == 1          # every CTA arrived: t advanced once
+        gp.set_state(x0, 0)
+        gp.step(2)
+        got, t = gp.state()
+        fresh = P.Problem(prob.y, prob.h, prob.sigma, None, seed=prob.seed)
+        fresh.set_state(x0, 0)
+        fresh.step(2)
+        want, _ = fresh.state()
+        assert t == 2
+        np.testing.assert_array_equal(got, want)
+    finally:
+        P.pnp_set_graph_mode(True)
