@@ -621,18 +621,42 @@ __global__ void __launch_bounds__(128) k_first_tc(const __grid_constant__ FirstT
         q.yy = (int)(r - (uint32_t)q.img * (uint32_t)J.ny);
         return q;
     };
-    // taps of one pixel of segment q (zero outside the image)
-    auto load_taps = [&](const Seg& q, float v[9]) {
+    // taps of one pixel of segment q (zero outside the image). Lanes hold
+    // consecutive pixels, so only the centre column is loaded per row (raw[0..2])
+    // and the left and right taps come from the adjacent lanes when the taps are
+    // expanded (expand_taps, after the loads have landed); lane 0 loads its left
+    // and lane 31 its right neighbour (raw[3..5]), which lie outside the warp.
+    auto load_taps = [&](const Seg& q, float raw[6]) {
         const FirstJob& J = T.j[q.job];
         const int yy = q.yy, img = q.img, ny = J.ny, nx = J.nx;
         const int xx = q.bx * 128 + p;
+        const int lane = p & 31;
+        const int xe = lane == 0 ? xx - 1 : xx + 1;   // the edge lanes' outside neighbour
+        const bool edge = lane == 0 || lane == 31;
         const float* x = J.x + (int64_t)img * ny * nx;
 #pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const int sy = yy + t / 3 - 1, sx = xx + t % 3 - 1;
-            v[t] = (sy >= 0 && sy < ny && sx >= 0 && sx < nx)
-                       ? __ldg(x + (int64_t)sy * nx + sx)
-                       : 0.f;
+        for (int dy = 0; dy < 3; ++dy) {
+            const int sy = yy + dy - 1;
+            const bool row_ok = sy >= 0 && sy < ny;
+            const float* xr = x + (int64_t)sy * nx;
+            raw[dy] = (row_ok && xx < nx) ? __ldg(xr + xx) : 0.f;
+            raw[3 + dy] = (edge && row_ok && xe >= 0 && xe < nx) ? __ldg(xr + xe) : 0.f;
+        }
+    };
+    // the 9 taps from the raw loads; every thread of the CTA calls it together
+    // (the shuffles need all lanes)
+    auto expand_taps = [&](const float raw[6], float v[9]) {
+        const int lane = p & 31;
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+            const float c = raw[dy];
+            float l = __shfl_up_sync(0xffffffffu, c, 1);
+            float r = __shfl_down_sync(0xffffffffu, c, 1);
+            if (lane == 0) l = raw[3 + dy];
+            if (lane == 31) r = raw[3 + dy];
+            v[3 * dy] = l;
+            v[3 * dy + 1] = c;
+            v[3 * dy + 2] = r;
         }
     };
     auto write_a = [&](int buf, const float v[9]) {
@@ -702,15 +726,19 @@ __global__ void __launch_bounds__(128) k_first_tc(const __grid_constant__ FirstT
 
     bool ok = true;
     uint32_t seg = blockIdx.x;
-    float v[9];
+    float raw[6];
     Seg cur = decompose(seg), prev = cur;
-    if (seg < nseg) load_taps(cur, v);
+    if (seg < nseg) load_taps(cur, raw);
     uint32_t k = 0;
     for (; seg < nseg && ok; seg += gridDim.x, ++k) {
         const int buf = k & 1;
         // A[buf] and TMEM[buf] were last used by segment k - 2, whose MMAs the
         // epilogue of iteration k - 1 waited for
-        write_a(buf, v);
+        {
+            float v[9];
+            expand_taps(raw, v);
+            write_a(buf, v);
+        }
         ptx::fence_proxy_async_shared();   // generic-proxy smem writes -> tensor core
         ptx::tc_fence_before();
         __syncthreads();
@@ -729,7 +757,7 @@ __global__ void __launch_bounds__(128) k_first_tc(const __grid_constant__ FirstT
         __syncwarp();
         // taps of the next segment in flight during the previous segment's epilogue
         const Seg next = decompose(seg + gridDim.x);
-        if (seg + gridDim.x < nseg) load_taps(next, v);
+        if (seg + gridDim.x < nseg) load_taps(next, raw);
         if (k > 0) {
             const int pb = buf ^ 1;
             // block-uniform: every thread leaves the loop in the same iteration
