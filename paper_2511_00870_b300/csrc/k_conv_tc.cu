@@ -451,14 +451,20 @@ __global__ void __launch_bounds__(TcMode<LAST, FP8>::THREADS, 1)
                 } else {
                     // BF16 activations: [img][y][8 cg][xp][8]
                     __nv_bfloat16* o = J->out + ((((int64_t)p.img * J->ny + yy) * 8) * nxp + x) * 8;
-                    const uint32_t keep = valid ? 0xffffffffu : 0u;   // zero outside the valid rect
+                    if (!valid) {
+                        // zero outside the valid rect
+#pragma unroll
+                        for (int cg = 0; cg < 8; ++cg)
+                            *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 8) = make_uint4(0u, 0u, 0u, 0u);
+                        return;
+                    }
 #pragma unroll
                     for (int cg = 0; cg < 8; ++cg) {
                         uint32_t pk[4];
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int c0 = cg * 8 + 2 * e;
-                            pk[e] = pack_bf16_relu(acc(c0) + c.bias[c0], acc(c0 + 1) + c.bias[c0 + 1]) & keep;
+                            pk[e] = pack_bf16_relu(acc(c0) + c.bias[c0], acc(c0 + 1) + c.bias[c0 + 1]);
                         }
                         *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     }
@@ -621,6 +627,35 @@ __global__ void __launch_bounds__(128) k_first_tc(const __grid_constant__ FirstT
         q.yy = (int)(r - (uint32_t)q.img * (uint32_t)J.ny);
         return q;
     };
+    // segment s_new = seg(q) + gridDim.x: within one job, gridDim.x segments are
+    // step_rows rows and step_bx column blocks, so q moves by those (one more
+    // row on a column carry, then image wrap) instead of two divisions; a
+    // segment in a later job is decomposed afresh
+    uint32_t step_rows = 0, step_bx = 0;
+    int step_job = -1;
+    auto advance = [&](const Seg& q, uint32_t s_new) {
+        if (jcur + 1 < T.n && s_new >= T.j[jcur + 1].seg_begin) return decompose(s_new);
+        const FirstJob& J = T.j[jcur];
+        if (step_job != jcur) {
+            step_rows = gridDim.x / J.nsx;
+            step_bx = gridDim.x - step_rows * J.nsx;
+            step_job = jcur;
+        }
+        Seg n = q;
+        uint32_t bx = (uint32_t)q.bx + step_bx, dr = step_rows;
+        if (bx >= J.nsx) {
+            bx -= J.nsx;
+            ++dr;
+        }
+        n.bx = (int)bx;
+        uint32_t yy = (uint32_t)q.yy + dr;
+        while (yy >= (uint32_t)J.ny) {
+            yy -= (uint32_t)J.ny;
+            ++n.img;
+        }
+        n.yy = (int)yy;
+        return n;
+    };
     // taps of one pixel of segment q (zero outside the image). Lanes hold
     // consecutive pixels, so only the centre column is loaded per row (raw[0..2])
     // and the left and right taps come from the adjacent lanes when the taps are
@@ -711,14 +746,20 @@ __global__ void __launch_bounds__(128) k_first_tc(const __grid_constant__ FirstT
             }
         } else {
             __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(J.out) + ((((int64_t)img * ny + yy) * 8) * nxp + xx) * 8;
-            const uint32_t keep = valid ? 0xffffffffu : 0u;   // zero outside the valid rect
+            if (!valid) {
+                // zero outside the valid rect
+#pragma unroll
+                for (int cg = 0; cg < 8; ++cg)
+                    *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 8) = make_uint4(0u, 0u, 0u, 0u);
+                return;
+            }
 #pragma unroll
             for (int cg = 0; cg < 8; ++cg) {
                 uint32_t pk[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
                     pk[e] = pack_bf16_relu(__uint_as_float(acc[cg * 8 + 2 * e]),
-                                           __uint_as_float(acc[cg * 8 + 2 * e + 1])) & keep;
+                                           __uint_as_float(acc[cg * 8 + 2 * e + 1]));
                 *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
         }
@@ -756,7 +797,7 @@ __global__ void __launch_bounds__(128) k_first_tc(const __grid_constant__ FirstT
         }
         __syncwarp();
         // taps of the next segment in flight during the previous segment's epilogue
-        const Seg next = decompose(seg + gridDim.x);
+        const Seg next = advance(cur, seg + gridDim.x);
         if (seg + gridDim.x < nseg) load_taps(next, raw);
         if (k > 0) {
             const int pb = buf ^ 1;
