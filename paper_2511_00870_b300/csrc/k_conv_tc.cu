@@ -57,6 +57,15 @@ __device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
     return r;
 }
 
+// Four FP32 values -> packed E4M3 (a in the lowest byte), saturating to the
+// finite range, with ReLU applied by the conversion.
+__device__ __forceinline__ uint32_t pack_e4m3x4_relu(float a, float b, float c, float d) {
+    unsigned short lo, hi;
+    asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;\n" : "=h"(lo) : "f"(b), "f"(a));
+    asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;\n" : "=h"(hi) : "f"(d), "f"(c));
+    return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
 namespace tc {
 constexpr int F = 64;
 constexpr int SEG = 128;                    // output pixels per row segment (UMMA M)
@@ -430,6 +439,13 @@ __global__ void __launch_bounds__(TcMode<LAST, FP8>::THREADS, 1)
                     // E4M3 activations: [img][y][4 cg][xp][16]
                     uint8_t* o = reinterpret_cast<uint8_t*>(J->out) +
                                  (((int64_t)p.img * J->ny + yy) * 4 * nxp + x) * 16;
+                    if (!valid) {
+                        // zero outside the valid rect
+#pragma unroll
+                        for (int cg = 0; cg < 4; ++cg)
+                            *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 16) = make_uint4(0u, 0u, 0u, 0u);
+                        return;
+                    }
 #pragma unroll
                     for (int cg = 0; cg < 4; ++cg) {
                         uint32_t pk[4];
@@ -439,12 +455,11 @@ __global__ void __launch_bounds__(TcMode<LAST, FP8>::THREADS, 1)
 #pragma unroll
                             for (int h = 0; h < 4; ++h) {
                                 const int ch = cg * 16 + 4 * e + h;
-                                const float t = fmaxf(fmaf(acc(ch), c.scale[ch], c.bias[ch]), 0.f);
-                                v[h] = valid ? t * c.inv_out : 0.f;
+                                // relu(t) s = relu(t s) for the scale s > 0: the
+                                // conversion applies the ReLU
+                                v[h] = fmaf(acc(ch), c.scale[ch], c.bias[ch]) * c.inv_out;
                             }
-                            const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[0], v[1]), __NV_SATFINITE, __NV_E4M3);
-                            const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v[2], v[3]), __NV_SATFINITE, __NV_E4M3);
-                            pk[e] = lo | (hi << 16);
+                            pk[e] = pack_e4m3x4_relu(v[0], v[1], v[2], v[3]);
                         }
                         *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     }
@@ -727,20 +742,22 @@ __global__ void __launch_bounds__(128) k_first_tc(const __grid_constant__ FirstT
         const bool valid = xx < nx && yy >= rc.y0 && yy < rc.y1 && xx >= rc.x0 && xx < rc.x1;
         if constexpr (FP8) {
             uint8_t* o = reinterpret_cast<uint8_t*>(J.out) + (((int64_t)img * ny + yy) * 4 * nxp + xx) * 16;
+            if (!valid) {
+                // zero outside the valid rect
+#pragma unroll
+                for (int cg = 0; cg < 4; ++cg)
+                    *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 16) = make_uint4(0u, 0u, 0u, 0u);
+                return;
+            }
 #pragma unroll
             for (int cg = 0; cg < 4; ++cg) {
                 uint32_t pk[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    float r4[4];
-#pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        const float v = __uint_as_float(acc[cg * 16 + 4 * e + h]);
-                        r4[h] = valid ? fmaxf(v, 0.f) * inv_out : 0.f;
-                    }
-                    const uint32_t l2 = __nv_cvt_float2_to_fp8x2(make_float2(r4[0], r4[1]), __NV_SATFINITE, __NV_E4M3);
-                    const uint32_t h2 = __nv_cvt_float2_to_fp8x2(make_float2(r4[2], r4[3]), __NV_SATFINITE, __NV_E4M3);
-                    pk[e] = l2 | (h2 << 16);
+                    const uint32_t* a = acc + cg * 16 + 4 * e;
+                    // relu(t) s = relu(t s) for s = inv_out > 0: the conversion applies the ReLU
+                    pk[e] = pack_e4m3x4_relu(__uint_as_float(a[0]) * inv_out, __uint_as_float(a[1]) * inv_out,
+                                             __uint_as_float(a[2]) * inv_out, __uint_as_float(a[3]) * inv_out);
                 }
                 *reinterpret_cast<uint4*>(o + (int64_t)cg * nxp * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
